@@ -1,0 +1,372 @@
+"""Throughput of the TBPM hot path on one GB300 (or N independent replicas).
+
+One step = one pass of the whole path over one batch of synthetic input: the
+Chebyshev coefficients, 2048 time steps of the Clenshaw-summed propagation
+with the correlation C(t_n), 4096 KPM moments, and both DOS transforms, for one
+random-phase state on 1024x1024 graphene (N = 2,097,152) with W = 1 eV
+Anderson disorder, FP64, stored matrix (SELL) path. Each rank advances its own
+state (seed = rank): weak scaling, no data-path collective.
+
+The metric is orbital-terms/s = N x (Chebyshev sweeps per step) x states /
+seconds, counting n_steps*(K-1) sweeps for the DOS and ceil(M/2) for the KPM
+moments of the workload, however an implementation obtains them.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Chebyshev orbital-terms/sec (N×terms/s) and HBM GB/s vs peak; FP32+batched vs FP64"
+UNIT = "orbital-terms/s"
+L1 = L2 = 1024
+W_DISORDER = 1.0
+RESCALE = 9.0
+DT = math.pi / 9.0
+N_STEPS = 2048
+M_MOMENTS = 4096
+N_E = 4096
+WORKLOAD = (f"graphene {L1}x{L2} (N={2 * L1 * L2}), W={W_DISORDER} eV Anderson disorder (seed 1), "
+            f"complex128 SELL, 1 random-phase state per GPU; DOS {N_STEPS} steps dt=pi/9 "
+            f"(K=18) + KPM M={M_MOMENTS} Jackson + Hann DOS")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_units(n: int, K: int, n_steps: int = N_STEPS, M: int = M_MOMENTS) -> int:
+    """Orbital-terms of one step of the workload for one state."""
+    return n * (n_steps * (K - 1) + (M + 1) // 2)
+
+
+def build_inputs():
+    import tbpm_inputs as ti
+    n = 2 * L1 * L2
+    h = ti.graphene_csr(L1, L2, onsite=ti.anderson_onsite(n, W_DISORDER, 1))
+    return h
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of one GPU while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def cpu_sample(h, seconds_target=(10.0, 30.0)):
+    """The oracle, as it stands, on a bounded sample of the same workload:
+    full-size matrix, s DOS steps and 8*s KPM moments, s grown until the run
+    takes >= 10 s (capped near 30 s). Returns (orbital-terms/s, sample text)."""
+    import oracle
+    import tbpm_inputs as ti
+    psi0 = ti.random_phase_state(h.n, 0)
+    K = oracle.cheb_num_terms(DT * RESCALE)
+    s = 1
+    while True:
+        t0 = time.perf_counter()
+        oracle.dos_corr(h, RESCALE, psi0, DT, s)
+        oracle.kpm_moments(h, RESCALE, psi0, 8 * s)
+        el = time.perf_counter() - t0
+        if el >= seconds_target[0] or s >= 256:
+            break
+        grow = max(2, int(math.ceil(seconds_target[0] / max(el, 1e-3))))
+        s = min(s * grow, 256) if el * grow < seconds_target[1] else s * 2
+    units = workload_units(h.n, K, s, 8 * s)
+    return units / el, f"N={h.n}, {s} DOS steps (K={K}) + {8 * s} KPM moments, {el:.1f} s"
+
+
+def threads_used() -> int:
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else os.cpu_count()
+
+
+# --------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import tbpm_inputs as ti
+    import paper_2509_26309_gb300 as tb
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)        # the library and the events share it
+    torch.cuda.set_stream(stream)
+    h = build_inputs()
+    n = h.n
+    ctx = tb.tbpm_create(n, h.row_ptr, h.col, h.val, RESCALE,
+                         tb.make_opts(device=local_rank, stream=stream.cuda_stream))
+    psi_host = ti.random_phase_state(n, rank).reshape(1, n)
+    dpsi = torch.from_numpy(psi_host).to(dev)
+    dcorr = torch.empty((1, N_STEPS + 1), dtype=torch.complex128, device=dev)
+    dmu = torch.empty((1, M_MOMENTS), dtype=torch.complex128, device=dev)
+    launches = [0]
+
+    def count():
+        launches[0] += tb.tbpm_get_info(ctx)["kernel_launches"]
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        tb.tbpm_dos_corr(ctx, dpsi, DT, N_STEPS, out=dcorr)
+        count()
+        if ev is not None:
+            ev[1].record(stream)
+        tb.kpm_moments(ctx, dpsi, M_MOMENTS, out=dmu)
+        count()
+        tb.tbpm_dos_from_corr(ctx, dcorr[0], DT)
+        count()
+        tb.kpm_dos_jackson(ctx, dmu[0], N_E)
+        count()
+
+    for _ in range(args.warmup):
+        step()
+    tb.tbpm_dos_corr(ctx, dpsi, DT, 1, out=dcorr[:, :2])
+    K = tb.tbpm_get_info(ctx)["num_terms"]
+    torch.cuda.synchronize()
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.barrier()
+    launches[0] = 0
+    dos_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clocks:
+        torch.cuda.synchronize()
+        start.record(stream)
+        for i in range(args.steps):
+            step(dos_ev[i])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        td.barrier()
+    gpu_launches = launches[0]
+    ms = start.elapsed_time(stop)
+    dos_ms = sum(a.elapsed_time(b) for a, b in dos_ev) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist:
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+    ms_max = float(t.item())
+    units = workload_units(n, K) * world * args.steps
+    value = units / (ms_max / 1e3)
+
+    # roofline of the dominant kernel family (the Clenshaw sweeps), measured
+    # over the timed region: DOS part time / sweeps; algorithmic bytes per row
+    # summed over the K-1 sweeps of one step (stored real matrix, FP64 vectors).
+    info = tb.tbpm_get_info(ctx)
+    # per row: 3 hoppings (int32 column + value), FP64 diagonal, slice offsets
+    mat = 3 * (4 + (8 if info["real_values"] else 16)) + 8 + 0.5
+    per_step_row = ((mat + 32) + (mat + 48) + (K - 4) * (mat + 64) + (mat + 80))
+    sweeps = N_STEPS * (K - 1)
+    bytes_per_sweep = n * per_step_row / (K - 1)
+    sweep_s = dos_ms / 1e3 / sweeps
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    hbm = float(peaks["hbm_gbs"])
+    achieved = bytes_per_sweep / sweep_s / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": profile_traffic(),
+                "kernel": "Clenshaw sweep (sweep_b1, FP64 SELL real values)",
+                "bytes_per_sweep": round(bytes_per_sweep), "sweep_us": round(sweep_s * 1e6, 2),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+
+    # e2e: the same step through the public API with pinned host buffers,
+    # H2D of psi0 and D2H of every result inside the timed region
+    hpsi = torch.from_numpy(psi_host.copy()).pin_memory()
+    hcorr = torch.empty((1, N_STEPS + 1), dtype=torch.complex128).pin_memory()
+    hmu = torch.empty((1, M_MOMENTS), dtype=torch.complex128).pin_memory()
+
+    def e2e_step():
+        tb.tbpm_dos_corr(ctx, hpsi, DT, N_STEPS, out=hcorr)
+        tb.kpm_moments(ctx, hpsi, M_MOMENTS, out=hmu)
+        tb.tbpm_dos_from_corr(ctx, hcorr[0], DT)
+        tb.kpm_dos_jackson(ctx, hmu[0], N_E)
+
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        td.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if dist:
+        td.all_reduce(te, op=td.ReduceOp.MAX)
+    e2e_value = workload_units(n, K) * world * e2e_steps / float(te.item())
+    h2d = 2 * n * 16 + (N_STEPS + 1) * 16 + M_MOMENTS * 16
+    d2h = (N_STEPS + 1) * 16 + M_MOMENTS * 16 + 2 * (2 * N_STEPS) * 8 + 2 * N_E * 8
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": n, "n_steps": N_STEPS, "M": M_MOMENTS, "K": K,
+                   "states_per_gpu": 1, "path": "sell", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: matrix 93 MB + 4 state vectors 134 MB"},
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": gpu_launches,
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample = cpu_sample(h)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+                               "sample": sample}
+    tb.tbpm_destroy(ctx)
+    return out
+
+
+def profile_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_2509_26309_gb300", "csrc", "cheb_sweep.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("cheb_sweep_sha") != digest:
+        return None
+    return rec.get("sweep_traffic_bytes")
+
+
+# --------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: each step is a bounded sample
+    of the workload (full matrix, 4 DOS steps + 32 KPM moments)."""
+    import oracle
+    import tbpm_inputs as ti
+    h = build_inputs()
+    psi0 = ti.random_phase_state(h.n, 0)
+    K = oracle.cheb_num_terms(DT * RESCALE)
+    s_dos, s_kpm = 4, 32
+
+    def step():
+        oracle.dos_corr(h, RESCALE, psi0, DT, s_dos)
+        oracle.kpm_moments(h, RESCALE, psi0, s_kpm)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    units = workload_units(h.n, K, s_dos, s_kpm) * args.steps
+    v = units / el
+    sample = f"N={h.n}, per step {s_dos} DOS steps (K={K}) + {s_kpm} KPM moments"
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": h.n, "n_steps": N_STEPS, "M": M_MOMENTS, "K": K,
+                   "states_per_gpu": 1, "path": "oracle (CPU)", "parallelism": "host cores"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * tbpm.h - C ABI of the GB300 (sm_103a) TBPM hot-path library (libtbpm.so).
+ *
+ * The tight-binding propagation method (TBPLaS 2.0, arXiv 2509.26309) evolves
+ * random-phase states with the Chebyshev expansion of exp(-iHt) and records
+ * the correlation C(t_n) = <psi0|psi(t_n)> (Sec. 2.2.1, the propagation
+ * listings; Sec. 3.2.3, calc_corr_dos), and evaluates kernel-polynomial
+ * moments mu_m = <psi0|T_m(H~)|psi0> (Sec. 1). The calls follow the order of
+ * the paper's workflow (Sec. 2.2.2, Sec. 3.2.3): build the model, create the
+ * solver with its rescale factor, run calc_corr_dos, analyse the DOS.
+ *
+ * Conventions shared by every call:
+ *   - Complex numbers are two doubles (re, im), interleaved.
+ *   - Energies in eV, times in hbar/eV (hbar = 1). H~ = H / rescale.
+ *   - Pointers to state, correlation, moment and DOS arrays may be host
+ *     memory (pageable or pinned) or device memory of the context's GPU; the
+ *     library tells them apart with cudaPointerGetAttributes. With host
+ *     buffers a call returns after its results are in host memory. With
+ *     device buffers a call only enqueues work on the context's stream and
+ *     returns; synchronise that stream before reading the results.
+ *   - The caller owns every buffer it passes; the library copies what it
+ *     needs and never keeps a caller pointer after a call returns.
+ *   - Every function returns TBPM_OK (0) or a negative status; no exception
+ *     crosses this boundary. Arguments are validated before any GPU work.
+ *   - A context serves one host thread at a time; calls on one context are
+ *     ordered on its stream.
+ */
+#ifndef TBPM_H
+#define TBPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ statuses */
+#define TBPM_OK                 0
+#define TBPM_ERR_ARG           -1  /* NULL pointer, size or option out of range   */
+#define TBPM_ERR_CSR           -2  /* row_ptr not monotone, column out of range    */
+#define TBPM_ERR_NOT_HERMITIAN -3  /* H_ij != conj(H_ji), or complex diagonal      */
+#define TBPM_ERR_RESCALE       -4  /* rescale below the Gershgorin bound of H     */
+#define TBPM_ERR_OOM           -5  /* device or host allocation failed            */
+#define TBPM_ERR_CUDA          -6  /* a CUDA runtime call failed                  */
+#define TBPM_ERR_TIMEOUT       -7  /* a bounded device wait gave up               */
+#define TBPM_ERR_NO_DEVICE     -8  /* no usable sm_103 GPU                         */
+#define TBPM_ERR_UNSUPPORTED   -9  /* valid request this build does not serve     */
+
+/* ------------------------------------------------------------- options */
+#define TBPM_FP64 0                /* complex128 vectors, FP64 matrix values        */
+#define TBPM_FP32 1                /* complex64 vectors and hoppings; Bessel
+                                      coefficients, dots and moments stay FP64     */
+
+#define TBPM_PATH_AUTO    0        /* stencil for lattice contexts, SELL otherwise */
+#define TBPM_PATH_SELL    1        /* stored matrix, sliced ELLPACK (32-row slices) */
+#define TBPM_PATH_STENCIL 2        /* matrix-free lattice stencil (lattice only)   */
+
+#define TBPM_F_NO_HERMITIAN_CHECK 0x1u /* skip the O(nnz) H = H^dagger check        */
+#define TBPM_F_FORCE_RESCALE      0x2u /* accept rescale below the Gershgorin bound */
+#define TBPM_F_RENORM             0x4u /* FP32: renormalise psi to 1 after each step */
+
+typedef struct tbpm_opts {
+    int precision;       /* TBPM_FP64 | TBPM_FP32                                  */
+    int path;            /* TBPM_PATH_*                                            */
+    unsigned flags;      /* TBPM_F_* bit set                                       */
+    int device;          /* CUDA device ordinal; -1 = the calling thread's current */
+    void *stream;        /* cudaStream_t to order work on; NULL = the legacy
+                            default stream of the device                           */
+    double bessel_tol;   /* Chebyshev cutoff |J_k| < tol; 0 selects 1e-12          */
+} tbpm_opts;
+
+/* Fills *opts with the defaults: FP64, PATH_AUTO, no flags, current device,
+ * legacy default stream, tolerance 1e-12. Returns TBPM_ERR_ARG if opts is NULL. */
+int tbpm_default_opts(tbpm_opts *opts);
+
+typedef struct tbpm_ctx tbpm_ctx;
+
+/* --------------------------------------------------------------- create */
+
+/* tbpm_create: the solver for a Hamiltonian given in CSR form (the sparse
+ * H_csr of Sec. 2.2.1; the rescale of config.rescale, Sec. 3.2.3).
+ *   n        number of orbitals, 1 <= n < 2^31
+ *   row_ptr  HOST int64[n+1], row_ptr[0] = 0, non-decreasing
+ *   col      HOST int32[nnz] column indices in [0, n), nnz = row_ptr[n]
+ *   val      HOST double[2*nnz] complex values H_ij (re, im)
+ *   rescale  > 0; H~ = H / rescale must have spectrum in [-1, 1]. Rejected
+ *            with TBPM_ERR_RESCALE if below max_i sum_j |H_ij| unless
+ *            TBPM_F_FORCE_RESCALE is set.
+ *   opts     NULL for defaults.
+ * Checks (host, before any GPU work): CSR structure (TBPM_ERR_CSR); real
+ * diagonal and, unless TBPM_F_NO_HERMITIAN_CHECK, H_ij = conj(H_ji)
+ * (TBPM_ERR_NOT_HERMITIAN). Repeated (i, j) entries are summed. The matrix is
+ * converted to the device layout once; a matrix whose values are all real is
+ * stored with real values. *out receives a context that owns all device
+ * memory until tbpm_destroy. */
+int tbpm_create(tbpm_ctx **out, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                const double *val, double rescale, const tbpm_opts *opts);
+
+#define TBPM_LATTICE_GRAPHENE   0  /* monolayer: i = 2*(m1*L2 + m2) + s, s = A, B */
+#define TBPM_LATTICE_AB_BILAYER 1  /* AB bilayer: i = 4*(m1*L2 + m2) + o,
+                                      o = A1, B1, A2, B2; dimer pair A1-B2       */
+
+typedef struct tbpm_lattice {
+    int kind;              /* TBPM_LATTICE_*                                     */
+    int64_t l1, l2;        /* periodic supercell of L1 x L2 primitive cells     */
+    double t;              /* nearest-neighbour hopping (eV), -2.7 for graphene */
+    double t_perp;         /* interlayer dimer hopping (eV), bilayer only       */
+    const double *onsite;  /* HOST double[N] on-site energies, or NULL (zero)   */
+} tbpm_lattice;
+
+/* tbpm_create_lattice: the solver for a periodic graphene or AB-bilayer
+ * supercell (the graphene primitive cell and hopping convention of Sec.
+ * 3.2.1: <A,0|H|B,0> = t, <B,0|H|A,a1> = t, <B,0|H|A,a2> = t, completed by
+ * H_ij(R) = H_ji(-R)^*). With TBPM_PATH_STENCIL (the AUTO choice) no matrix
+ * is stored: the kernels compute H~ v from the lattice and the on-site array.
+ * With TBPM_PATH_SELL the same matrix is assembled and stored. Requires
+ * L1, L2 >= 3. Errors as tbpm_create. */
+int tbpm_create_lattice(tbpm_ctx **out, const tbpm_lattice *lat, double rescale,
+                        const tbpm_opts *opts);
+
+/* Releases every resource of ctx (NULL is ignored). */
+void tbpm_destroy(tbpm_ctx *ctx);
+
+/* ------------------------------------------------------------ hot path */
+
+/* tbpm_dos_corr: time evolution and DOS correlation (calc_corr_dos,
+ * Sec. 3.2.3; the series loop of Sec. 2.2.1).
+ * For each state j, psi(t_0) = psi0_j and, for n = 0..n_steps-1,
+ *   psi(t_{n+1}) = sum_{k<K} c_k T_k(H~) psi(t_n),
+ *   c_k = (2 - delta_k0) (-i)^k J_k(dt * rescale),
+ * K = the first k > |dt*rescale| with |J_k| < bessel_tol; the coefficients
+ * are generated on the GPU. Writes corr[j*(n_steps+1) + n] = <psi0_j|psi(t_n)>
+ * for n = 0..n_steps (complex, so 2*(n_steps+1) doubles per state).
+ *   psi0     double[2*n*nstates], state-major: state j at offset 2*n*j
+ *   nstates  >= 1. FP32 contexts advance up to 16 states together as one
+ *            block; FP64 contexts advance states one after another.
+ *   dt       time step, dt != 0, |dt*rescale| <= 40 (K <= 64)
+ *   n_steps  >= 0
+ * The states are not normalised by the library. */
+int tbpm_dos_corr(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, int n_steps,
+                  double *corr);
+
+/* kpm_moments: mu_m = <psi0_j|T_m(H~)|psi0_j>, m = 0..M-1 (the kernel
+ * polynomial method named in Sec. 1), written as complex numbers to
+ * mu[j*M + m]. The GPU uses the product identities
+ *   mu_{2m} = 2<T_m|T_m> - mu_0,  mu_{2m+1} = 2<T_{m+1}|T_m> - mu_1
+ * (T_m = T_m(H~) psi0), so about M/2 matrix products are made.
+ *   psi0  as tbpm_dos_corr;  M >= 1. */
+int kpm_moments(tbpm_ctx *ctx, const double *psi0, int nstates, int M, double *mu);
+
+/* ------------------------------------------------------- DOS post-step */
+
+/* tbpm_dos_from_corr: the DOS from one correlation (Analyzer.calc_dos,
+ * Sec. 3.2.3), on the GPU: with N = n_steps, C(-t) = conj C(t) and the Hann
+ * window w_m = (1 + cos(pi m / N)) / 2,
+ *   D(E_j) = dt/(2 pi) sum_{m=-N}^{N-1} w_m C(t_m) exp(i E_j t_m),
+ *   E_j = (j - N) pi / (N dt),  j = 0..2N-1.
+ *   corr      double[2*(n_steps+1)] complex C(t_0..t_N), host or device
+ *   energies  double[2N] out; dos double[2N] out (real part). n_steps >= 1. */
+int tbpm_dos_from_corr(tbpm_ctx *ctx, const double *corr, int n_steps, double dt,
+                       double *energies, double *dos);
+
+/* kpm_dos_jackson: the KPM DOS with the Jackson kernel
+ *   g_m = [(M-m+1) cos(pi m/(M+1)) + sin(pi m/(M+1)) cot(pi/(M+1))] / (M+1),
+ *   rho(x) = [g_0 mu_0 + 2 sum_{m>=1} g_m mu_m T_m(x)] / (pi sqrt(1-x^2)),
+ * on the n_e Chebyshev nodes x_j = cos(pi (j+1/2)/n_e); energies[j] =
+ * rescale*x_j, rho_out[j] = rho(x_j)/rescale. Uses Re(mu).
+ *   mu  double[2*M] complex moments, host or device; n_e >= 1. */
+int kpm_dos_jackson(tbpm_ctx *ctx, const double *mu, int M, int n_e, double *energies,
+                    double *rho_out);
+
+/* ---------------------------------------------------------- diagnostics */
+
+typedef struct tbpm_info {
+    int64_t n;                 /* orbitals                                      */
+    int64_t nnz;               /* stored off-diagonal entries (0 for stencil)   */
+    int path;                  /* TBPM_PATH_SELL | TBPM_PATH_STENCIL in use     */
+    int precision;             /* TBPM_FP64 | TBPM_FP32                         */
+    int real_values;           /* 1 when the stored hoppings are real           */
+    int num_terms;             /* K of the last tbpm_dos_corr call              */
+    int64_t passes;            /* sparse-product passes of the last call        */
+    int64_t kernel_launches;   /* kernels the last call launched                */
+    double gershgorin;         /* max_i sum_j |H_ij|                            */
+    double rescale;
+} tbpm_info;
+
+/* Fills *info with the context's layout and the counters of its last call. */
+int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info);
+
+/* A static, human-readable name for a status code. */
+const char *tbpm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TBPM_H */

@@ -1,0 +1,257 @@
+// Small kernels around the sweeps: Chebyshev coefficients, dots, deterministic
+// reductions, state loading and the KPM moment assembly.
+#include "tbpm_internal.cuh"
+
+namespace tbpm {
+namespace {
+
+// c_k = (2 - delta_k0) (-i)^k J_k(x) for k < kMaxTerms, and K = the first
+// k > |x| with |J_k(x)| < tol (the cutoff of the series; the coefficient
+// array of the propagation listings of Sec. 2.2.1).
+//
+// J_k(|x|) comes from Miller's backward recurrence (J.C.P. Miller 1952; the
+// method of Abramowitz & Stegun 9.12, Example 1): start far above the wanted
+// orders with J_{m+1} = 0, J_m = tiny, run J_{k-1} = (2k/x) J_k - J_{k+1}
+// down to k = 0, and normalise with the identity J_0 + 2 sum_{k>=1} J_{2k} = 1
+// (A&S 9.1.46). The recurrence is stable downwards and the normalisation
+// removes the arbitrary start value. Whenever the running values exceed 1e200
+// they and everything stored so far are scaled by 1e-200. Below |x| = 0.5 the
+// power series J_k(x) = sum_m (-1)^m (x/2)^{2m+k} / (m! (m+k)!) (A&S 9.1.10)
+// converges in a few terms without cancellation and is used instead, which
+// also keeps the recurrence ratio 2k/x bounded. J_k(-x) = (-1)^k J_k(x)
+// (A&S 9.1.5).
+__global__ void bessel_kernel(double x, double tol, double2 *coef, int *K_out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double ax = fabs(x);
+    double j[kMaxTerms];
+    if (ax < 0.5) {
+        const double h = 0.5 * ax, h2 = h * h;
+        double lead = 1.0;                               // (x/2)^k / k!
+        for (int k = 0; k < kMaxTerms; ++k) {
+            if (k > 0) lead *= h / k;
+            double term = lead, sum = lead;
+            for (int q = 1; q < 30 && term != 0.0; ++q) {
+                term *= -h2 / ((double)q * (double)(q + k));
+                sum += term;
+            }
+            j[k] = sum;
+        }
+    } else {
+        int m = kMaxTerms + 30 + 2 * (int)ceil(ax);
+        m += (m & 1);                                    // even start order
+        double jp1 = 0.0, jk = 1e-300, norm = 0.0;
+        for (int k = 0; k < kMaxTerms; ++k) j[k] = 0.0;
+        for (int k = m; k >= 1; --k) {
+            // jk = J_k, jp1 = J_{k+1}  ->  J_{k-1}
+            const double jm1 = (2.0 * k / ax) * jk - jp1;
+            if (k < kMaxTerms) j[k] = jk;
+            if ((k & 1) == 0) norm += 2.0 * jk;
+            jp1 = jk;
+            jk = jm1;
+            if (fabs(jk) > 1e200) {
+                jk *= 1e-200; jp1 *= 1e-200; norm *= 1e-200;
+                for (int q = 0; q < kMaxTerms; ++q) j[q] *= 1e-200;
+            }
+        }
+        j[0] = jk;
+        norm += jk;
+        const double inv = 1.0 / norm;
+        for (int k = 0; k < kMaxTerms; ++k) j[k] *= inv;
+    }
+    int K = -1;
+    for (int k = 1; k < kMaxTerms; ++k) {
+        if ((double)k > ax && fabs(j[k]) < tol) { K = k; break; }
+    }
+    for (int k = 0; k < kMaxTerms; ++k) {
+        double v = j[k];
+        if (x < 0.0 && (k & 1)) v = -v;
+        const double f = (k == 0) ? v : 2.0 * v;
+        double2 c;
+        switch (k & 3) {                                  // (-i)^k
+        case 0: c = make_double2(f, 0.0); break;
+        case 1: c = make_double2(0.0, -f); break;
+        case 2: c = make_double2(-f, 0.0); break;
+        default: c = make_double2(0.0, f); break;
+        }
+        coef[k] = c;
+    }
+    *K_out = K;
+}
+
+template <typename R> struct V2;
+template <> struct V2<double> { typedef double2 T; };
+template <> struct V2<float> { typedef float2 T; };
+
+__device__ __forceinline__ double2 block_sum2(double re, double im, double2 *sm)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sm[w] = make_double2(re, im);
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { r.x += sm[i].x; r.y += sm[i].y; }
+    __syncthreads();
+    return r;
+}
+
+// <a|b> per block over rows (grid-stride, the same row order for every call).
+template <typename R>
+__global__ void __launch_bounds__(kBlock) dot_kernel(const void *a_, const void *b_, int64_t rows,
+                                                     double2 *partials)
+{
+    typedef typename V2<R>::T V;
+    __shared__ double2 red[kBlock / 32];
+    const V *a = reinterpret_cast<const V *>(a_);
+    const V *b = reinterpret_cast<const V *>(b_);
+    double re = 0.0, im = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += stride) {
+        const V p = a[i], q = b[i];
+        const double pr = p.x, pi = p.y, qr = q.x, qi = q.y;
+        re = fma(pr, qr, fma(pi, qi, re));
+        im = fma(pr, qi, fma(-pi, qr, im));
+    }
+    const double2 r = block_sum2(re, im, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = r;
+}
+
+// One warp per (slot, term): lane-strided partial sums, then a fixed butterfly.
+__global__ void reduce_kernel(const double2 *partials, int nslot, int nterm, int nblk,
+                              const int *counter, int offset, double2 *out)
+{
+    const int wid = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (wid >= nslot * nterm) return;
+    const int d = wid / nterm, q = wid - d * nterm;
+    const double2 *p = partials + ((int64_t)d * nterm + q) * nblk;
+    double re = 0.0, im = 0.0;
+    for (int b = lane; b < nblk; b += 32) { re += p[b].x; im += p[b].y; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+        const int base = counter ? *counter : 0;
+        out[(int64_t)(base + offset + d) * nterm + q] = make_double2(re, im);
+    }
+}
+
+__global__ void advance_kernel(int *counter, int by)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *counter += by;
+}
+
+// src: FP64 complex [nstates][n] (state-major); dst: R2 [n_pad][B] for states
+// j0 .. j0+B-1, zero for padding rows and for states >= nstates.
+template <typename R>
+__global__ void load_states_kernel(const double2 *src, int64_t n, int64_t n_pad, int nstates,
+                                   int j0, int B, void *dst0_, void *dst1_)
+{
+    typedef typename V2<R>::T V;
+    V *dst0 = reinterpret_cast<V *>(dst0_);
+    V *dst1 = reinterpret_cast<V *>(dst1_);
+    const int64_t total = n_pad * B;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const int64_t row = e / B;
+        const int j = (int)(e - row * B) + j0;
+        V v;
+        if (row < n && j < nstates) {
+            const double2 s = src[(int64_t)j * n + row];
+            v.x = (R)s.x; v.y = (R)s.y;
+        } else {
+            v.x = (R)0; v.y = (R)0;
+        }
+        if (dst0) dst0[e] = v;
+        if (dst1) dst1[e] = v;
+    }
+}
+
+// dots[q] = (<T_q|T_q>, <T_{q+1}|T_q>), q = 0..; the product identities
+//   mu_{2q} = 2<T_q|T_q> - mu_0,  mu_{2q+1} = 2<T_q|T_{q+1}> - mu_1
+// with mu_0 = <T_0|T_0> and mu_1 = <T_0|T_1>.
+__global__ void kpm_finalize_kernel(const double2 *dots, int M, double2 *mu)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const double2 mu0 = dots[0];
+    const double2 c01 = dots[1];                          // <T_1|T_0>
+    const double2 mu1 = make_double2(c01.x, -c01.y);      // <T_0|T_1>
+    double2 r;
+    if (m == 0) r = mu0;
+    else if (m == 1) r = mu1;
+    else if ((m & 1) == 0) {
+        const double2 d = dots[(m >> 1) * 2];
+        r = make_double2(2.0 * d.x - mu0.x, 2.0 * d.y - mu0.y);
+    } else {
+        const double2 d = dots[(m >> 1) * 2 + 1];         // <T_{q+1}|T_q>
+        r = make_double2(2.0 * d.x - mu1.x, -2.0 * d.y - mu1.y);
+    }
+    mu[m] = r;
+}
+
+}  // namespace
+
+cudaError_t launch_bessel(double x, double tol, double2 *d_coef, int *d_K, cudaStream_t s)
+{
+    bessel_kernel<<<1, 32, 0, s>>>(x, tol, d_coef, d_K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot(int precision, const void *a, const void *b, int64_t rows,
+                       double2 *partials, int grid, cudaStream_t s)
+{
+    if (precision == TBPM_FP64) dot_kernel<double><<<grid, kBlock, 0, s>>>(a, b, rows, partials);
+    else dot_kernel<float><<<grid, kBlock, 0, s>>>(a, b, rows, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double2 *partials, int nslot, int nterm, int nblk,
+                          const int *counter, int offset, double2 *out, cudaStream_t s)
+{
+    const int warps = nslot * nterm;
+    if (warps <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (warps * 32 + threads - 1) / threads;
+    reduce_kernel<<<blocks, threads, 0, s>>>(partials, nslot, nterm, nblk, counter, offset, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance(int *counter, int by, cudaStream_t s)
+{
+    advance_kernel<<<1, 32, 0, s>>>(counter, by);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_states(int precision, const double *src, int64_t n, int64_t n_pad,
+                               int nstates_src, int j0, int B, void *dst0, void *dst1,
+                               cudaStream_t s)
+{
+    const int64_t total = n_pad * B;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    if (blocks < 1) blocks = 1;
+    const double2 *sp = reinterpret_cast<const double2 *>(src);
+    if (precision == TBPM_FP64)
+        load_states_kernel<double><<<(int)blocks, 256, 0, s>>>(sp, n, n_pad, nstates_src, j0, B, dst0, dst1);
+    else
+        load_states_kernel<float><<<(int)blocks, 256, 0, s>>>(sp, n, n_pad, nstates_src, j0, B, dst0, dst1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kpm_finalize(const double2 *dots, int M, int states, double2 *mu,
+                                cudaStream_t s)
+{
+    (void)states;
+    kpm_finalize_kernel<<<(M + 255) / 256, 256, 0, s>>>(dots, M, mu);
+    return cudaGetLastError();
+}
+
+}  // namespace tbpm

@@ -1,0 +1,357 @@
+// Fused Chebyshev sweeps: sparse (or stencil) product, three-term recurrence,
+// series accumulation and the correlation dot, one HBM pass per term.
+//
+// The series of one time step (Sec. 2.2.1, the propagation listings),
+//   psi(t+dt) = sum_{k<K} c_k T_k(H~) psi,   c_k = (2 - delta_k0)(-i)^k J_k(dt*rescale),
+// is summed here by Clenshaw's backward recurrence instead of the forward
+// recurrence of the listings. With b_K = b_{K+1} = 0,
+//   b_k = c_k psi + 2 H~ b_{k+1} - b_{k+2}      (k = K-1 .. 1),
+//   psi(t+dt) = c_0 psi + H~ b_1 - b_2.
+// Both forms make K-1 sparse products per step. The backward form keeps no
+// running sum vector: each sweep reads psi, gathers b_{k+1}, and overwrites
+// b_{k+2} with b_k in place, 4 vector streams per row instead of the 5 of the
+// forward form (T_{k-1}, T_{k-2} -> T_k, out read and written). As in the
+// paper's C++ form, the imaginary factors stay in the coefficients, so the
+// sparse product is real-scalar: c_k is real for even k and imaginary for odd
+// k, and each sweep multiplies psi by a purely real or purely imaginary number.
+//
+// The stored operator is pre-scaled at create time to A = 2 H / rescale, so a
+// sweep forms acc = A x and
+//   FIRST  (k = K-2): y = c_{K-2} psi + c_{K-1} A psi
+//   SECOND (k = K-3): y = (c_{K-3} - c_{K-1}) psi + A b_{K-2}
+//   MID    (k < K-3): y = c_k psi + A b_{k+1} - b_{k+2}           (y aliases b_{k+2})
+//   FINAL  (k = 0)  : y = (c_0 - [K=3] c_2) psi + A b_1 / 2 - [K>=4] b_2   (y aliases psi)
+// and the final sweep also accumulates <psi0|y> into per-block partials.
+// The KPM sweep (Sec. 1) is T_{m+1} = A T_m - T_{m-1} with the two dots that
+// the doubling identities need.
+#include "tbpm_internal.cuh"
+
+namespace tbpm {
+namespace {
+
+template <typename R> struct V2;
+template <> struct V2<double> { typedef double2 T; };
+template <> struct V2<float> { typedef float2 T; };
+
+enum BMode { B_ONE = 0, B_REAL = 1, B_IMAG = 2 };
+
+// acc = A x for row `row` of a SELL slice, accumulated onto (ar, ai).
+template <typename R, bool REALV>
+__device__ __forceinline__ void sell_apply(const SweepParams &p, int64_t s, int lane,
+                                           const typename V2<R>::T *__restrict__ x,
+                                           R &ar, R &ai)
+{
+    typedef typename V2<R>::T V;
+    const int64_t off = __ldg(p.slice_off + s);
+    const int w = (int)((__ldg(p.slice_off + s + 1) - off) >> 5);
+    const int32_t *cp = p.cols + off + lane;
+    if (REALV) {
+        const R *vp = reinterpret_cast<const R *>(p.vals) + off + lane;
+        int j = 0;
+        for (; j + 4 <= w; j += 4) {
+            int c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * (j + 1));
+            int c2 = __ldg(cp + 32 * (j + 2)), c3 = __ldg(cp + 32 * (j + 3));
+            R v0 = __ldg(vp + 32 * j), v1 = __ldg(vp + 32 * (j + 1));
+            R v2 = __ldg(vp + 32 * (j + 2)), v3 = __ldg(vp + 32 * (j + 3));
+            V x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+            ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
+            ar = fma(v1, x1.x, ar); ai = fma(v1, x1.y, ai);
+            ar = fma(v2, x2.x, ar); ai = fma(v2, x2.y, ai);
+            ar = fma(v3, x3.x, ar); ai = fma(v3, x3.y, ai);
+        }
+        if (j + 2 <= w) {
+            int c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * (j + 1));
+            R v0 = __ldg(vp + 32 * j), v1 = __ldg(vp + 32 * (j + 1));
+            V x0 = __ldg(x + c0), x1 = __ldg(x + c1);
+            ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
+            ar = fma(v1, x1.x, ar); ai = fma(v1, x1.y, ai);
+            j += 2;
+        }
+        if (j < w) {
+            int c0 = __ldg(cp + 32 * j);
+            R v0 = __ldg(vp + 32 * j);
+            V x0 = __ldg(x + c0);
+            ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
+        }
+    } else {
+        const V *vp = reinterpret_cast<const V *>(p.vals) + off + lane;
+        int j = 0;
+        for (; j + 2 <= w; j += 2) {
+            int c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * (j + 1));
+            V v0 = __ldg(vp + 32 * j), v1 = __ldg(vp + 32 * (j + 1));
+            V x0 = __ldg(x + c0), x1 = __ldg(x + c1);
+            ar = fma(v0.x, x0.x, fma(-v0.y, x0.y, ar)); ai = fma(v0.x, x0.y, fma(v0.y, x0.x, ai));
+            ar = fma(v1.x, x1.x, fma(-v1.y, x1.y, ar)); ai = fma(v1.x, x1.y, fma(v1.y, x1.x, ai));
+        }
+        if (j < w) {
+            int c0 = __ldg(cp + 32 * j);
+            V v0 = __ldg(vp + 32 * j);
+            V x0 = __ldg(x + c0);
+            ar = fma(v0.x, x0.x, fma(-v0.y, x0.y, ar)); ai = fma(v0.x, x0.y, fma(v0.y, x0.x, ai));
+        }
+    }
+}
+
+// acc = A x - (on-site part excluded) for a periodic lattice row, onto (ar, ai).
+// Monolayer, row = 2 cell + s, cell = m1 L2 + m2:
+//   A(m) couples to B(m), B(m - a1), B(m - a2); B(m) to A(m), A(m + a1), A(m + a2).
+// Bilayer, row = 4 cell + o (o = A1, B1, A2, B2): each layer as above, plus the
+// dimer bond A1(m) - B2(m).
+template <typename R, int OP>
+__device__ __forceinline__ void stencil_apply(const SweepParams &p, int64_t row,
+                                              const typename V2<R>::T *__restrict__ x,
+                                              R &ar, R &ai)
+{
+    typedef typename V2<R>::T V;
+    const int per = (OP == OP_STENCIL_MONO) ? 2 : 4;
+    const int64_t cell = row / per;
+    const int o = (int)(row - cell * per);
+    const int64_t m1 = cell / p.l2;
+    const int64_t m2 = cell - m1 * p.l2;
+    const int layer = o >> 1;
+    const int s = o & 1;
+    const int64_t base_o = 2 * layer;                   // orbital of A in this layer
+    int64_t n0, n1, n2;                                 // the three in-layer neighbours
+    if (s == 0) {                                       // A: B(m), B(m-a1), B(m-a2)
+        const int64_t mm1 = (m1 == 0) ? p.l1 - 1 : m1 - 1;
+        const int64_t mm2 = (m2 == 0) ? p.l2 - 1 : m2 - 1;
+        n0 = cell * per + base_o + 1;
+        n1 = (mm1 * p.l2 + m2) * per + base_o + 1;
+        n2 = (m1 * p.l2 + mm2) * per + base_o + 1;
+    } else {                                            // B: A(m), A(m+a1), A(m+a2)
+        const int64_t pm1 = (m1 == p.l1 - 1) ? 0 : m1 + 1;
+        const int64_t pm2 = (m2 == p.l2 - 1) ? 0 : m2 + 1;
+        n0 = cell * per + base_o;
+        n1 = (pm1 * p.l2 + m2) * per + base_o;
+        n2 = (m1 * p.l2 + pm2) * per + base_o;
+    }
+    const V x0 = __ldg(x + n0), x1 = __ldg(x + n1), x2 = __ldg(x + n2);
+    const R t = (R)p.t;
+    ar = fma(t, x0.x + x1.x + x2.x, ar);
+    ai = fma(t, x0.y + x1.y + x2.y, ai);
+    if (OP == OP_STENCIL_BI && (o == 0 || o == 3)) {
+        const V xd = __ldg(x + (o == 0 ? cell * 4 + 3 : cell * 4));
+        const R tp = (R)p.t_perp;
+        ar = fma(tp, xd.x, ar);
+        ai = fma(tp, xd.y, ai);
+    }
+}
+
+// Block-wide deterministic sum of (re, im) pairs: fixed butterfly in each warp,
+// then warp 0 adds the warp results in order. Result valid in thread 0.
+__device__ __forceinline__ double2 block_sum(double re, double im, double2 *sm)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sm[w] = make_double2(re, im);
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { r.x += sm[i].x; r.y += sm[i].y; }
+    }
+    __syncthreads();
+    return r;
+}
+
+// One Clenshaw sweep for a single state per row (B = 1).
+template <typename R, int OP, bool REALV, int BM, bool AIMAG, bool HASZ, bool FINAL>
+__global__ void __launch_bounds__(kBlock) sweep_b1(SweepParams p)
+{
+    typedef typename V2<R>::T V;
+    __shared__ double2 red[kBlock / 32];
+    // coefficients: a on psi (real or imaginary), beta on A x
+    const double2 ca = p.coef[p.ia];
+    const double2 cb = p.ib >= 0 ? p.coef[p.ib] : make_double2(0.0, 0.0);
+    const R a = (R)(AIMAG ? (ca.y - cb.y) : (ca.x - cb.x));
+    R beta = (R)p.bscale;
+    if (BM == B_REAL && p.ic >= 0) beta = (R)(p.bscale * p.coef[p.ic].x);
+    if (BM == B_IMAG && p.ic >= 0) beta = (R)(p.bscale * p.coef[p.ic].y);
+
+    const V *__restrict__ x = reinterpret_cast<const V *>(p.x);
+    const V *psi = reinterpret_cast<const V *>(p.psi);
+    const V *z = reinterpret_cast<const V *>(p.z);
+    V *y = reinterpret_cast<V *>(p.y);
+    const V *psi0 = reinterpret_cast<const V *>(p.psi0);
+    const R *diag = reinterpret_cast<const R *>(p.diag);
+
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double dr = 0.0, di = 0.0;
+
+    for (int64_t s = warp; s < p.nslices; s += nwarps) {
+        const int64_t row = (s << 5) + lane;
+        const V ps = psi[row];
+        // t = a psi - z  (a real: a*psi; a imaginary: i*a*psi)
+        R tr, ti;
+        if (AIMAG) { tr = -a * ps.y; ti = a * ps.x; } else { tr = a * ps.x; ti = a * ps.y; }
+        if (HASZ) { const V zz = z[row]; tr -= zz.x; ti -= zz.y; }
+        const V xi = __ldg(x + row);
+        const R d = diag ? __ldg(diag + row) : (R)0;
+        R ar, ai;
+        if (BM == B_ONE) { ar = fma(d, xi.x, tr); ai = fma(d, xi.y, ti); }
+        else { ar = d * xi.x; ai = d * xi.y; }
+        if (OP == OP_SELL) sell_apply<R, REALV>(p, s, lane, x, ar, ai);
+        else if (row < p.n) stencil_apply<R, OP>(p, row, x, ar, ai);
+        V out;
+        if (BM == B_ONE) { out.x = ar; out.y = ai; }
+        else if (BM == B_REAL) { out.x = fma(beta, ar, tr); out.y = fma(beta, ai, ti); }
+        else { out.x = fma(-beta, ai, tr); out.y = fma(beta, ar, ti); }
+        y[row] = out;
+        if (FINAL) {
+            const V q = psi0[row];
+            const double qr = (double)q.x, qi = (double)q.y;
+            const double orr = (double)out.x, oi = (double)out.y;
+            dr = fma(qr, orr, fma(qi, oi, dr));
+            di = fma(qr, oi, fma(-qi, orr, di));
+        }
+    }
+    if (FINAL) {
+        const double2 r = block_sum(dr, di, red);
+        if (threadIdx.x == 0) p.partials[(int64_t)p.delta * p.nblk + blockIdx.x] = r;
+    }
+}
+
+// KPM sweep for B = 1: y = scale * (A x) - [!first] y; dots <x|x>, <y|x>.
+template <typename R, int OP, bool REALV, bool FIRST>
+__global__ void __launch_bounds__(kBlock) kpm_b1(KpmParams p)
+{
+    typedef typename V2<R>::T V;
+    __shared__ double2 red[kBlock / 32];
+    SweepParams sp;                     // operator fields for the shared helpers
+    sp.n = p.n; sp.nslices = p.nslices; sp.slice_off = p.slice_off; sp.cols = p.cols; sp.vals = p.vals;
+    sp.diag = p.diag; sp.l1 = p.l1; sp.l2 = p.l2; sp.t = p.t; sp.t_perp = p.t_perp;
+    const V *__restrict__ x = reinterpret_cast<const V *>(p.x);
+    V *y = reinterpret_cast<V *>(p.y);
+    const R *diag = reinterpret_cast<const R *>(p.diag);
+    const R sc = (R)p.scale;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double nn = 0.0, cr = 0.0, ci = 0.0;
+    for (int64_t s = warp; s < p.nslices; s += nwarps) {
+        const int64_t row = (s << 5) + lane;
+        const V xi = __ldg(x + row);
+        const R d = diag ? __ldg(diag + row) : (R)0;
+        R ar, ai;
+        V out;
+        if (FIRST) {
+            ar = d * xi.x; ai = d * xi.y;
+            if (OP == OP_SELL) sell_apply<R, REALV>(sp, s, lane, x, ar, ai);
+            else if (row < p.n) stencil_apply<R, OP>(sp, row, x, ar, ai);
+            out.x = sc * ar; out.y = sc * ai;
+        } else {
+            const V zz = y[row];
+            ar = fma(d, xi.x, -zz.x); ai = fma(d, xi.y, -zz.y);
+            if (OP == OP_SELL) sell_apply<R, REALV>(sp, s, lane, x, ar, ai);
+            else if (row < p.n) stencil_apply<R, OP>(sp, row, x, ar, ai);
+            out.x = ar; out.y = ai;
+        }
+        y[row] = out;
+        const double xr = (double)xi.x, xim = (double)xi.y;
+        const double orr = (double)out.x, oi = (double)out.y;
+        nn = fma(xr, xr, fma(xim, xim, nn));
+        // <y|x> = sum conj(y) x
+        cr = fma(orr, xr, fma(oi, xim, cr));
+        ci = fma(orr, xim, fma(-oi, xr, ci));
+    }
+    const double2 r0 = block_sum(nn, 0.0, red);
+    const double2 r1 = block_sum(cr, ci, red);
+    if (threadIdx.x == 0) {
+        double2 *base = p.partials + (int64_t)p.delta * 2 * p.nblk;
+        base[blockIdx.x] = r0;
+        base[p.nblk + blockIdx.x] = r1;
+    }
+}
+
+template <typename R, int OP, bool REALV>
+cudaError_t sweep_dispatch(SweepKind kind, bool a_imag, bool has_z, const SweepParams &p,
+                           int grid, cudaStream_t s)
+{
+    switch (kind) {
+    case SW_FIRST:
+        if (a_imag) sweep_b1<R, OP, REALV, B_REAL, true, false, false><<<grid, kBlock, 0, s>>>(p);
+        else sweep_b1<R, OP, REALV, B_IMAG, false, false, false><<<grid, kBlock, 0, s>>>(p);
+        break;
+    case SW_SECOND:
+        if (a_imag) sweep_b1<R, OP, REALV, B_ONE, true, false, false><<<grid, kBlock, 0, s>>>(p);
+        else sweep_b1<R, OP, REALV, B_ONE, false, false, false><<<grid, kBlock, 0, s>>>(p);
+        break;
+    case SW_MID:
+        if (a_imag) sweep_b1<R, OP, REALV, B_ONE, true, true, false><<<grid, kBlock, 0, s>>>(p);
+        else sweep_b1<R, OP, REALV, B_ONE, false, true, false><<<grid, kBlock, 0, s>>>(p);
+        break;
+    case SW_FINAL:
+        if (has_z) sweep_b1<R, OP, REALV, B_REAL, false, true, true><<<grid, kBlock, 0, s>>>(p);
+        else sweep_b1<R, OP, REALV, B_REAL, false, false, true><<<grid, kBlock, 0, s>>>(p);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename R, int OP, bool REALV>
+cudaError_t kpm_dispatch(const KpmParams &p, int grid, cudaStream_t s)
+{
+    if (p.first) kpm_b1<R, OP, REALV, true><<<grid, kBlock, 0, s>>>(p);
+    else kpm_b1<R, OP, REALV, false><<<grid, kBlock, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sweep(const SweepVariant &v, SweepKind kind, bool a_imag, bool has_z,
+                         const SweepParams &p, int grid, cudaStream_t s)
+{
+    if (v.states != 1) return cudaErrorInvalidValue;
+    if (v.precision == TBPM_FP64) {
+        if (v.op == OP_SELL)
+            return v.real_values ? sweep_dispatch<double, OP_SELL, true>(kind, a_imag, has_z, p, grid, s)
+                                 : sweep_dispatch<double, OP_SELL, false>(kind, a_imag, has_z, p, grid, s);
+        if (v.op == OP_STENCIL_MONO)
+            return sweep_dispatch<double, OP_STENCIL_MONO, true>(kind, a_imag, has_z, p, grid, s);
+        return sweep_dispatch<double, OP_STENCIL_BI, true>(kind, a_imag, has_z, p, grid, s);
+    }
+    if (v.op == OP_SELL)
+        return v.real_values ? sweep_dispatch<float, OP_SELL, true>(kind, a_imag, has_z, p, grid, s)
+                             : sweep_dispatch<float, OP_SELL, false>(kind, a_imag, has_z, p, grid, s);
+    if (v.op == OP_STENCIL_MONO)
+        return sweep_dispatch<float, OP_STENCIL_MONO, true>(kind, a_imag, has_z, p, grid, s);
+    return sweep_dispatch<float, OP_STENCIL_BI, true>(kind, a_imag, has_z, p, grid, s);
+}
+
+cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cudaStream_t s)
+{
+    if (v.states != 1) return cudaErrorInvalidValue;
+    if (v.precision == TBPM_FP64) {
+        if (v.op == OP_SELL)
+            return v.real_values ? kpm_dispatch<double, OP_SELL, true>(p, grid, s)
+                                 : kpm_dispatch<double, OP_SELL, false>(p, grid, s);
+        if (v.op == OP_STENCIL_MONO) return kpm_dispatch<double, OP_STENCIL_MONO, true>(p, grid, s);
+        return kpm_dispatch<double, OP_STENCIL_BI, true>(p, grid, s);
+    }
+    if (v.op == OP_SELL)
+        return v.real_values ? kpm_dispatch<float, OP_SELL, true>(p, grid, s)
+                             : kpm_dispatch<float, OP_SELL, false>(p, grid, s);
+    if (v.op == OP_STENCIL_MONO) return kpm_dispatch<float, OP_STENCIL_MONO, true>(p, grid, s);
+    return kpm_dispatch<float, OP_STENCIL_BI, true>(p, grid, s);
+}
+
+int sweep_grid(const SweepVariant &v, int num_sms)
+{
+    int per_sm = 0;
+    cudaError_t e;
+    if (v.precision == TBPM_FP64)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, sweep_b1<double, OP_SELL, true, B_ONE, false, true, false>, kBlock, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, sweep_b1<float, OP_SELL, true, B_ONE, false, true, false>, kBlock, 0);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 4;
+    return per_sm * num_sms;
+}
+
+}  // namespace tbpm

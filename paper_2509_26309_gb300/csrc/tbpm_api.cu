@@ -1,0 +1,850 @@
+// C ABI of libtbpm: argument and matrix validation, device layout, graph
+// capture of the sweep sequences, and the calls declared in tbpm.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tbpm_internal.cuh"
+
+using namespace tbpm;
+
+namespace {
+
+#define CU(call)                                                                 \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) {                                                 \
+            if (ctx) ctx->last_error = std::string(#call) + ": " + cudaGetErrorString(e_); \
+            return (e_ == cudaErrorMemoryAllocation) ? TBPM_ERR_OOM : TBPM_ERR_CUDA; \
+        }                                                                        \
+    } while (0)
+
+// ------------------------------------------------------------- host matrix
+
+// A validated Hermitian matrix: per row, off-diagonal entries sorted by column
+// with duplicates summed, and the real diagonal apart.
+struct HostMatrix {
+    int64_t n = 0;
+    std::vector<int64_t> rp;     // off-diagonal row pointers
+    std::vector<int32_t> col;
+    std::vector<double> re, im;
+    std::vector<double> diag;
+    double gershgorin = 0.0;
+    bool real_values = true;
+};
+
+int build_host_matrix(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                      bool check_hermitian, HostMatrix &m)
+{
+    if (row_ptr[0] != 0) return TBPM_ERR_CSR;
+    for (int64_t i = 0; i < n; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return TBPM_ERR_CSR;
+    const int64_t nnz = row_ptr[n];
+    for (int64_t p = 0; p < nnz; ++p)
+        if (col[p] < 0 || (int64_t)col[p] >= n) return TBPM_ERR_CSR;
+    for (int64_t p = 0; p < nnz; ++p)
+        if (!std::isfinite(val[2 * p]) || !std::isfinite(val[2 * p + 1])) return TBPM_ERR_ARG;
+    m.n = n;
+    m.rp.assign(n + 1, 0);
+    m.diag.assign(n, 0.0);
+    m.col.reserve(nnz);
+    m.re.reserve(nnz);
+    m.im.reserve(nnz);
+    std::vector<std::pair<int32_t, int64_t>> row;
+    std::vector<double> dim(n, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        row.clear();
+        for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) row.emplace_back(col[p], p);
+        std::sort(row.begin(), row.end());
+        double gs = 0.0;
+        size_t q = 0;
+        while (q < row.size()) {
+            const int32_t c = row[q].first;
+            double sr = 0.0, si = 0.0;
+            for (; q < row.size() && row[q].first == c; ++q) {
+                sr += val[2 * row[q].second];
+                si += val[2 * row[q].second + 1];
+            }
+            if (c == i) {
+                m.diag[i] = sr;
+                dim[i] = si;
+            } else {
+                m.col.push_back(c);
+                m.re.push_back(sr);
+                m.im.push_back(si);
+                if (si != 0.0) m.real_values = false;
+            }
+            gs += std::hypot(sr, si);
+        }
+        m.rp[i + 1] = (int64_t)m.col.size();
+        m.gershgorin = std::max(m.gershgorin, gs);
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (dim[i] != 0.0) return TBPM_ERR_NOT_HERMITIAN;
+    if (check_hermitian) {
+        for (int64_t i = 0; i < n; ++i) {
+            for (int64_t p = m.rp[i]; p < m.rp[i + 1]; ++p) {
+                const int32_t j = m.col[p];
+                const int32_t *b = m.col.data() + m.rp[j], *e = m.col.data() + m.rp[j + 1];
+                const int32_t *f = std::lower_bound(b, e, (int32_t)i);
+                double tr = 0.0, ti = 0.0;
+                if (f != e && *f == (int32_t)i) {
+                    const int64_t q = f - m.col.data();
+                    tr = m.re[q];
+                    ti = -m.im[q];
+                }
+                const double scale = std::hypot(m.re[p], m.im[p]) + std::hypot(tr, ti);
+                if (std::hypot(m.re[p] - tr, m.im[p] - ti) > 1e-13 * scale) return TBPM_ERR_NOT_HERMITIAN;
+            }
+        }
+    }
+    return TBPM_OK;
+}
+
+// The periodic lattice as a CSR matrix (tbpm_create_lattice with PATH_SELL).
+void lattice_to_host_matrix(const tbpm_lattice &lat, HostMatrix &m)
+{
+    const int per = lat.kind == TBPM_LATTICE_GRAPHENE ? 2 : 4;
+    const int64_t l1 = lat.l1, l2 = lat.l2, ncell = l1 * l2, n = ncell * per;
+    m.n = n;
+    m.rp.assign(n + 1, 0);
+    m.diag.assign(n, 0.0);
+    m.col.clear(); m.re.clear(); m.im.clear();
+    m.real_values = true;
+    std::vector<std::pair<int32_t, double>> row;
+    double g = 0.0;
+    for (int64_t c = 0; c < ncell; ++c) {
+        const int64_t m1 = c / l2, m2 = c % l2;
+        const int64_t cm1 = ((m1 + l1 - 1) % l1) * l2 + m2, cm2 = m1 * l2 + (m2 + l2 - 1) % l2;
+        const int64_t cp1 = ((m1 + 1) % l1) * l2 + m2, cp2 = m1 * l2 + (m2 + 1) % l2;
+        for (int o = 0; o < per; ++o) {
+            const int64_t i = c * per + o;
+            const int layer = o >> 1, s = o & 1;
+            row.clear();
+            if (s == 0) {
+                row.emplace_back((int32_t)(c * per + 2 * layer + 1), lat.t);
+                row.emplace_back((int32_t)(cm1 * per + 2 * layer + 1), lat.t);
+                row.emplace_back((int32_t)(cm2 * per + 2 * layer + 1), lat.t);
+            } else {
+                row.emplace_back((int32_t)(c * per + 2 * layer), lat.t);
+                row.emplace_back((int32_t)(cp1 * per + 2 * layer), lat.t);
+                row.emplace_back((int32_t)(cp2 * per + 2 * layer), lat.t);
+            }
+            if (per == 4 && o == 0) row.emplace_back((int32_t)(c * 4 + 3), lat.t_perp);
+            if (per == 4 && o == 3) row.emplace_back((int32_t)(c * 4), lat.t_perp);
+            std::sort(row.begin(), row.end());
+            double gs = 0.0;
+            for (auto &e : row) {
+                m.col.push_back(e.first);
+                m.re.push_back(e.second);
+                m.im.push_back(0.0);
+                gs += std::fabs(e.second);
+            }
+            m.rp[i + 1] = (int64_t)m.col.size();
+            m.diag[i] = lat.onsite ? lat.onsite[i] : 0.0;
+            g = std::max(g, gs + std::fabs(m.diag[i]));
+        }
+    }
+    m.gershgorin = g;
+}
+
+// ---------------------------------------------------------------- helpers
+
+bool is_device_ptr(const void *p, int device, bool *bad_device)
+{
+    cudaPointerAttributes a;
+    *bad_device = false;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        if (a.device != device) *bad_device = true;
+        return true;
+    }
+    return false;
+}
+
+size_t vec_bytes(int precision) { return precision == TBPM_FP64 ? 16 : 8; }
+
+int init_device(tbpm_ctx *ctx, const tbpm_opts &o)
+{
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        ctx->last_error = "no CUDA device";
+        return TBPM_ERR_NO_DEVICE;
+    }
+    int dev = o.device;
+    if (dev < 0) CU(cudaGetDevice(&dev));
+    if (dev >= count) return TBPM_ERR_ARG;
+    cudaDeviceProp prop;
+    CU(cudaGetDeviceProperties(&prop, dev));
+    if (!(prop.major == 10 && prop.minor == 3)) {
+        ctx->last_error = "libtbpm is built for sm_103a only";
+        return TBPM_ERR_NO_DEVICE;
+    }
+    CU(cudaSetDevice(dev));
+    ctx->device = dev;
+    ctx->num_sms = prop.multiProcessorCount;
+    // NULL selects the legacy default stream, which orders the library's work
+    // with every other blocking stream of the device (e.g. torch's default).
+    ctx->stream = o.stream ? (cudaStream_t)o.stream : cudaStreamLegacy;
+    ctx->own_stream = false;
+    CU(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    CU(cudaMalloc(&ctx->d_coef, sizeof(double2) * kMaxTerms));
+    CU(cudaMalloc(&ctx->d_K, sizeof(int)));
+    CU(cudaMalloc(&ctx->d_counter, sizeof(int) * 4));
+    return TBPM_OK;
+}
+
+template <typename R>
+void to_sell(const HostMatrix &m, int64_t n_pad, double s, bool real_values,
+             std::vector<int64_t> &off, std::vector<int32_t> &cols, std::vector<R> &vals,
+             std::vector<R> &diag, int &max_width)
+{
+    const int64_t nslices = n_pad / kSlice;
+    off.assign(nslices + 1, 0);
+    max_width = 0;
+    for (int64_t sl = 0; sl < nslices; ++sl) {
+        int w = 0;
+        for (int l = 0; l < kSlice; ++l) {
+            const int64_t r = sl * kSlice + l;
+            if (r < m.n) w = std::max<int>(w, (int)(m.rp[r + 1] - m.rp[r]));
+        }
+        max_width = std::max(max_width, w);
+        off[sl + 1] = off[sl] + (int64_t)w * kSlice;
+    }
+    const int64_t nent = off[nslices];
+    const int cw = real_values ? 1 : 2;
+    cols.assign(nent, 0);
+    vals.assign(nent * cw, (R)0);
+    diag.assign(n_pad, (R)0);
+    for (int64_t sl = 0; sl < nslices; ++sl) {
+        const int w = (int)((off[sl + 1] - off[sl]) / kSlice);
+        for (int l = 0; l < kSlice; ++l) {
+            const int64_t r = sl * kSlice + l;
+            const int64_t len = r < m.n ? m.rp[r + 1] - m.rp[r] : 0;
+            for (int j = 0; j < w; ++j) {
+                const int64_t e = off[sl] + (int64_t)j * kSlice + l;
+                if (j < len) {
+                    const int64_t p = m.rp[r] + j;
+                    cols[e] = m.col[p];
+                    if (real_values) vals[e] = (R)(s * m.re[p]);
+                    else { vals[2 * e] = (R)(s * m.re[p]); vals[2 * e + 1] = (R)(s * m.im[p]); }
+                } else {
+                    cols[e] = (int32_t)r;      // padding: own row, value 0
+                }
+            }
+            if (r < m.n) diag[r] = (R)(s * m.diag[r]);
+        }
+    }
+}
+
+template <typename T>
+int upload(tbpm_ctx *ctx, void **dst, const std::vector<T> &src)
+{
+    const size_t bytes = std::max<size_t>(src.size() * sizeof(T), 16);
+    CU(cudaMalloc(dst, bytes));
+    if (!src.empty()) CU(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return TBPM_OK;
+}
+
+int setup_sell(tbpm_ctx *ctx, const HostMatrix &m)
+{
+    const double s = 2.0 / ctx->rescale;                 // stored operator A = 2 H / rescale
+    std::vector<int64_t> off;
+    std::vector<int32_t> cols;
+    int rc;
+    ctx->sell.real_values = m.real_values;
+    if (ctx->precision == TBPM_FP64) {
+        std::vector<double> vals, diag;
+        to_sell<double>(m, ctx->n_pad, s, m.real_values, off, cols, vals, diag, ctx->sell.max_width);
+        if ((rc = upload(ctx, (void **)&ctx->sell.vals, vals))) return rc;
+        if ((rc = upload(ctx, (void **)&ctx->sell.diag, diag))) return rc;
+    } else {
+        std::vector<float> vals, diag;
+        to_sell<float>(m, ctx->n_pad, s, m.real_values, off, cols, vals, diag, ctx->sell.max_width);
+        if ((rc = upload(ctx, (void **)&ctx->sell.vals, vals))) return rc;
+        if ((rc = upload(ctx, (void **)&ctx->sell.diag, diag))) return rc;
+    }
+    ctx->sell.nslices = ctx->n_pad / kSlice;
+    ctx->sell.nent = off.back();
+    if ((rc = upload(ctx, (void **)&ctx->sell.slice_off, off))) return rc;
+    if ((rc = upload(ctx, (void **)&ctx->sell.cols, cols))) return rc;
+    ctx->nnz = (int64_t)m.col.size();
+    ctx->op = OP_SELL;
+    return TBPM_OK;
+}
+
+SweepVariant variant(const tbpm_ctx *ctx, int states)
+{
+    SweepVariant v;
+    v.precision = ctx->precision;
+    v.op = ctx->op;
+    v.real_values = ctx->op == OP_SELL ? ctx->sell.real_values : true;
+    v.states = states;
+    return v;
+}
+
+void fill_operator(const tbpm_ctx *ctx, SweepParams &p)
+{
+    memset(&p, 0, sizeof(p));
+    p.n = ctx->n;
+    p.nslices = ctx->n_pad / kSlice;
+    if (ctx->op == OP_SELL) {
+        p.slice_off = ctx->sell.slice_off;
+        p.cols = ctx->sell.cols;
+        p.vals = ctx->sell.vals;
+        p.diag = ctx->sell.diag;
+    } else {
+        p.diag = ctx->sten.onsite;
+        p.l1 = ctx->sten.l1;
+        p.l2 = ctx->sten.l2;
+        p.t = ctx->sten.t;
+        p.t_perp = ctx->sten.t_perp;
+    }
+    p.nblk = ctx->nblk;
+}
+
+void destroy_graphs(tbpm_ctx *ctx)
+{
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second);
+    ctx->graphs.clear();
+}
+
+// Work vectors for `states` interleaved states, partials, and per-call output.
+int ensure_work(tbpm_ctx *ctx, int states, size_t out_elems, size_t stage_doubles)
+{
+    if (states > ctx->cap_states) {
+        destroy_graphs(ctx);
+        cudaFree(ctx->d_psi); cudaFree(ctx->d_b0); cudaFree(ctx->d_b1); cudaFree(ctx->d_psi0);
+        cudaFree(ctx->d_partials);
+        ctx->d_psi = ctx->d_b0 = ctx->d_b1 = ctx->d_psi0 = nullptr;
+        ctx->d_partials = nullptr;
+        const size_t vb = vec_bytes(ctx->precision) * (size_t)ctx->n_pad * states;
+        CU(cudaMalloc(&ctx->d_psi, vb));
+        CU(cudaMalloc(&ctx->d_b0, vb));
+        CU(cudaMalloc(&ctx->d_b1, vb));
+        CU(cudaMalloc(&ctx->d_psi0, vb));
+        CU(cudaMemsetAsync(ctx->d_b0, 0, vb, ctx->stream));
+        CU(cudaMemsetAsync(ctx->d_b1, 0, vb, ctx->stream));
+        ctx->partials_cap = (size_t)(kChunk + 1) * 2 * ctx->nblk * states;
+        CU(cudaMalloc(&ctx->d_partials, ctx->partials_cap * sizeof(double2)));
+        ctx->cap_states = states;
+    }
+    if (out_elems > ctx->out_cap) {
+        destroy_graphs(ctx);
+        cudaFree(ctx->d_out);
+        ctx->d_out = nullptr;
+        CU(cudaMalloc(&ctx->d_out, out_elems * sizeof(double2)));
+        ctx->out_cap = out_elems;
+    }
+    if (stage_doubles > ctx->stage_cap) {
+        cudaFree(ctx->d_stage);
+        ctx->d_stage = nullptr;
+        CU(cudaMalloc(&ctx->d_stage, stage_doubles * sizeof(double)));
+        ctx->stage_cap = stage_doubles;
+    }
+    return TBPM_OK;
+}
+
+// Chebyshev coefficients for x = dt * rescale on the device; K read back once per x.
+int ensure_coeffs(tbpm_ctx *ctx, double x, int *K)
+{
+    if (ctx->K_cached > 0 && x == ctx->x_cached) {
+        *K = ctx->K_cached;
+        return TBPM_OK;
+    }
+    CU(launch_bessel(x, ctx->tol, ctx->d_coef, ctx->d_K, ctx->stream));
+    int k = -1;
+    CU(cudaMemcpyAsync(&k, ctx->d_K, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (k < 1) return TBPM_ERR_ARG;
+    ctx->x_cached = x;
+    ctx->K_cached = k;
+    *K = k;
+    return TBPM_OK;
+}
+
+// Enqueues `len` time steps (each K-1 sweeps) on stream s; step d of the
+// chunk writes dot partials to slot d, then one reduction stores
+// C(t_{base+1..base+len}) and the base counter advances.
+int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, cudaStream_t s, int64_t *launches)
+{
+    const SweepVariant v = variant(ctx, 1);
+    SweepParams p;
+    fill_operator(ctx, p);
+    p.coef = ctx->d_coef;
+    p.psi = ctx->d_psi;
+    p.psi0 = ctx->d_psi0;
+    p.partials = ctx->d_partials;
+    void *B[2] = {ctx->d_b0, ctx->d_b1};
+    const int grid = ctx->nblk;
+    for (int d = 0; d < len; ++d) {
+        // FIRST: b_{K-2} = c_{K-2} psi + c_{K-1} A psi  -> B[0]
+        p.x = ctx->d_psi; p.z = nullptr; p.y = B[0];
+        p.ia = K - 2; p.ib = -1; p.ic = K - 1; p.bscale = 1.0;
+        CU(launch_sweep(v, SW_FIRST, ((K - 2) & 1) != 0, false, p, grid, s));
+        ++*launches;
+        if (K >= 4) {
+            // SECOND: b_{K-3} = (c_{K-3} - c_{K-1}) psi + A b_{K-2}  -> B[1]
+            p.x = B[0]; p.z = nullptr; p.y = B[1];
+            p.ia = K - 3; p.ib = K - 1; p.ic = -1; p.bscale = 1.0;
+            CU(launch_sweep(v, SW_SECOND, ((K - 3) & 1) != 0, false, p, grid, s));
+            ++*launches;
+        }
+        for (int k = K - 4; k >= 1; --k) {
+            // b_k (in B[(K-2-k)&1], over b_{k+2}) = c_k psi + A b_{k+1} - b_{k+2}
+            p.x = B[(K - 3 - k) & 1];
+            p.y = B[(K - 2 - k) & 1];
+            p.z = p.y;
+            p.ia = k; p.ib = -1; p.ic = -1; p.bscale = 1.0;
+            CU(launch_sweep(v, SW_MID, (k & 1) != 0, true, p, grid, s));
+            ++*launches;
+        }
+        // FINAL: psi <- (c_0 - [K=3] c_2) psi + A b_1 / 2 - [K>=4] b_2, with <psi0|psi>
+        p.x = B[(K - 3) & 1];
+        p.z = K >= 4 ? B[(K - 4) & 1] : nullptr;
+        p.y = ctx->d_psi;
+        p.ia = 0; p.ib = K == 3 ? 2 : -1; p.ic = -1; p.bscale = 0.5;
+        p.delta = d;
+        CU(launch_sweep(v, SW_FINAL, false, K >= 4, p, grid, s));
+        ++*launches;
+    }
+    CU(launch_reduce(ctx->d_partials, len, 1, ctx->nblk, ctx->d_counter, 1, ctx->d_out, s));
+    CU(launch_advance(ctx->d_counter, len, s));
+    *launches += 2;
+    return TBPM_OK;
+}
+
+// Enqueues `len` KPM sweeps starting at an odd pass index (T_q in B0 for odd q).
+int enqueue_kpm_chunk(tbpm_ctx *ctx, int len, cudaStream_t s, int64_t *launches)
+{
+    const SweepVariant v = variant(ctx, 1);
+    SweepParams op;
+    fill_operator(ctx, op);
+    KpmParams p;
+    memset(&p, 0, sizeof(p));
+    p.n = op.n; p.nslices = op.nslices; p.slice_off = op.slice_off; p.cols = op.cols;
+    p.vals = op.vals; p.diag = op.diag; p.l1 = op.l1; p.l2 = op.l2; p.t = op.t; p.t_perp = op.t_perp;
+    p.partials = ctx->d_partials;
+    p.nblk = ctx->nblk;
+    p.scale = 1.0;
+    p.first = false;
+    for (int d = 0; d < len; ++d) {
+        // pass q (odd first): x = T_q, y = T_{q-1} -> T_{q+1}
+        p.x = (d & 1) == 0 ? ctx->d_b0 : ctx->d_psi;
+        p.y = (d & 1) == 0 ? ctx->d_psi : ctx->d_b0;
+        p.delta = d;
+        CU(launch_kpm(v, p, ctx->nblk, s));
+        ++*launches;
+    }
+    CU(launch_reduce(ctx->d_partials, len, 2, ctx->nblk, ctx->d_counter, 1, ctx->d_out, s));
+    CU(launch_advance(ctx->d_counter, len, s));
+    *launches += 2;
+    return TBPM_OK;
+}
+
+// Runs (and on first use captures) the graph of one chunk.
+int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches)
+{
+    const auto key = std::make_tuple(kind, len, K, 1);
+    auto it = ctx->graphs.find(key);
+    int64_t nl = 0;
+    if (it == ctx->graphs.end()) {
+        cudaGraph_t g;
+        CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = kind == 0 ? enqueue_dos_chunk(ctx, K, len, ctx->cap_stream, &nl)
+                           : enqueue_kpm_chunk(ctx, len, ctx->cap_stream, &nl);
+        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+        if (rc) return rc;
+        CU(e);
+        cudaGraphExec_t ex;
+        cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        CU(ei);
+        it = ctx->graphs.emplace(key, ex).first;
+    } else {
+        nl = kind == 0 ? (int64_t)len * (K - 1) + 2 : (int64_t)len + 2;
+    }
+    CU(cudaGraphLaunch(it->second, ctx->stream));
+    *launches += nl;
+    return TBPM_OK;
+}
+
+// Copies caller input (host or device, FP64 complex) for state j to a device
+// pointer usable by the load kernel.
+int stage_input(tbpm_ctx *ctx, const double *src, bool src_dev, size_t doubles, const double **out)
+{
+    if (src_dev) {
+        *out = src;
+        return TBPM_OK;
+    }
+    CU(cudaMemcpyAsync(ctx->d_stage, src, doubles * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    *out = ctx->d_stage;
+    return TBPM_OK;
+}
+
+int classify(tbpm_ctx *ctx, const void *p, bool *dev)
+{
+    bool bad = false;
+    *dev = is_device_ptr(p, ctx->device, &bad);
+    return bad ? TBPM_ERR_ARG : TBPM_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+int tbpm_default_opts(tbpm_opts *o)
+{
+    if (!o) return TBPM_ERR_ARG;
+    o->precision = TBPM_FP64;
+    o->path = TBPM_PATH_AUTO;
+    o->flags = 0;
+    o->device = -1;
+    o->stream = nullptr;
+    o->bessel_tol = 0.0;
+    return TBPM_OK;
+}
+
+const char *tbpm_strerror(int s)
+{
+    switch (s) {
+    case TBPM_OK: return "ok";
+    case TBPM_ERR_ARG: return "invalid argument";
+    case TBPM_ERR_CSR: return "malformed CSR matrix";
+    case TBPM_ERR_NOT_HERMITIAN: return "matrix is not Hermitian";
+    case TBPM_ERR_RESCALE: return "rescale below the Gershgorin bound of H";
+    case TBPM_ERR_OOM: return "out of memory";
+    case TBPM_ERR_CUDA: return "CUDA runtime error";
+    case TBPM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case TBPM_ERR_NO_DEVICE: return "no usable sm_103 GPU";
+    case TBPM_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+    }
+}
+
+static int check_opts(const tbpm_opts *in, tbpm_opts *o)
+{
+    tbpm_default_opts(o);
+    if (in) *o = *in;
+    if (o->precision != TBPM_FP64 && o->precision != TBPM_FP32) return TBPM_ERR_ARG;
+    if (o->path < TBPM_PATH_AUTO || o->path > TBPM_PATH_STENCIL) return TBPM_ERR_ARG;
+    if (o->flags & ~(unsigned)(TBPM_F_NO_HERMITIAN_CHECK | TBPM_F_FORCE_RESCALE | TBPM_F_RENORM))
+        return TBPM_ERR_ARG;
+    if (o->bessel_tol == 0.0) o->bessel_tol = 1e-12;
+    if (!(o->bessel_tol > 0.0 && o->bessel_tol < 1e-2)) return TBPM_ERR_ARG;
+    return TBPM_OK;
+}
+
+static int finish_create(tbpm_ctx *ctx, const tbpm_opts &o)
+{
+    int rc = init_device(ctx, o);
+    if (rc) return rc;
+    ctx->nblk = sweep_grid(variant(ctx, 1), ctx->num_sms);
+    return TBPM_OK;
+}
+
+int tbpm_create(tbpm_ctx **out, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                const double *val, double rescale, const tbpm_opts *opts)
+{
+    if (!out) return TBPM_ERR_ARG;
+    *out = nullptr;
+    tbpm_opts o;
+    int rc = check_opts(opts, &o);
+    if (rc) return rc;
+    if (n < 1 || n >= ((int64_t)1 << 31) - kSlice || !row_ptr) return TBPM_ERR_ARG;
+    if (row_ptr[n] > 0 && (!col || !val)) return TBPM_ERR_ARG;
+    if (!(rescale > 0.0) || !std::isfinite(rescale)) return TBPM_ERR_ARG;
+    if (o.path == TBPM_PATH_STENCIL) return TBPM_ERR_ARG;
+    HostMatrix m;
+    try {
+        rc = build_host_matrix(n, row_ptr, col, val, !(o.flags & TBPM_F_NO_HERMITIAN_CHECK), m);
+    } catch (const std::bad_alloc &) {
+        return TBPM_ERR_OOM;
+    }
+    if (rc) return rc;
+    if (m.gershgorin > rescale && !(o.flags & TBPM_F_FORCE_RESCALE)) return TBPM_ERR_RESCALE;
+    tbpm_ctx *ctx = new (std::nothrow) tbpm_ctx;
+    if (!ctx) return TBPM_ERR_OOM;
+    ctx->precision = o.precision;
+    ctx->path = TBPM_PATH_SELL;
+    ctx->flags = o.flags;
+    ctx->tol = o.bessel_tol;
+    ctx->n = n;
+    ctx->n_pad = (n + kSlice - 1) / kSlice * kSlice;
+    ctx->rescale = rescale;
+    ctx->gershgorin = m.gershgorin;
+    if ((rc = finish_create(ctx, o)) || (rc = setup_sell(ctx, m))) {
+        tbpm_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return TBPM_OK;
+}
+
+int tbpm_create_lattice(tbpm_ctx **out, const tbpm_lattice *lat, double rescale,
+                        const tbpm_opts *opts)
+{
+    if (!out || !lat) return TBPM_ERR_ARG;
+    *out = nullptr;
+    tbpm_opts o;
+    int rc = check_opts(opts, &o);
+    if (rc) return rc;
+    if (lat->kind != TBPM_LATTICE_GRAPHENE && lat->kind != TBPM_LATTICE_AB_BILAYER) return TBPM_ERR_ARG;
+    if (lat->l1 < 3 || lat->l2 < 3) return TBPM_ERR_ARG;
+    const int per = lat->kind == TBPM_LATTICE_GRAPHENE ? 2 : 4;
+    if (lat->l1 > ((int64_t)1 << 30) / lat->l2 / per) return TBPM_ERR_ARG;
+    const int64_t n = lat->l1 * lat->l2 * per;
+    if (!std::isfinite(lat->t) || !std::isfinite(lat->t_perp)) return TBPM_ERR_ARG;
+    if (!(rescale > 0.0) || !std::isfinite(rescale)) return TBPM_ERR_ARG;
+    double maxe = 0.0;
+    if (lat->onsite)
+        for (int64_t i = 0; i < n; ++i) {
+            if (!std::isfinite(lat->onsite[i])) return TBPM_ERR_ARG;
+            maxe = std::max(maxe, std::fabs(lat->onsite[i]));
+        }
+    const double gersh = 3.0 * std::fabs(lat->t) + (per == 4 ? std::fabs(lat->t_perp) : 0.0) + maxe;
+    if (gersh > rescale && !(o.flags & TBPM_F_FORCE_RESCALE)) return TBPM_ERR_RESCALE;
+    tbpm_ctx *ctx = new (std::nothrow) tbpm_ctx;
+    if (!ctx) return TBPM_ERR_OOM;
+    ctx->precision = o.precision;
+    ctx->flags = o.flags;
+    ctx->tol = o.bessel_tol;
+    ctx->n = n;
+    ctx->n_pad = (n + kSlice - 1) / kSlice * kSlice;
+    ctx->rescale = rescale;
+    ctx->gershgorin = gersh;
+    rc = finish_create(ctx, o);
+    if (!rc) {
+        if (o.path == TBPM_PATH_SELL) {
+            HostMatrix m;
+            try {
+                lattice_to_host_matrix(*lat, m);
+                ctx->path = TBPM_PATH_SELL;
+                rc = setup_sell(ctx, m);
+            } catch (const std::bad_alloc &) {
+                rc = TBPM_ERR_OOM;
+            }
+        } else {
+            ctx->path = TBPM_PATH_STENCIL;
+            ctx->op = per == 2 ? OP_STENCIL_MONO : OP_STENCIL_BI;
+            ctx->sten.kind = lat->kind;
+            ctx->sten.l1 = lat->l1;
+            ctx->sten.l2 = lat->l2;
+            const double s = 2.0 / rescale;
+            ctx->sten.t = s * lat->t;
+            ctx->sten.t_perp = s * lat->t_perp;
+            if (lat->onsite) {
+                if (ctx->precision == TBPM_FP64) {
+                    std::vector<double> e(ctx->n_pad, 0.0);
+                    for (int64_t i = 0; i < n; ++i) e[i] = s * lat->onsite[i];
+                    rc = upload(ctx, &ctx->sten.onsite, e);
+                } else {
+                    std::vector<float> e(ctx->n_pad, 0.0f);
+                    for (int64_t i = 0; i < n; ++i) e[i] = (float)(s * lat->onsite[i]);
+                    rc = upload(ctx, &ctx->sten.onsite, e);
+                }
+            }
+        }
+    }
+    if (rc) {
+        tbpm_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return TBPM_OK;
+}
+
+void tbpm_destroy(tbpm_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    destroy_graphs(ctx);
+    cudaFree(ctx->sell.slice_off); cudaFree(ctx->sell.cols); cudaFree(ctx->sell.vals);
+    cudaFree(ctx->sell.diag); cudaFree(ctx->sten.onsite);
+    cudaFree(ctx->d_coef); cudaFree(ctx->d_K); cudaFree(ctx->d_counter);
+    cudaFree(ctx->d_psi); cudaFree(ctx->d_b0); cudaFree(ctx->d_b1); cudaFree(ctx->d_psi0);
+    cudaFree(ctx->d_partials); cudaFree(ctx->d_out); cudaFree(ctx->d_stage); cudaFree(ctx->d_misc);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    cudaGetLastError();
+    delete ctx;
+}
+
+int tbpm_dos_corr(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, int n_steps,
+                  double *corr)
+{
+    if (!ctx || !psi0 || !corr || nstates < 1 || n_steps < 0) return TBPM_ERR_ARG;
+    if (!(dt != 0.0) || !std::isfinite(dt)) return TBPM_ERR_ARG;
+    const double x = dt * ctx->rescale;
+    if (!(std::fabs(x) <= 40.0)) return TBPM_ERR_ARG;
+    CU(cudaSetDevice(ctx->device));
+    bool in_dev, out_dev;
+    int rc;
+    if ((rc = classify(ctx, psi0, &in_dev)) || (rc = classify(ctx, corr, &out_dev))) return rc;
+    int K;
+    if ((rc = ensure_coeffs(ctx, x, &K))) return rc;
+    const int Ke = std::max(K, 3);
+    const int64_t n = ctx->n;
+    if ((rc = ensure_work(ctx, 1, (size_t)n_steps + 1, in_dev ? 0 : (size_t)2 * n))) return rc;
+    int64_t launches = 0;
+    for (int j = 0; j < nstates; ++j) {
+        const double *src;
+        if ((rc = stage_input(ctx, psi0 + (size_t)2 * n * j, in_dev, (size_t)2 * n, &src))) return rc;
+        CU(launch_load_states(ctx->precision, src, n, ctx->n_pad, 1, 0, 1, ctx->d_psi0, ctx->d_psi,
+                              ctx->stream));
+        CU(launch_dot(ctx->precision, ctx->d_psi0, ctx->d_psi0, ctx->n_pad, ctx->d_partials, ctx->nblk,
+                      ctx->stream));
+        CU(launch_reduce(ctx->d_partials, 1, 1, ctx->nblk, nullptr, 0, ctx->d_out, ctx->stream));
+        CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
+        launches += 3;
+        int done = 0;
+        while (done < n_steps) {
+            const int len = std::min(kChunk, n_steps - done);
+            if ((rc = run_chunk(ctx, 0, Ke, len, &launches))) return rc;
+            done += len;
+        }
+        double *dst = corr + (size_t)2 * (n_steps + 1) * j;
+        CU(cudaMemcpyAsync(dst, ctx->d_out, sizeof(double2) * (n_steps + 1),
+                           out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+        if (!in_dev && nstates > 1) CU(cudaStreamSynchronize(ctx->stream));  // staging reuse
+    }
+    if (!out_dev || !in_dev) CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaGetLastError());
+    ctx->last_K = Ke;
+    ctx->last_passes = (int64_t)nstates * n_steps * (Ke - 1);
+    ctx->last_launches = launches;
+    return TBPM_OK;
+}
+
+int kpm_moments(tbpm_ctx *ctx, const double *psi0, int nstates, int M, double *mu)
+{
+    if (!ctx || !psi0 || !mu || nstates < 1 || M < 1) return TBPM_ERR_ARG;
+    CU(cudaSetDevice(ctx->device));
+    bool in_dev, out_dev;
+    int rc;
+    if ((rc = classify(ctx, psi0, &in_dev)) || (rc = classify(ctx, mu, &out_dev))) return rc;
+    const int64_t n = ctx->n;
+    const int P = (M + 1) / 2 - 1;                        // sweeps after the first
+    const size_t ndots = 2 * (size_t)(P + 1);
+    if ((rc = ensure_work(ctx, 1, ndots + (size_t)M, in_dev ? 0 : (size_t)2 * n))) return rc;
+    const SweepVariant v = variant(ctx, 1);
+    int64_t launches = 0;
+    for (int j = 0; j < nstates; ++j) {
+        const double *src;
+        if ((rc = stage_input(ctx, psi0 + (size_t)2 * n * j, in_dev, (size_t)2 * n, &src))) return rc;
+        CU(launch_load_states(ctx->precision, src, n, ctx->n_pad, 1, 0, 1, ctx->d_psi0, ctx->d_psi,
+                              ctx->stream));
+        // first sweep: T_1 = A T_0 / 2 into B0, dots (<T_0|T_0>, <T_1|T_0>) -> dots[0..1]
+        SweepParams op;
+        fill_operator(ctx, op);
+        KpmParams p;
+        memset(&p, 0, sizeof(p));
+        p.n = op.n; p.nslices = op.nslices; p.slice_off = op.slice_off; p.cols = op.cols;
+        p.vals = op.vals; p.diag = op.diag; p.l1 = op.l1; p.l2 = op.l2; p.t = op.t; p.t_perp = op.t_perp;
+        p.x = ctx->d_psi; p.y = ctx->d_b0; p.scale = 0.5; p.first = true;
+        p.partials = ctx->d_partials; p.delta = 0; p.nblk = ctx->nblk;
+        CU(launch_kpm(v, p, ctx->nblk, ctx->stream));
+        CU(launch_reduce(ctx->d_partials, 1, 2, ctx->nblk, nullptr, 0, ctx->d_out, ctx->stream));
+        CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
+        launches += 3;
+        int done = 0;
+        while (done < P) {
+            const int len = std::min(kChunk, P - done);
+            if ((rc = run_chunk(ctx, 1, 0, len, &launches))) return rc;
+            done += len;
+        }
+        double2 *dmu = ctx->d_out + ndots;
+        CU(launch_kpm_finalize(ctx->d_out, M, 1, dmu, ctx->stream));
+        ++launches;
+        double *dst = mu + (size_t)2 * M * j;
+        CU(cudaMemcpyAsync(dst, dmu, sizeof(double2) * M,
+                           out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+        if (!in_dev && nstates > 1) CU(cudaStreamSynchronize(ctx->stream));
+    }
+    if (!out_dev || !in_dev) CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaGetLastError());
+    ctx->last_passes = (int64_t)nstates * (P + 1);
+    ctx->last_launches = launches;
+    return TBPM_OK;
+}
+
+int tbpm_dos_from_corr(tbpm_ctx *ctx, const double *corr, int n_steps, double dt,
+                       double *energies, double *dos)
+{
+    if (!ctx || !corr || !energies || !dos || n_steps < 1) return TBPM_ERR_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt) || n_steps > (1 << 28)) return TBPM_ERR_ARG;
+    CU(cudaSetDevice(ctx->device));
+    bool in_dev, e_dev, d_dev;
+    int rc;
+    if ((rc = classify(ctx, corr, &in_dev)) || (rc = classify(ctx, energies, &e_dev)) ||
+        (rc = classify(ctx, dos, &d_dev)))
+        return rc;
+    const size_t nc = (size_t)n_steps + 1, ne = 2 * (size_t)n_steps;
+    if ((rc = ensure_work(ctx, 1, 0, 2 * nc + 2 * ne))) return rc;
+    const double2 *c = reinterpret_cast<const double2 *>(corr);
+    if (!in_dev) {
+        CU(cudaMemcpyAsync(ctx->d_stage, corr, nc * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+        c = reinterpret_cast<const double2 *>(ctx->d_stage);
+    }
+    double *de = e_dev ? energies : ctx->d_stage + 2 * nc;
+    double *dd = d_dev ? dos : ctx->d_stage + 2 * nc + ne;
+    CU(launch_dos_hann(c, n_steps, dt, de, dd, ctx->stream));
+    if (!e_dev) CU(cudaMemcpyAsync(energies, de, ne * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (!d_dev) CU(cudaMemcpyAsync(dos, dd, ne * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (!in_dev || !e_dev || !d_dev) CU(cudaStreamSynchronize(ctx->stream));
+    ctx->last_launches = 1;
+    return TBPM_OK;
+}
+
+int kpm_dos_jackson(tbpm_ctx *ctx, const double *mu, int M, int n_e, double *energies,
+                    double *rho_out)
+{
+    if (!ctx || !mu || !energies || !rho_out || M < 1 || n_e < 1) return TBPM_ERR_ARG;
+    CU(cudaSetDevice(ctx->device));
+    bool in_dev, e_dev, r_dev;
+    int rc;
+    if ((rc = classify(ctx, mu, &in_dev)) || (rc = classify(ctx, energies, &e_dev)) ||
+        (rc = classify(ctx, rho_out, &r_dev)))
+        return rc;
+    if ((rc = ensure_work(ctx, 1, 0, 2 * (size_t)M + 2 * (size_t)n_e))) return rc;
+    const double2 *m = reinterpret_cast<const double2 *>(mu);
+    if (!in_dev) {
+        CU(cudaMemcpyAsync(ctx->d_stage, mu, M * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+        m = reinterpret_cast<const double2 *>(ctx->d_stage);
+    }
+    double *de = e_dev ? energies : ctx->d_stage + 2 * (size_t)M;
+    double *dr = r_dev ? rho_out : ctx->d_stage + 2 * (size_t)M + n_e;
+    CU(launch_kpm_dos(m, M, n_e, ctx->rescale, de, dr, ctx->stream));
+    if (!e_dev) CU(cudaMemcpyAsync(energies, de, n_e * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (!r_dev) CU(cudaMemcpyAsync(rho_out, dr, n_e * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (!in_dev || !e_dev || !r_dev) CU(cudaStreamSynchronize(ctx->stream));
+    ctx->last_launches = 1;
+    return TBPM_OK;
+}
+
+int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info)
+{
+    if (!ctx || !info) return TBPM_ERR_ARG;
+    info->n = ctx->n;
+    info->nnz = ctx->op == OP_SELL ? ctx->nnz : 0;
+    info->path = ctx->path;
+    info->precision = ctx->precision;
+    info->real_values = ctx->op == OP_SELL ? (int)ctx->sell.real_values : 1;
+    info->num_terms = ctx->last_K;
+    info->passes = ctx->last_passes;
+    info->kernel_launches = ctx->last_launches;
+    info->gershgorin = ctx->gershgorin;
+    info->rescale = ctx->rescale;
+    return TBPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,200 @@
+// Internal declarations of libtbpm: device layouts, kernel parameter blocks,
+// and the launch entry points each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "tbpm.h"
+
+namespace tbpm {
+
+constexpr int kSlice = 32;          // SELL slice height = warp width
+constexpr int kBlock = 256;         // threads per block of the sweep kernels
+constexpr int kMaxTerms = 128;      // Chebyshev coefficients generated on device
+constexpr int kChunk = 16;          // time steps (or KPM passes) per captured graph
+constexpr int kMaxBlockStates = 16; // states advanced together (FP32 batched)
+
+// ---------------------------------------------------------------- layouts
+
+// Sliced ELLPACK with slice height 32 and no row sorting (the lattice order of
+// the rows is kept for the locality of the gathers). Slice s covers rows
+// [32 s, 32 s + 32); its entry (lane, j) sits at slice_off[s] + 32 j + lane.
+// Padding entries point at their own row with value 0. The diagonal is kept
+// apart as a real array (a Hermitian matrix has a real diagonal).
+struct Sell {
+    int64_t nslices = 0;
+    int64_t nent = 0;             // stored off-diagonal slots incl. padding
+    int64_t *slice_off = nullptr; // int64[nslices + 1]
+    int32_t *cols = nullptr;      // int32[nent]
+    void *vals = nullptr;         // real: R[nent]; complex: R2[nent]
+    void *diag = nullptr;         // R[n_pad]
+    bool real_values = true;
+    int max_width = 0;
+};
+
+// Periodic graphene / AB-bilayer stencil (matrix-free H v).
+struct Stencil {
+    int kind = TBPM_LATTICE_GRAPHENE;
+    int64_t l1 = 0, l2 = 0;
+    double t = 0, t_perp = 0;
+    void *onsite = nullptr;       // R[n_pad] or nullptr
+};
+
+// Parameters of one Clenshaw sweep (see cheb_sweep.cu for the recurrence).
+struct SweepParams {
+    // operator
+    int64_t n;                    // rows holding orbitals (rows >= n are padding)
+    int64_t nslices;              // SELL slices, or stencil cells / 32 rounded up
+    const int64_t *slice_off;
+    const int32_t *cols;
+    const void *vals;
+    const void *diag;
+    int64_t l1, l2;               // stencil geometry
+    double t, t_perp;
+    // vectors (all padded to n_pad rows, B states interleaved per row)
+    const void *x;                // gathered operand
+    const void *psi;              // current state psi(t_n)
+    void *y;                      // output (may alias z, or psi in the final sweep)
+    const void *z;                // b_{k+2} (subtracted), or nullptr
+    // coefficients, on device: a = c[ia] - (ib >= 0 ? c[ib] : 0),
+    // beta = bscale * (ic >= 0 ? c[ic] : 1)
+    const double2 *coef;
+    int ia, ib, ic;
+    double bscale;
+    // final sweep: <psi0|y> partials, one per block per state, slot `delta`
+    const void *psi0;
+    double2 *partials;
+    int delta;
+    int nblk;
+};
+
+// KPM sweep: T_{m+1} = 2 H~ T_m - T_{m-1} with <T_m|T_m> and <T_{m+1}|T_m>.
+struct KpmParams {
+    int64_t n;
+    int64_t nslices;
+    const int64_t *slice_off;
+    const int32_t *cols;
+    const void *vals;
+    const void *diag;
+    int64_t l1, l2;
+    double t, t_perp;
+    const void *x;                // T_m
+    void *y;                      // in: T_{m-1}, out: T_{m+1} (nullptr z => first)
+    double scale;                 // 2/rescale, or 1/rescale for T_1 = H~ T_0
+    bool first;                   // y = scale * H T_0 (no subtraction)
+    double2 *partials;            // [slot][2][nblk][B]
+    int delta;
+    int nblk;
+};
+
+enum OpKind { OP_SELL = 0, OP_STENCIL_MONO = 1, OP_STENCIL_BI = 2 };
+
+// Signature of a device kernel variant chosen on the host.
+struct SweepVariant {
+    int precision;                // TBPM_FP64 | TBPM_FP32
+    int op;                       // OpKind
+    bool real_values;
+    int states;                   // B: 1 or 16
+};
+
+// ---------------------------------------------------------------- context
+
+}  // namespace tbpm
+
+struct tbpm_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;   // private stream used for graph capture
+    int precision = TBPM_FP64;
+    int path = TBPM_PATH_SELL;
+    unsigned flags = 0;
+    double tol = 1e-12;
+    int64_t n = 0, n_pad = 0;
+    double rescale = 1.0, gershgorin = 0.0;
+    int op = tbpm::OP_SELL;
+    tbpm::Sell sell;
+    tbpm::Stencil sten;
+    int64_t nnz = 0;
+    // sweep grid (fixed per context so the dot partials are deterministic)
+    int nblk = 0;
+    // coefficients
+    double2 *d_coef = nullptr;       // [kMaxTerms]
+    int *d_K = nullptr;
+    double x_cached = 0.0;
+    int K_cached = -1;
+    // work vectors, sized for `cap_states` interleaved states
+    int cap_states = 0;
+    void *d_psi = nullptr, *d_b0 = nullptr, *d_b1 = nullptr, *d_psi0 = nullptr;
+    double2 *d_partials = nullptr;   // [(kChunk+1) * 2 * nblk * B]
+    size_t partials_cap = 0;
+    double2 *d_out = nullptr;        // per-call device results
+    size_t out_cap = 0;
+    double *d_stage = nullptr;       // FP64 staging for host inputs
+    size_t stage_cap = 0;
+    int *d_counter = nullptr;        // chunk base counter for graphs
+    double *d_misc = nullptr;        // small scratch (norms, moment bases)
+    // cached executable graphs keyed by (kind, len, K, states)
+    std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
+    // counters of the last call
+    int last_K = 0;
+    int64_t last_passes = 0;
+    int64_t last_launches = 0;
+    std::string last_error;
+};
+
+namespace tbpm {
+
+// ------------------------------------------------------------ launchers
+// Each returns cudaSuccess or the launch error.
+
+// Chebyshev coefficients c_k, k < kMaxTerms, and K into d_K (bessel.cu).
+cudaError_t launch_bessel(double x, double tol, double2 *d_coef, int *d_K, cudaStream_t s);
+
+// One Clenshaw sweep of the given kind (cheb_sweep.cu).
+enum SweepKind { SW_FIRST = 0, SW_SECOND = 1, SW_MID = 2, SW_FINAL = 3 };
+cudaError_t launch_sweep(const SweepVariant &v, SweepKind kind, bool a_imag, bool has_z,
+                         const SweepParams &p, int grid, cudaStream_t s);
+
+// KPM sweep (cheb_sweep.cu).
+cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cudaStream_t s);
+
+// <a|b> = sum_i conj(a_i) b_i as per-block partials over `rows` rows of one
+// state, written to partials[0..grid) (aux.cu).
+cudaError_t launch_dot(int precision, const void *a, const void *b, int64_t rows,
+                       double2 *partials, int grid, cudaStream_t s);
+
+// Deterministic reduction of per-block partials laid out [nslot][nterm][nblk]:
+//   out[(base + offset + d) * nterm + q] = sum_b partials[(d * nterm + q) * nblk + b]
+// with base = *counter (0 when counter is nullptr) (aux.cu).
+cudaError_t launch_reduce(const double2 *partials, int nslot, int nterm, int nblk,
+                          const int *counter, int offset, double2 *out, cudaStream_t s);
+cudaError_t launch_advance(int *counter, int by, cudaStream_t s);
+
+// State layout conversion: src FP64 complex state-major [nstates][n] ->
+// dst (precision) interleaved [n_pad][B] for states [j0, j0 + B) (aux.cu).
+cudaError_t launch_load_states(int precision, const double *src, int64_t n, int64_t n_pad,
+                               int nstates_src, int j0, int B, void *dst0, void *dst1,
+                               cudaStream_t s);
+
+// KPM moments from the reduced dot products (aux.cu).
+cudaError_t launch_kpm_finalize(const double2 *dots, int M, int states, double2 *mu,
+                                cudaStream_t s);
+
+// DOS transforms (dos.cu).
+cudaError_t launch_dos_hann(const double2 *corr, int n_steps, double dt, double *energies,
+                            double *dos, cudaStream_t s);
+cudaError_t launch_kpm_dos(const double2 *mu, int M, int n_e, double rescale, double *energies,
+                           double *rho, cudaStream_t s);
+
+// Block count of the sweep kernels at full occupancy (cheb_sweep.cu).
+int sweep_grid(const SweepVariant &v, int num_sms);
+
+}  // namespace tbpm

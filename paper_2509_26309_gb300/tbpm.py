@@ -1,0 +1,267 @@
+"""ctypes binding of libtbpm.so: the C calls of include/tbpm.h under the same names.
+
+Argument marshalling only: every step of the propagation runs in the CUDA
+library. Arrays may be numpy arrays (host memory) or torch tensors (host or
+the context's GPU); complex arrays are complex128 (two interleaved doubles).
+Outputs follow the input: a CUDA tensor in gives CUDA tensors out (the call is
+then asynchronous on the context's stream), anything else gives numpy arrays.
+If the library cannot be loaded the import fails; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB, build as _build
+
+TBPM_OK = 0
+TBPM_ERR_ARG = -1
+TBPM_ERR_CSR = -2
+TBPM_ERR_NOT_HERMITIAN = -3
+TBPM_ERR_RESCALE = -4
+TBPM_ERR_OOM = -5
+TBPM_ERR_CUDA = -6
+TBPM_ERR_TIMEOUT = -7
+TBPM_ERR_NO_DEVICE = -8
+TBPM_ERR_UNSUPPORTED = -9
+
+TBPM_FP64 = 0
+TBPM_FP32 = 1
+TBPM_PATH_AUTO = 0
+TBPM_PATH_SELL = 1
+TBPM_PATH_STENCIL = 2
+TBPM_F_NO_HERMITIAN_CHECK = 0x1
+TBPM_F_FORCE_RESCALE = 0x2
+TBPM_F_RENORM = 0x4
+TBPM_LATTICE_GRAPHENE = 0
+TBPM_LATTICE_AB_BILAYER = 1
+
+
+class tbpm_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("path", C.c_int), ("flags", C.c_uint),
+                ("device", C.c_int), ("stream", C.c_void_p), ("bessel_tol", C.c_double)]
+
+
+class tbpm_lattice(C.Structure):
+    _fields_ = [("kind", C.c_int), ("l1", C.c_int64), ("l2", C.c_int64), ("t", C.c_double),
+                ("t_perp", C.c_double), ("onsite", C.c_void_p)]
+
+
+class tbpm_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("path", C.c_int), ("precision", C.c_int),
+                ("real_values", C.c_int), ("num_terms", C.c_int), ("passes", C.c_int64),
+                ("kernel_launches", C.c_int64), ("gershgorin", C.c_double), ("rescale", C.c_double)]
+
+
+class TbpmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {tbpm_strerror(status)} ({status})")
+        self.status = status
+
+
+_lib = None
+
+# name: (restype, argtypes) for every entry point the header declares
+SIGNATURES = {
+    "tbpm_default_opts": (C.c_int, [C.c_void_p]),
+    "tbpm_create": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.c_double, C.c_void_p]),
+    "tbpm_create_lattice": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
+    "tbpm_destroy": (None, [C.c_void_p]),
+    "tbpm_dos_corr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p]),
+    "kpm_moments": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "tbpm_dos_from_corr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p,
+                                     C.c_void_p]),
+    "kpm_dos_jackson": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "tbpm_get_info": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tbpm_strerror": (C.c_char_p, [C.c_int]),
+}
+
+
+def lib(build_if_missing: bool = True) -> C.CDLL:
+    """The loaded libtbpm.so (built in-tree on first use when missing)."""
+    global _lib
+    if _lib is None:
+        path = _build() if build_if_missing else LIB
+        if not os.path.exists(path):
+            raise ImportError(f"libtbpm.so not found at {path}")
+        l = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(l, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = l
+    return _lib
+
+
+def tbpm_strerror(status: int) -> str:
+    return lib().tbpm_strerror(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != TBPM_OK:
+        raise TbpmError(status, what)
+
+
+# ------------------------------------------------------------ marshalling
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    """Address of a contiguous numpy array or torch tensor."""
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _complex_in(a, n: int):
+    """Returns (array, nstates, on_cuda) for a complex128 (n,) or (nstates, n) input."""
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.complex128:
+            raise TypeError("psi0 must be complex128")
+        a = a.contiguous()
+        on_cuda = a.is_cuda
+    else:
+        a = np.ascontiguousarray(a, dtype=np.complex128)
+        on_cuda = False
+    if a.ndim == 1:
+        ns = 1
+    elif a.ndim == 2:
+        ns = a.shape[0]
+    else:
+        raise ValueError("psi0 must be 1-D or 2-D (nstates, n)")
+    if a.shape[-1] != n:
+        raise ValueError(f"psi0 has {a.shape[-1]} orbitals, the context {n}")
+    return a, ns, on_cuda
+
+
+def _alloc(shape, dtype, like_cuda: bool, device=None):
+    if like_cuda:
+        import torch
+        td = {np.complex128: torch.complex128, np.float64: torch.float64}[dtype]
+        return torch.empty(shape, dtype=td, device=device)
+    return np.empty(shape, dtype=dtype)
+
+
+class Ctx:
+    """An owned tbpm_ctx handle; freed by tbpm_destroy or when collected."""
+
+    def __init__(self, handle: C.c_void_p, n: int, device: int):
+        self.handle = handle
+        self.n = n
+        self.device = device
+
+    def __del__(self):
+        try:
+            tbpm_destroy(self)
+        except Exception:
+            pass
+
+
+def make_opts(precision: int = TBPM_FP64, path: int = TBPM_PATH_AUTO, flags: int = 0,
+              device: int = -1, stream=None, bessel_tol: float = 0.0) -> tbpm_opts:
+    o = tbpm_opts()
+    _check(lib().tbpm_default_opts(C.byref(o)), "tbpm_default_opts")
+    o.precision, o.path, o.flags, o.device = precision, path, flags, device
+    o.stream = stream if stream is None else C.c_void_p(int(stream))
+    o.bessel_tol = bessel_tol
+    return o
+
+
+def tbpm_create(n: int, row_ptr, col, val, rescale: float, opts: tbpm_opts | None = None) -> Ctx:
+    """Solver context for a CSR Hamiltonian (host arrays: int64, int32, complex128)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.complex128)
+    if row_ptr.shape != (n + 1,):
+        raise ValueError("row_ptr must have n + 1 entries")
+    h = C.c_void_p()
+    _check(lib().tbpm_create(C.byref(h), int(n), _ptr(row_ptr), _ptr(col), _ptr(val),
+                             float(rescale), C.byref(opts) if opts is not None else None),
+           "tbpm_create")
+    return Ctx(h, int(n), opts.device if opts is not None else -1)
+
+
+def tbpm_create_lattice(kind: int, l1: int, l2: int, t: float, t_perp: float = 0.0,
+                        onsite=None, rescale: float = 9.0, opts: tbpm_opts | None = None) -> Ctx:
+    """Solver context for a periodic graphene (kind 0) or AB-bilayer (kind 1) supercell."""
+    per = 2 if kind == TBPM_LATTICE_GRAPHENE else 4
+    n = per * l1 * l2
+    lat = tbpm_lattice(kind, l1, l2, t, t_perp, None)
+    if onsite is not None:
+        onsite = np.ascontiguousarray(onsite, dtype=np.float64)
+        if onsite.shape != (n,):
+            raise ValueError("onsite must have one entry per orbital")
+        lat.onsite = onsite.ctypes.data_as(C.c_void_p)
+    h = C.c_void_p()
+    _check(lib().tbpm_create_lattice(C.byref(h), C.byref(lat), float(rescale),
+                                     C.byref(opts) if opts is not None else None),
+           "tbpm_create_lattice")
+    return Ctx(h, n, opts.device if opts is not None else -1)
+
+
+def tbpm_destroy(ctx: Ctx) -> None:
+    if ctx.handle:
+        lib().tbpm_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def tbpm_dos_corr(ctx: Ctx, psi0, dt: float, n_steps: int, out=None):
+    """C(t_n) = <psi0|psi(t_n)>, n = 0..n_steps: shape (n_steps+1,) or (nstates, n_steps+1)."""
+    a, ns, cuda = _complex_in(psi0, ctx.n)
+    if out is None:
+        out = _alloc((ns, n_steps + 1), np.complex128, cuda, a.device if cuda else None)
+    _check(lib().tbpm_dos_corr(ctx.handle, _ptr(a), ns, float(dt), int(n_steps), _ptr(out)),
+           "tbpm_dos_corr")
+    return out[0] if (a.ndim == 1 and out.shape[0] == 1) else out
+
+
+def kpm_moments(ctx: Ctx, psi0, M: int, out=None):
+    """mu_m = <psi0|T_m(H~)|psi0>, m = 0..M-1 (complex): shape (M,) or (nstates, M)."""
+    a, ns, cuda = _complex_in(psi0, ctx.n)
+    if out is None:
+        out = _alloc((ns, M), np.complex128, cuda, a.device if cuda else None)
+    _check(lib().kpm_moments(ctx.handle, _ptr(a), ns, int(M), _ptr(out)), "kpm_moments")
+    return out[0] if (a.ndim == 1 and out.shape[0] == 1) else out
+
+
+def tbpm_dos_from_corr(ctx: Ctx, corr, dt: float):
+    """(energies[2N], dos[2N]) of the Hann-windowed transform of corr[N+1]."""
+    cuda = _is_torch(corr) and corr.is_cuda
+    if not _is_torch(corr):
+        corr = np.ascontiguousarray(corr, dtype=np.complex128)
+    n_steps = corr.shape[-1] - 1
+    dev = corr.device if cuda else None
+    e = _alloc((2 * n_steps,), np.float64, cuda, dev)
+    d = _alloc((2 * n_steps,), np.float64, cuda, dev)
+    _check(lib().tbpm_dos_from_corr(ctx.handle, _ptr(corr), int(n_steps), float(dt), _ptr(e), _ptr(d)),
+           "tbpm_dos_from_corr")
+    return e, d
+
+
+def kpm_dos_jackson(ctx: Ctx, mu, n_e: int):
+    """(energies[n_e], rho[n_e]) of the Jackson-kernel KPM DOS on Chebyshev nodes."""
+    cuda = _is_torch(mu) and mu.is_cuda
+    if not _is_torch(mu):
+        mu = np.ascontiguousarray(mu, dtype=np.complex128)
+    dev = mu.device if cuda else None
+    e = _alloc((n_e,), np.float64, cuda, dev)
+    r = _alloc((n_e,), np.float64, cuda, dev)
+    _check(lib().kpm_dos_jackson(ctx.handle, _ptr(mu), int(mu.shape[-1]), int(n_e), _ptr(e), _ptr(r)),
+           "kpm_dos_jackson")
+    return e, r
+
+
+def tbpm_get_info(ctx: Ctx) -> dict:
+    info = tbpm_info()
+    _check(lib().tbpm_get_info(ctx.handle, C.byref(info)), "tbpm_get_info")
+    return {name: getattr(info, name) for name, _ in tbpm_info._fields_}

@@ -1,0 +1,174 @@
+"""CUDA path vs the FP64 oracle on the same seeded inputs, through the C ABI.
+
+Tolerance: |dC| <= 1e-10 and |dmu| <= 1e-10 for the FP64 path. Both sides use
+the same truncated series; what differs is the summation (Clenshaw on the GPU,
+forward recurrence in the oracle), the Bessel method (Miller's recurrence vs
+the power series) and the rounding order of the sums, each of order 1e-16 per
+operation, far below 1e-10 over 10^4 sweeps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import tbpm_inputs as ti
+import paper_2509_26309_gb300 as tb
+
+pytestmark = pytest.mark.gpu
+DT = math.pi / 9
+TOL = 1e-10
+
+
+def create(h, rescale=9.0, **kw):
+    return tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, rescale, tb.make_opts(**kw))
+
+
+def test_config1_pristine_64x64_full(orc):
+    """64x64 pristine graphene, psi0 seed 0, 1024 steps of pi/9, K = 18."""
+    h = ti.graphene_csr(64, 64)
+    psi0 = ti.random_phase_state(h.n, 0)
+    ctx = create(h)
+    c = tb.tbpm_dos_corr(ctx, psi0, DT, 1024)
+    ref = orc.dos_corr(h, 9.0, psi0, DT, 1024)
+    assert tb.tbpm_get_info(ctx)["num_terms"] == 18
+    assert np.max(np.abs(c - ref)) <= TOL
+    c2 = tb.tbpm_dos_corr(ctx, psi0, DT, 1024)
+    assert np.array_equal(c, c2)                      # deterministic reductions
+
+
+@pytest.mark.parametrize("n,steps", [(1, 5), (31, 40), (1000, 200), (4133, 64)])
+def test_ragged_complex_hermitian(orc, n, steps):
+    h = ti.random_hermitian_csr(n, 3, seed=n, scale=1.5) if n > 1 else ti.graphene_csr(1, 1)
+    rescale = 1.05 * ti.gershgorin_bound(h) if n > 1 else 9.0
+    dt = 2.7 / rescale
+    psi0 = ti.random_phase_state(h.n, 3)
+    ctx = create(h, rescale)
+    assert tb.tbpm_get_info(ctx)["real_values"] == (0 if n > 1 else 1)
+    c = tb.tbpm_dos_corr(ctx, psi0, dt, steps)
+    ref = orc.dos_corr(h, rescale, psi0, dt, steps)
+    assert np.max(np.abs(c - ref)) <= TOL
+
+
+def test_bilayer_disorder_and_phases(orc):
+    h = ti.bilayer_csr(20, 17, onsite=ti.anderson_onsite(4 * 340, 1.5, 9))
+    psi0 = ti.random_phase_state(h.n, 1)
+    rescale = 1.02 * ti.gershgorin_bound(h)
+    ctx = create(h, rescale)
+    c = tb.tbpm_dos_corr(ctx, psi0, math.pi / rescale, 300)
+    ref = orc.dos_corr(h, rescale, psi0, math.pi / rescale, 300)
+    assert np.max(np.abs(c - ref)) <= TOL
+    hp = ti.graphene_csr(13, 11, onsite=ti.anderson_onsite(286, 1.0, 2), bond_phases=[0.7, -0.4, 1.9])
+    ctx = create(hp)
+    psi0 = ti.random_phase_state(hp.n, 2)
+    c = tb.tbpm_dos_corr(ctx, psi0, DT, 256)
+    assert np.max(np.abs(c - orc.dos_corr(hp, 9.0, psi0, DT, 256))) <= TOL
+
+
+@pytest.mark.parametrize("dt", [1e-7, 1e-5, 2e-4, 2e-3, 0.05, -DT, 2 * DT, 30.0 / 9.0])
+def test_term_counts_and_signs(orc, dt):
+    """Small x gives K = 3 or 4 (the short Clenshaw forms); negative dt runs backwards."""
+    h = ti.graphene_csr(9, 7, onsite=ti.anderson_onsite(126, 1.0, 4))
+    psi0 = ti.random_phase_state(h.n, 5)
+    ctx = create(h)
+    c = tb.tbpm_dos_corr(ctx, psi0, dt, 50)
+    ref = orc.dos_corr(h, 9.0, psi0, dt, 50)
+    K_orc = orc.cheb_num_terms(abs(dt) * 9.0)
+    assert tb.tbpm_get_info(ctx)["num_terms"] == max(K_orc, 3)
+    assert np.max(np.abs(c - ref)) <= TOL
+
+
+def test_zero_steps_and_multistate(orc):
+    h = ti.graphene_csr(10, 10, onsite=ti.anderson_onsite(200, 1.0, 7))
+    ctx = create(h)
+    psi = ti.random_phase_block(h.n, 3, seed0=4).T.copy()       # (3, n)
+    c0 = tb.tbpm_dos_corr(ctx, psi, DT, 0)
+    assert c0.shape == (3, 1) and np.allclose(c0[:, 0], 1.0, atol=1e-14)
+    c = tb.tbpm_dos_corr(ctx, psi, DT, 33)
+    for j in range(3):
+        assert np.max(np.abs(c[j] - orc.dos_corr(h, 9.0, psi[j], DT, 33))) <= TOL
+
+
+def test_config2_full_size_first_steps(orc):
+    """1024x1024 graphene (N = 2,097,152), W = 1 eV seed 1, psi0 seed 0: the bench's
+    matrix and launch configuration, checked over the first steps and moments."""
+    n = 2 * 1024 * 1024
+    h = ti.graphene_csr(1024, 1024, onsite=ti.anderson_onsite(n, 1.0, 1))
+    psi0 = ti.random_phase_state(n, 0)
+    ctx = create(h)
+    c = tb.tbpm_dos_corr(ctx, psi0, DT, 4)
+    assert np.max(np.abs(c - orc.dos_corr(h, 9.0, psi0, DT, 4))) <= TOL
+    mu = tb.kpm_moments(ctx, psi0, 40)
+    assert np.max(np.abs(mu - orc.kpm_moments(h, 9.0, psi0, 40))) <= TOL
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 17, 512])
+def test_kpm_moments(orc, M):
+    h = ti.graphene_csr(24, 20, onsite=ti.anderson_onsite(960, 1.0, 3), bond_phases=[0.3, 0.1, 0.2])
+    psi0 = ti.random_phase_state(h.n, 8)
+    ctx = create(h)
+    mu = tb.kpm_moments(ctx, psi0, M)
+    ref = orc.kpm_moments(h, 9.0, psi0, M)
+    assert mu.shape == (M,)
+    assert np.max(np.abs(mu - ref)) <= TOL
+
+
+def test_kpm_config1_site_state(orc):
+    h = ti.graphene_csr(64, 64)
+    ctx = create(h)
+    psi0 = ti.site_state(h.n, 0)
+    mu = tb.kpm_moments(ctx, psi0, 4096)
+    assert np.max(np.abs(mu - orc.kpm_moments(h, 9.0, psi0, 4096))) <= TOL
+
+
+@pytest.mark.parametrize("kind,l1,l2,w", [(0, 7, 9, 1.0), (0, 64, 64, 0.0), (1, 5, 6, 2.0),
+                                          (1, 33, 17, 0.5)])
+def test_stencil_matches_oracle(orc, kind, l1, l2, w):
+    per = 2 if kind == 0 else 4
+    n = per * l1 * l2
+    eps = ti.anderson_onsite(n, w, 11) if w > 0 else None
+    h = ti.graphene_csr(l1, l2, onsite=eps) if kind == 0 else ti.bilayer_csr(l1, l2, onsite=eps)
+    rescale = max(9.0, 1.02 * ti.gershgorin_bound(h))
+    psi0 = ti.random_phase_state(n, 6)
+    for path in (tb.TBPM_PATH_STENCIL, tb.TBPM_PATH_SELL):
+        ctx = tb.tbpm_create_lattice(kind, l1, l2, -2.7, 0.39, eps, rescale, tb.make_opts(path=path))
+        info = tb.tbpm_get_info(ctx)
+        assert info["path"] == path
+        c = tb.tbpm_dos_corr(ctx, psi0, math.pi / rescale, 120)
+        ref = orc.dos_corr(h, rescale, psi0, math.pi / rescale, 120)
+        assert np.max(np.abs(c - ref)) <= TOL
+        mu = tb.kpm_moments(ctx, psi0, 200)
+        assert np.max(np.abs(mu - orc.kpm_moments(h, rescale, psi0, 200))) <= TOL
+
+
+def test_dos_transforms(orc):
+    h = ti.graphene_csr(16, 16, onsite=ti.anderson_onsite(512, 1.0, 1))
+    psi0 = ti.random_phase_state(h.n, 0)
+    ctx = create(h)
+    corr = orc.dos_corr(h, 9.0, psi0, DT, 256)
+    e, d = tb.tbpm_dos_from_corr(ctx, corr, DT)
+    er, dr, _ = orc.dos_hann(corr, DT)
+    assert np.max(np.abs(e - er)) < 1e-12 and np.max(np.abs(d - dr)) < 1e-12
+    mu = orc.kpm_moments(h, 9.0, psi0, 300)
+    e, r = tb.kpm_dos_jackson(ctx, mu, 700)
+    er, rr = orc.kpm_dos(mu, 9.0, 700)
+    assert np.max(np.abs(e - er)) < 1e-12 and np.max(np.abs(r - rr)) < 1e-12
+
+
+def test_torch_device_buffers(orc):
+    torch = pytest.importorskip("torch")
+    h = ti.graphene_csr(32, 16, onsite=ti.anderson_onsite(1024, 1.0, 5))
+    psi0 = ti.random_phase_block(h.n, 2, seed0=1).T.copy()
+    s = torch.cuda.current_stream()
+    ctx = tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, 9.0, tb.make_opts(stream=s.cuda_stream))
+    dpsi = torch.from_numpy(psi0).cuda()
+    dc = tb.tbpm_dos_corr(ctx, dpsi, DT, 40)
+    dmu = tb.kpm_moments(ctx, dpsi, 64)
+    torch.cuda.synchronize()
+    assert dc.is_cuda and dmu.is_cuda
+    hc = tb.tbpm_dos_corr(ctx, psi0, DT, 40)
+    assert np.array_equal(dc.cpu().numpy(), hc)
+    assert np.max(np.abs(dmu.cpu().numpy()[1] - orc.kpm_moments(h, 9.0, psi0[1], 64))) <= TOL
+    e, d = tb.tbpm_dos_from_corr(ctx, dc[0], DT)
+    torch.cuda.synchronize()
+    er, dr, _ = orc.dos_hann(hc[0], DT)
+    assert np.max(np.abs(d.cpu().numpy() - dr)) < 1e-12
