@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     return ap.parse_args()
 
 
@@ -284,12 +285,87 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": gpu_launches,
         "clocks": clocks.summary(),
     }
+    tb.tbpm_destroy(ctx)
+    del h
+    if rank == 0 and world == 1 and not args.no_variants:
+        out["variants"] = run_variants(args, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sample = cpu_sample(h)
+        v, sample = cpu_sample(build_inputs())
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
                                "sample": sample}
-    tb.tbpm_destroy(ctx)
     return out
+
+
+def timed_calls(fn, reps, stream):
+    """Mean device time (ms) of fn() over reps calls, after one warm-up call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_variants(args, dev, stream):
+    """The precision and batching patterns, each timed with CUDA events on
+    device-resident inputs (not part of the headline value):
+      - FP32 single state, stored matrix: graphene 2048x2048, W = 1 (N = 8,388,608),
+        1024 steps;
+      - FP32 block of 16 states vs FP64 single state on graphene 4096x4096,
+        W = 1 (N = 33,554,432, the paper's benchmark lattice), stencil path,
+        32 steps each (the speedup is a throughput ratio, so the step count
+        only sets the sample length)."""
+    import numpy as np
+    import torch
+    import tbpm_inputs as ti
+    import paper_2509_26309_gb300 as tb
+    res = {}
+    # config 3: FP32 single state, SELL
+    n3 = 2 * 2048 * 2048
+    h3 = ti.graphene_csr(2048, 2048, onsite=ti.anderson_onsite(n3, W_DISORDER, 1))
+    ctx = tb.tbpm_create(n3, h3.row_ptr, h3.col, h3.val, RESCALE,
+                         tb.make_opts(precision=tb.TBPM_FP32, stream=stream.cuda_stream))
+    del h3
+    psi = torch.from_numpy(ti.random_phase_state(n3, 0).reshape(1, n3)).to(dev)
+    out = torch.empty((1, 1025), dtype=torch.complex128, device=dev)
+    ms = timed_calls(lambda: tb.tbpm_dos_corr(ctx, psi, DT, 1024, out=out), 2, stream)
+    K = tb.tbpm_get_info(ctx)["num_terms"]
+    res["fp32_sell_2048x2048"] = {"value": n3 * 1024 * (K - 1) / (ms / 1e3), "unit": UNIT,
+                                  "ms_per_call": ms, "states": 1, "n_steps": 1024}
+    tb.tbpm_destroy(ctx)
+    del psi
+    # config 4 lattice: FP32 x16 states vs FP64 x1, stencil
+    l4 = 4096
+    n4 = 2 * l4 * l4
+    eps = ti.anderson_onsite(n4, W_DISORDER, 1)
+    steps = 32
+    ctx32 = tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l4, l4, ti.T_GRAPHENE, 0.0, eps, RESCALE,
+                                   tb.make_opts(precision=tb.TBPM_FP32, stream=stream.cuda_stream))
+    blk = torch.empty((16, n4), dtype=torch.complex128, device=dev)
+    for j in range(16):
+        blk[j].copy_(torch.from_numpy(ti.random_phase_state(n4, j)))
+    o16 = torch.empty((16, steps + 1), dtype=torch.complex128, device=dev)
+    ms32 = timed_calls(lambda: tb.tbpm_dos_corr(ctx32, blk, DT, steps, out=o16), 2, stream)
+    tb.tbpm_destroy(ctx32)
+    v32 = n4 * 16 * steps * (K - 1) / (ms32 / 1e3)
+    ctx64 = tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l4, l4, ti.T_GRAPHENE, 0.0, eps, RESCALE,
+                                   tb.make_opts(precision=tb.TBPM_FP64, stream=stream.cuda_stream))
+    one = blk[0:1].contiguous()
+    del blk
+    o1 = torch.empty((1, steps + 1), dtype=torch.complex128, device=dev)
+    ms64 = timed_calls(lambda: tb.tbpm_dos_corr(ctx64, one, DT, steps, out=o1), 2, stream)
+    tb.tbpm_destroy(ctx64)
+    v64 = n4 * steps * (K - 1) / (ms64 / 1e3)
+    res["fp32_x16_stencil_4096x4096"] = {"value": v32, "unit": "orbital-term-states/s",
+                                         "ms_per_call": ms32, "states": 16, "n_steps": steps}
+    res["fp64_x1_stencil_4096x4096"] = {"value": v64, "unit": UNIT, "ms_per_call": ms64, "states": 1,
+                                        "n_steps": steps}
+    res["fp32_batched_speedup_vs_fp64"] = v32 / v64
+    return res
 
 
 def profile_traffic():

@@ -58,7 +58,15 @@ extern "C" {
 
 #define TBPM_F_NO_HERMITIAN_CHECK 0x1u /* skip the O(nnz) H = H^dagger check        */
 #define TBPM_F_FORCE_RESCALE      0x2u /* accept rescale below the Gershgorin bound */
-#define TBPM_F_RENORM             0x4u /* FP32: renormalise psi to 1 after each step */
+#define TBPM_F_RENORM             0x4u /* tbpm_dos_corr renormalises psi to unit
+                                          norm (FP64 norm) after each step; meant
+                                          for FP32 contexts, whose rounding lets
+                                          the norm drift                           */
+#define TBPM_F_NO_CLUSTER         0x8u /* never use the single-launch cluster path
+                                          that single-state tbpm_dos_corr takes for
+                                          systems of up to 16 x 4096 (FP64) or
+                                          16 x 8192 (FP32) padded rows; the result
+                                          is the same either way                   */
 
 typedef struct tbpm_opts {
     int precision;       /* TBPM_FP64 | TBPM_FP32                                  */
@@ -119,6 +127,41 @@ typedef struct tbpm_lattice {
 int tbpm_create_lattice(tbpm_ctx **out, const tbpm_lattice *lat, double rescale,
                         const tbpm_opts *opts);
 
+/* One lattice of an uneven batch (tbpm_create_batch). */
+typedef struct tbpm_instance {
+    int64_t n;               /* orbitals of this instance, >= 1                */
+    const int64_t *row_ptr;  /* HOST CSR of this instance, as tbpm_create     */
+    const int32_t *col;
+    const double *val;
+    double rescale;          /* this instance's rescale factor, > 0          */
+} tbpm_instance;
+
+/* tbpm_create_batch: one solver for many independent Hamiltonians of uneven
+ * size (the random-sample and model parallelism of Sec. 2.4.2, here in one
+ * GPU launch sequence). The instances are stored as one block-diagonal
+ * operator, each padded to a multiple of 32 rows and pre-scaled by its own
+ * 2/rescale; every sweep covers all instances, and each instance keeps its
+ * own coefficients, state and correlation.
+ *   ninst  1 <= ninst <= 4096;  inst  HOST array of ninst descriptors.
+ * Each instance is validated as in tbpm_create (same statuses); the sum of
+ * the padded sizes must stay below 2^31. tbpm_dos_corr and kpm_moments are
+ * not available on a batch context (TBPM_ERR_UNSUPPORTED); use
+ * tbpm_batch_dos_corr. */
+int tbpm_create_batch(tbpm_ctx **out, int ninst, const tbpm_instance *inst,
+                      const tbpm_opts *opts);
+
+/* tbpm_batch_dos_corr: tbpm_dos_corr for every instance of a batch context,
+ * one state per instance, all advanced in the same sweeps.
+ *   psi0  double[2 * sum_g n_g]: instance g's state at offset 2 * sum_{h<g} n_h
+ *   dt    HOST double[ninst]: per-instance time step (x_g = dt_g * rescale_g,
+ *         |x_g| <= 40); instances with fewer terms K_g run the largest K with
+ *         their coefficients beyond K_g set to zero, which leaves their
+ *         results those of K_g terms
+ *   n_steps >= 0;  corr double[2 * ninst * (n_steps + 1)], instance-major.
+ * psi0 and corr may be host or device memory, as for tbpm_dos_corr. */
+int tbpm_batch_dos_corr(tbpm_ctx *ctx, const double *psi0, const double *dt, int n_steps,
+                        double *corr);
+
 /* Releases every resource of ctx (NULL is ignored). */
 void tbpm_destroy(tbpm_ctx *ctx);
 
@@ -140,6 +183,15 @@ void tbpm_destroy(tbpm_ctx *ctx);
  * The states are not normalised by the library. */
 int tbpm_dos_corr(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, int n_steps,
                   double *corr);
+
+/* tbpm_propagate: the time-dependent wave function (WFT, one of the TBPM
+ * capabilities benchmarked in Sec. 4.2.2): the same evolution as tbpm_dos_corr,
+ * returning psi(t_{n_steps}) of every state.
+ *   psi_out  double[2*n*nstates], state-major as psi0 (host or device)
+ *   corr     as tbpm_dos_corr, or NULL when the correlation is not wanted
+ * With TBPM_F_RENORM the returned state is normalised to 1. */
+int tbpm_propagate(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, int n_steps,
+                   double *psi_out, double *corr);
 
 /* kpm_moments: mu_m = <psi0_j|T_m(H~)|psi0_j>, m = 0..M-1 (the kernel
  * polynomial method named in Sec. 1), written as complex numbers to

@@ -100,25 +100,111 @@ __device__ __forceinline__ double2 block_sum2(double re, double im, double2 *sm)
     return r;
 }
 
-// <a|b> per block over rows (grid-stride, the same row order for every call).
+// <a|b> per 32-row slice: one warp per slice, fixed butterfly; partials[s].
 template <typename R>
-__global__ void __launch_bounds__(kBlock) dot_kernel(const void *a_, const void *b_, int64_t rows,
+__global__ void __launch_bounds__(kBlock) dot_slices(const void *a_, const void *b_, int64_t nslices,
                                                      double2 *partials)
 {
     typedef typename V2<R>::T V;
-    __shared__ double2 red[kBlock / 32];
     const V *a = reinterpret_cast<const V *>(a_);
     const V *b = reinterpret_cast<const V *>(b_);
-    double re = 0.0, im = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += stride) {
-        const V p = a[i], q = b[i];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = warp; s < nslices; s += nwarps) {
+        const V p = a[s * 32 + lane], q = b[s * 32 + lane];
         const double pr = p.x, pi = p.y, qr = q.x, qi = q.y;
-        re = fma(pr, qr, fma(pi, qi, re));
-        im = fma(pr, qi, fma(-pi, qr, im));
+        double re = fma(pr, qr, pi * qi), im = fma(pr, qi, -pi * qr);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) partials[s] = make_double2(re, im);
     }
-    const double2 r = block_sum2(re, im, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = r;
+}
+
+// Segmented fixed-order sums of per-slice partials laid out [nslot][nterm][nslices]:
+//   out[g * ld + (base + offset + d) * nterm + q] = sum_{s in segment g} P[(d * nterm + q) * nslices + s],
+// segment g = [seg_off[g], seg_off[g+1]) (one segment [0, nslices) if seg_off is
+// null), base = *counter (0 if null). One block per (d, q, g).
+__global__ void __launch_bounds__(256) reduce_seg_kernel(const double2 *partials, int nslot, int nterm,
+                                                         int64_t nslices, const int64_t *seg_off,
+                                                         int nseg, const int *counter, int offset,
+                                                         double2 *out, int64_t ld)
+{
+    __shared__ double sr[256], si[256];
+    const int idx = blockIdx.x;
+    const int g = idx % nseg, dq = idx / nseg;
+    const int d = dq / nterm, q = dq - d * nterm;
+    if (d >= nslot) return;
+    const int64_t lo = seg_off ? seg_off[g] : 0, hi = seg_off ? seg_off[g + 1] : nslices;
+    const double2 *p = partials + ((int64_t)d * nterm + q) * nslices;
+    double re = 0.0, im = 0.0;
+    for (int64_t s = lo + threadIdx.x; s < hi; s += blockDim.x) { re += p[s].x; im += p[s].y; }
+    sr[threadIdx.x] = re;
+    si[threadIdx.x] = im;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) { sr[threadIdx.x] += sr[threadIdx.x + o]; si[threadIdx.x] += si[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int base = counter ? *counter : 0;
+        out[(int64_t)g * ld + (int64_t)(base + offset + d) * nterm + q] = make_double2(sr[0], si[0]);
+    }
+}
+
+// scale[g] = 1/sqrt(sum_{s in segment g} norm[s].x): one block per segment.
+__global__ void __launch_bounds__(256) renorm_seg_kernel(const double2 *norm, int64_t nslices,
+                                                         const int64_t *seg_off, double *scale)
+{
+    __shared__ double sm[256];
+    const int g = blockIdx.x;
+    const int64_t lo = seg_off ? seg_off[g] : 0, hi = seg_off ? seg_off[g + 1] : nslices;
+    double v = 0.0;
+    for (int64_t s = lo + threadIdx.x; s < hi; s += blockDim.x) v += norm[s].x;
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scale[g] = sm[0] > 0.0 ? 1.0 / sqrt(sm[0]) : 1.0;
+}
+
+// Column `col` of an interleaved [n_pad][B] state buffer, scaled by scale[col]
+// (or 1), as FP64 complex [n] (the inverse of load_column).
+template <typename R>
+__global__ void store_column_kernel(const void *src_, int64_t n, int B, int col, const double *scale,
+                                    double2 *dst)
+{
+    typedef typename V2<R>::T V;
+    const V *src = reinterpret_cast<const V *>(src_);
+    const double sc = scale ? scale[col] : 1.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const V v = src[i * B + col];
+        dst[i] = make_double2(sc * (double)v.x, sc * (double)v.y);
+    }
+}
+
+// Batch coefficients: zero c_k for k >= max(K_g, 3) of every instance g, so
+// that running more terms than an instance needs changes nothing (the
+// Clenshaw terms b_k of those orders stay exactly zero).
+__global__ void mask_coef_kernel(double2 *coef, const int *K, int ninst)
+{
+    const int g = blockIdx.x;
+    if (g >= ninst) return;
+    const int Ke = K[g] < 3 ? 3 : K[g];
+    for (int k = threadIdx.x; k < kMaxTerms; k += blockDim.x)
+        if (k >= Ke) coef[(int64_t)g * kMaxTerms + k] = make_double2(0.0, 0.0);
+}
+
+__global__ void fill_kernel(double *p, int n, double v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
 }
 
 // One warp per (slot, term): lane-strided partial sums, then a fixed butterfly.
@@ -174,6 +260,40 @@ __global__ void load_states_kernel(const double2 *src, int64_t n, int64_t n_pad,
     }
 }
 
+template <typename R>
+__global__ void load_column_kernel(const double2 *src, int64_t n, int B, int col, void *dst0_,
+                                   void *dst1_)
+{
+    typedef typename V2<R>::T V;
+    V *dst0 = reinterpret_cast<V *>(dst0_);
+    V *dst1 = reinterpret_cast<V *>(dst1_);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double2 s = src[i];
+        V v;
+        v.x = (R)s.x; v.y = (R)s.y;
+        dst0[i * B + col] = v;
+        dst1[i * B + col] = v;
+    }
+}
+
+// 1/||psi_j|| per state from the final sweep's FP64 norm partials (one warp
+// per state, fixed order); all ones when there are no partials yet.
+__global__ void renorm_kernel(const double2 *norm_partials, int nblk, int B, double *scale)
+{
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (j >= B) return;
+    if (!norm_partials) {
+        if (lane == 0) scale[j] = 1.0;
+        return;
+    }
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += norm_partials[(int64_t)b * B + j].x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) scale[j] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+}
+
 // dots[q] = (<T_q|T_q>, <T_{q+1}|T_q>), q = 0..; the product identities
 //   mu_{2q} = 2<T_q|T_q> - mu_0,  mu_{2q+1} = 2<T_q|T_{q+1}> - mu_1
 // with mu_0 = <T_0|T_0> and mu_1 = <T_0|T_1>.
@@ -205,11 +325,54 @@ cudaError_t launch_bessel(double x, double tol, double2 *d_coef, int *d_K, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_dot(int precision, const void *a, const void *b, int64_t rows,
+cudaError_t launch_dot(int precision, const void *a, const void *b, int64_t nslices,
                        double2 *partials, int grid, cudaStream_t s)
 {
-    if (precision == TBPM_FP64) dot_kernel<double><<<grid, kBlock, 0, s>>>(a, b, rows, partials);
-    else dot_kernel<float><<<grid, kBlock, 0, s>>>(a, b, rows, partials);
+    if (precision == TBPM_FP64) dot_slices<double><<<grid, kBlock, 0, s>>>(a, b, nslices, partials);
+    else dot_slices<float><<<grid, kBlock, 0, s>>>(a, b, nslices, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_seg(const double2 *partials, int nslot, int nterm, int64_t nslices,
+                              const int64_t *seg_off, int nseg, const int *counter, int offset,
+                              double2 *out, int64_t ld, cudaStream_t s)
+{
+    const int blocks = nslot * nterm * nseg;
+    if (blocks <= 0) return cudaSuccess;
+    reduce_seg_kernel<<<blocks, 256, 0, s>>>(partials, nslot, nterm, nslices, seg_off, nseg, counter,
+                                             offset, out, ld);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_renorm_seg(const double2 *norm, int64_t nslices, const int64_t *seg_off, int nseg,
+                              double *scale, cudaStream_t s)
+{
+    renorm_seg_kernel<<<nseg, 256, 0, s>>>(norm, nslices, seg_off, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_column(int precision, const void *src, int64_t n, int B, int col,
+                                const double *scale, double *dst, cudaStream_t s)
+{
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    double2 *d = reinterpret_cast<double2 *>(dst);
+    if (precision == TBPM_FP64)
+        store_column_kernel<double><<<(int)blocks, 256, 0, s>>>(src, n, B, col, scale, d);
+    else
+        store_column_kernel<float><<<(int)blocks, 256, 0, s>>>(src, n, B, col, scale, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mask_coef(double2 *coef, const int *K, int ninst, cudaStream_t s)
+{
+    mask_coef_kernel<<<ninst, 128, 0, s>>>(coef, K, ninst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double *p, int n, double v, cudaStream_t s)
+{
+    fill_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, n, v);
     return cudaGetLastError();
 }
 
@@ -243,6 +406,26 @@ cudaError_t launch_load_states(int precision, const double *src, int64_t n, int6
         load_states_kernel<double><<<(int)blocks, 256, 0, s>>>(sp, n, n_pad, nstates_src, j0, B, dst0, dst1);
     else
         load_states_kernel<float><<<(int)blocks, 256, 0, s>>>(sp, n, n_pad, nstates_src, j0, B, dst0, dst1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_column(int precision, const double *src, int64_t n, int B, int col,
+                               void *dst0, void *dst1, cudaStream_t s)
+{
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    const double2 *sp = reinterpret_cast<const double2 *>(src);
+    if (precision == TBPM_FP64)
+        load_column_kernel<double><<<(int)blocks, 256, 0, s>>>(sp, n, B, col, dst0, dst1);
+    else
+        load_column_kernel<float><<<(int)blocks, 256, 0, s>>>(sp, n, B, col, dst0, dst1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_renorm(const double2 *norm_partials, int nblk, int B, double *scale,
+                          cudaStream_t s)
+{
+    renorm_kernel<<<1, 32 * B, 0, s>>>(norm_partials, nblk, B, scale);
     return cudaGetLastError();
 }
 

@@ -103,27 +103,27 @@ __device__ __forceinline__ void stencil_apply(const SweepParams &p, int64_t row,
                                               R &ar, R &ai)
 {
     typedef typename V2<R>::T V;
-    const int per = (OP == OP_STENCIL_MONO) ? 2 : 4;
-    const int64_t cell = row / per;
-    const int o = (int)(row - cell * per);
-    const int64_t m1 = cell / p.l2;
-    const int64_t m2 = cell - m1 * p.l2;
-    const int layer = o >> 1;
-    const int s = o & 1;
-    const int64_t base_o = 2 * layer;                   // orbital of A in this layer
-    int64_t n0, n1, n2;                                 // the three in-layer neighbours
-    if (s == 0) {                                       // A: B(m), B(m-a1), B(m-a2)
-        const int64_t mm1 = (m1 == 0) ? p.l1 - 1 : m1 - 1;
-        const int64_t mm2 = (m2 == 0) ? p.l2 - 1 : m2 - 1;
+    // orbital counts are below 2^31, so the index arithmetic is 32-bit
+    const unsigned per = (OP == OP_STENCIL_MONO) ? 2u : 4u;
+    const unsigned r = (unsigned)row, L1 = (unsigned)p.l1, L2 = (unsigned)p.l2;
+    const unsigned cell = r / per;
+    const unsigned o = r - cell * per;
+    const unsigned m1 = cell / L2;
+    const unsigned m2 = cell - m1 * L2;
+    const unsigned base_o = o & 2u;                     // orbital of A in this layer
+    unsigned n0, n1, n2;                                // the three in-layer neighbours
+    if ((o & 1u) == 0) {                                // A: B(m), B(m-a1), B(m-a2)
+        const unsigned mm1 = (m1 == 0) ? L1 - 1 : m1 - 1;
+        const unsigned mm2 = (m2 == 0) ? L2 - 1 : m2 - 1;
         n0 = cell * per + base_o + 1;
-        n1 = (mm1 * p.l2 + m2) * per + base_o + 1;
-        n2 = (m1 * p.l2 + mm2) * per + base_o + 1;
+        n1 = (mm1 * L2 + m2) * per + base_o + 1;
+        n2 = (m1 * L2 + mm2) * per + base_o + 1;
     } else {                                            // B: A(m), A(m+a1), A(m+a2)
-        const int64_t pm1 = (m1 == p.l1 - 1) ? 0 : m1 + 1;
-        const int64_t pm2 = (m2 == p.l2 - 1) ? 0 : m2 + 1;
+        const unsigned pm1 = (m1 == L1 - 1) ? 0 : m1 + 1;
+        const unsigned pm2 = (m2 == L2 - 1) ? 0 : m2 + 1;
         n0 = cell * per + base_o;
-        n1 = (pm1 * p.l2 + m2) * per + base_o;
-        n2 = (m1 * p.l2 + pm2) * per + base_o;
+        n1 = (pm1 * L2 + m2) * per + base_o;
+        n2 = (m1 * L2 + pm2) * per + base_o;
     }
     const V x0 = __ldg(x + n0), x1 = __ldg(x + n1), x2 = __ldg(x + n2);
     const R t = (R)p.t;
@@ -137,39 +137,42 @@ __device__ __forceinline__ void stencil_apply(const SweepParams &p, int64_t row,
     }
 }
 
-// Block-wide deterministic sum of (re, im) pairs: fixed butterfly in each warp,
-// then warp 0 adds the warp results in order. Result valid in thread 0.
-__device__ __forceinline__ double2 block_sum(double re, double im, double2 *sm)
+// Warp-wide sum in a fixed butterfly order; every lane gets the result.
+__device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_xor_sync(0xffffffffu, re, o);
-        im += __shfl_xor_sync(0xffffffffu, im, o);
-    }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) sm[w] = make_double2(re, im);
-    __syncthreads();
-    double2 r = make_double2(0.0, 0.0);
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { r.x += sm[i].x; r.y += sm[i].y; }
-    }
-    __syncthreads();
-    return r;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-// One Clenshaw sweep for a single state per row (B = 1).
+// Coefficients of one sweep: a on psi (real, or imaginary if AIMAG), beta on A x.
+// For a batch of instances, coefficients and the renormalisation scale are
+// those of the slice's instance.
+template <typename R, int BM, bool AIMAG>
+__device__ __forceinline__ void sweep_coeffs(const SweepParams &p, int inst, R &a, R &beta)
+{
+    const double2 *c = p.coef + (int64_t)inst * kMaxTerms;
+    const double2 ca = c[p.ia];
+    const double2 cb = p.ib >= 0 ? c[p.ib] : make_double2(0.0, 0.0);
+    // renormalisation folds 1/||psi|| into the coefficients that multiply psi
+    // (in the first sweep also into beta, whose operand is psi itself)
+    const double sc = p.scale ? p.scale[inst] : 1.0;
+    a = (R)(sc * (AIMAG ? (ca.y - cb.y) : (ca.x - cb.x)));
+    beta = (R)p.bscale;
+    if (BM == B_REAL && p.ic >= 0) beta = (R)(sc * p.bscale * c[p.ic].x);
+    if (BM == B_IMAG && p.ic >= 0) beta = (R)(sc * p.bscale * c[p.ic].y);
+}
+
+// One Clenshaw sweep for a single state per row (B = 1). A warp owns one
+// 32-row slice at a time. The final sweep reduces <psi0|y> (and ||y||^2 when
+// renormalising) over each slice in a fixed butterfly and stores one partial
+// per slice, so the reduced values do not depend on the launch configuration.
 template <typename R, int OP, bool REALV, int BM, bool AIMAG, bool HASZ, bool FINAL>
 __global__ void __launch_bounds__(kBlock) sweep_b1(SweepParams p)
 {
     typedef typename V2<R>::T V;
-    __shared__ double2 red[kBlock / 32];
-    // coefficients: a on psi (real or imaginary), beta on A x
-    const double2 ca = p.coef[p.ia];
-    const double2 cb = p.ib >= 0 ? p.coef[p.ib] : make_double2(0.0, 0.0);
-    const R a = (R)(AIMAG ? (ca.y - cb.y) : (ca.x - cb.x));
-    R beta = (R)p.bscale;
-    if (BM == B_REAL && p.ic >= 0) beta = (R)(p.bscale * p.coef[p.ic].x);
-    if (BM == B_IMAG && p.ic >= 0) beta = (R)(p.bscale * p.coef[p.ic].y);
+    R a, beta;
+    sweep_coeffs<R, BM, AIMAG>(p, 0, a, beta);
 
     const V *__restrict__ x = reinterpret_cast<const V *>(p.x);
     const V *psi = reinterpret_cast<const V *>(p.psi);
@@ -181,9 +184,9 @@ __global__ void __launch_bounds__(kBlock) sweep_b1(SweepParams p)
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double dr = 0.0, di = 0.0;
 
     for (int64_t s = warp; s < p.nslices; s += nwarps) {
+        if (p.slice_inst) sweep_coeffs<R, BM, AIMAG>(p, __ldg(p.slice_inst + s), a, beta);
         const int64_t row = (s << 5) + lane;
         const V ps = psi[row];
         // t = a psi - z  (a real: a*psi; a imaginary: i*a*psi)
@@ -206,22 +209,23 @@ __global__ void __launch_bounds__(kBlock) sweep_b1(SweepParams p)
             const V q = psi0[row];
             const double qr = (double)q.x, qi = (double)q.y;
             const double orr = (double)out.x, oi = (double)out.y;
-            dr = fma(qr, orr, fma(qi, oi, dr));
-            di = fma(qr, oi, fma(-qi, orr, di));
+            const double dr = warp_sum(fma(qr, orr, qi * oi));
+            const double di = warp_sum(fma(qr, oi, -qi * orr));
+            if (lane == 0) p.partials[(int64_t)p.delta * p.nslices + s] = make_double2(dr, di);
+            if (p.norm_partials) {
+                const double nn = warp_sum(fma(orr, orr, oi * oi));
+                if (lane == 0) p.norm_partials[(int64_t)p.delta * p.nslices + s] = make_double2(nn, 0.0);
+            }
         }
-    }
-    if (FINAL) {
-        const double2 r = block_sum(dr, di, red);
-        if (threadIdx.x == 0) p.partials[(int64_t)p.delta * p.nblk + blockIdx.x] = r;
     }
 }
 
-// KPM sweep for B = 1: y = scale * (A x) - [!first] y; dots <x|x>, <y|x>.
+// KPM sweep for B = 1: y = scale * (A x) - [!first] y, with per-slice partials
+// of <x|x> and <y|x> at partials[(2 delta + 0/1) * nslices + slice].
 template <typename R, int OP, bool REALV, bool FIRST>
 __global__ void __launch_bounds__(kBlock) kpm_b1(KpmParams p)
 {
     typedef typename V2<R>::T V;
-    __shared__ double2 red[kBlock / 32];
     SweepParams sp;                     // operator fields for the shared helpers
     sp.n = p.n; sp.nslices = p.nslices; sp.slice_off = p.slice_off; sp.cols = p.cols; sp.vals = p.vals;
     sp.diag = p.diag; sp.l1 = p.l1; sp.l2 = p.l2; sp.t = p.t; sp.t_perp = p.t_perp;
@@ -232,7 +236,8 @@ __global__ void __launch_bounds__(kBlock) kpm_b1(KpmParams p)
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double nn = 0.0, cr = 0.0, ci = 0.0;
+    double2 *pn = p.partials + (int64_t)p.delta * 2 * p.nslices;
+    double2 *pc = pn + p.nslices;
     for (int64_t s = warp; s < p.nslices; s += nwarps) {
         const int64_t row = (s << 5) + lane;
         const V xi = __ldg(x + row);
@@ -254,17 +259,14 @@ __global__ void __launch_bounds__(kBlock) kpm_b1(KpmParams p)
         y[row] = out;
         const double xr = (double)xi.x, xim = (double)xi.y;
         const double orr = (double)out.x, oi = (double)out.y;
-        nn = fma(xr, xr, fma(xim, xim, nn));
+        const double nn = warp_sum(fma(xr, xr, xim * xim));
         // <y|x> = sum conj(y) x
-        cr = fma(orr, xr, fma(oi, xim, cr));
-        ci = fma(orr, xim, fma(-oi, xr, ci));
-    }
-    const double2 r0 = block_sum(nn, 0.0, red);
-    const double2 r1 = block_sum(cr, ci, red);
-    if (threadIdx.x == 0) {
-        double2 *base = p.partials + (int64_t)p.delta * 2 * p.nblk;
-        base[blockIdx.x] = r0;
-        base[p.nblk + blockIdx.x] = r1;
+        const double cr = warp_sum(fma(orr, xr, oi * xim));
+        const double ci = warp_sum(fma(orr, xim, -oi * xr));
+        if (lane == 0) {
+            pn[s] = make_double2(nn, 0.0);
+            pc[s] = make_double2(cr, ci);
+        }
     }
 }
 

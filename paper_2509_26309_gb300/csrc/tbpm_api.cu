@@ -195,14 +195,15 @@ int init_device(tbpm_ctx *ctx, const tbpm_opts &o)
     ctx->stream = o.stream ? (cudaStream_t)o.stream : cudaStreamLegacy;
     ctx->own_stream = false;
     CU(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
-    CU(cudaMalloc(&ctx->d_coef, sizeof(double2) * kMaxTerms));
-    CU(cudaMalloc(&ctx->d_K, sizeof(int)));
+    const int ncoef = std::max(1, ctx->ninst);
+    CU(cudaMalloc(&ctx->d_coef, sizeof(double2) * kMaxTerms * ncoef));
+    CU(cudaMalloc(&ctx->d_K, sizeof(int) * ncoef));
     CU(cudaMalloc(&ctx->d_counter, sizeof(int) * 4));
     return TBPM_OK;
 }
 
 template <typename R>
-void to_sell(const HostMatrix &m, int64_t n_pad, double s, bool real_values,
+void to_sell(const HostMatrix &m, int64_t n_pad, const std::vector<double> &row_scale, bool real_values,
              std::vector<int64_t> &off, std::vector<int32_t> &cols, std::vector<R> &vals,
              std::vector<R> &diag, int &max_width)
 {
@@ -233,13 +234,14 @@ void to_sell(const HostMatrix &m, int64_t n_pad, double s, bool real_values,
                 if (j < len) {
                     const int64_t p = m.rp[r] + j;
                     cols[e] = m.col[p];
+                    const double s = row_scale[r];
                     if (real_values) vals[e] = (R)(s * m.re[p]);
                     else { vals[2 * e] = (R)(s * m.re[p]); vals[2 * e + 1] = (R)(s * m.im[p]); }
                 } else {
                     cols[e] = (int32_t)r;      // padding: own row, value 0
                 }
             }
-            if (r < m.n) diag[r] = (R)(s * m.diag[r]);
+            if (r < m.n) diag[r] = (R)(row_scale[r] * m.diag[r]);
         }
     }
 }
@@ -253,9 +255,15 @@ int upload(tbpm_ctx *ctx, void **dst, const std::vector<T> &src)
     return TBPM_OK;
 }
 
-int setup_sell(tbpm_ctx *ctx, const HostMatrix &m)
+// Stores A = 2 H / rescale (per row: 2 / rescale of the row's instance).
+int setup_sell(tbpm_ctx *ctx, const HostMatrix &m, const std::vector<double> *row_scale = nullptr)
 {
-    const double s = 2.0 / ctx->rescale;                 // stored operator A = 2 H / rescale
+    std::vector<double> uniform;
+    if (!row_scale) {
+        uniform.assign(m.n, 2.0 / ctx->rescale);
+        row_scale = &uniform;
+    }
+    const std::vector<double> &s = *row_scale;
     std::vector<int64_t> off;
     std::vector<int32_t> cols;
     int rc;
@@ -322,9 +330,10 @@ int ensure_work(tbpm_ctx *ctx, int states, size_t out_elems, size_t stage_double
     if (states > ctx->cap_states) {
         destroy_graphs(ctx);
         cudaFree(ctx->d_psi); cudaFree(ctx->d_b0); cudaFree(ctx->d_b1); cudaFree(ctx->d_psi0);
-        cudaFree(ctx->d_partials);
+        cudaFree(ctx->d_partials); cudaFree(ctx->d_norm); cudaFree(ctx->d_scale);
         ctx->d_psi = ctx->d_b0 = ctx->d_b1 = ctx->d_psi0 = nullptr;
-        ctx->d_partials = nullptr;
+        ctx->d_partials = ctx->d_norm = nullptr;
+        ctx->d_scale = nullptr;
         const size_t vb = vec_bytes(ctx->precision) * (size_t)ctx->n_pad * states;
         CU(cudaMalloc(&ctx->d_psi, vb));
         CU(cudaMalloc(&ctx->d_b0, vb));
@@ -332,8 +341,15 @@ int ensure_work(tbpm_ctx *ctx, int states, size_t out_elems, size_t stage_double
         CU(cudaMalloc(&ctx->d_psi0, vb));
         CU(cudaMemsetAsync(ctx->d_b0, 0, vb, ctx->stream));
         CU(cudaMemsetAsync(ctx->d_b1, 0, vb, ctx->stream));
-        ctx->partials_cap = (size_t)(kChunk + 1) * 2 * ctx->nblk * states;
+        // single-state partials: one per slice; 16-state partials: one per block and state
+        const size_t nsl = (size_t)(ctx->n_pad / kSlice);
+        const size_t per_slot = std::max<size_t>(2 * nsl, (size_t)ctx->nblk16 * kMaxBlockStates);
+        ctx->partials_cap = (size_t)(kChunk + 1) * per_slot;
         CU(cudaMalloc(&ctx->d_partials, ctx->partials_cap * sizeof(double2)));
+        if (ctx->flags & TBPM_F_RENORM) {
+            CU(cudaMalloc(&ctx->d_norm, (size_t)kChunk * per_slot * sizeof(double2)));
+            CU(cudaMalloc(&ctx->d_scale, sizeof(double) * std::max(kMaxBlockStates, ctx->ninst)));
+        }
         ctx->cap_states = states;
     }
     if (out_elems > ctx->out_cap) {
@@ -373,49 +389,72 @@ int ensure_coeffs(tbpm_ctx *ctx, double x, int *K)
 // Enqueues `len` time steps (each K-1 sweeps) on stream s; step d of the
 // chunk writes dot partials to slot d, then one reduction stores
 // C(t_{base+1..base+len}) and the base counter advances.
-int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, cudaStream_t s, int64_t *launches)
+int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, int B, int64_t ld, cudaStream_t s,
+                      int64_t *launches)
 {
-    const SweepVariant v = variant(ctx, 1);
+    const SweepVariant v = variant(ctx, B);
+    auto sweep = [&](SweepKind kind, bool a_imag, bool has_z, const SweepParams &p) {
+        return B == 1 ? launch_sweep(v, kind, a_imag, has_z, p, ctx->nblk, s)
+                      : launch_sweep_b16(v, kind, a_imag, has_z, p, ctx->nblk16, s);
+    };
     SweepParams p;
     fill_operator(ctx, p);
     p.coef = ctx->d_coef;
     p.psi = ctx->d_psi;
     p.psi0 = ctx->d_psi0;
     p.partials = ctx->d_partials;
-    void *B[2] = {ctx->d_b0, ctx->d_b1};
-    const int grid = ctx->nblk;
+    p.nblk = B == 1 ? ctx->nblk : ctx->nblk16;
+    const bool renorm = (ctx->flags & TBPM_F_RENORM) != 0;
+    if (renorm) {
+        p.scale = ctx->d_scale;
+        p.norm_partials = ctx->d_norm;
+    }
+    const int nseg = std::max(1, ctx->ninst);
+    p.slice_inst = ctx->d_slice_inst;                    // nullptr for a single instance
+    void *Bv[2] = {ctx->d_b0, ctx->d_b1};
     for (int d = 0; d < len; ++d) {
         // FIRST: b_{K-2} = c_{K-2} psi + c_{K-1} A psi  -> B[0]
-        p.x = ctx->d_psi; p.z = nullptr; p.y = B[0];
+        p.x = ctx->d_psi; p.z = nullptr; p.y = Bv[0];
         p.ia = K - 2; p.ib = -1; p.ic = K - 1; p.bscale = 1.0;
-        CU(launch_sweep(v, SW_FIRST, ((K - 2) & 1) != 0, false, p, grid, s));
+        CU(sweep(SW_FIRST, ((K - 2) & 1) != 0, false, p));
         ++*launches;
         if (K >= 4) {
             // SECOND: b_{K-3} = (c_{K-3} - c_{K-1}) psi + A b_{K-2}  -> B[1]
-            p.x = B[0]; p.z = nullptr; p.y = B[1];
+            p.x = Bv[0]; p.z = nullptr; p.y = Bv[1];
             p.ia = K - 3; p.ib = K - 1; p.ic = -1; p.bscale = 1.0;
-            CU(launch_sweep(v, SW_SECOND, ((K - 3) & 1) != 0, false, p, grid, s));
+            CU(sweep(SW_SECOND, ((K - 3) & 1) != 0, false, p));
             ++*launches;
         }
         for (int k = K - 4; k >= 1; --k) {
             // b_k (in B[(K-2-k)&1], over b_{k+2}) = c_k psi + A b_{k+1} - b_{k+2}
-            p.x = B[(K - 3 - k) & 1];
-            p.y = B[(K - 2 - k) & 1];
+            p.x = Bv[(K - 3 - k) & 1];
+            p.y = Bv[(K - 2 - k) & 1];
             p.z = p.y;
             p.ia = k; p.ib = -1; p.ic = -1; p.bscale = 1.0;
-            CU(launch_sweep(v, SW_MID, (k & 1) != 0, true, p, grid, s));
+            CU(sweep(SW_MID, (k & 1) != 0, true, p));
             ++*launches;
         }
         // FINAL: psi <- (c_0 - [K=3] c_2) psi + A b_1 / 2 - [K>=4] b_2, with <psi0|psi>
-        p.x = B[(K - 3) & 1];
-        p.z = K >= 4 ? B[(K - 4) & 1] : nullptr;
+        p.x = Bv[(K - 3) & 1];
+        p.z = K >= 4 ? Bv[(K - 4) & 1] : nullptr;
         p.y = ctx->d_psi;
         p.ia = 0; p.ib = K == 3 ? 2 : -1; p.ic = -1; p.bscale = 0.5;
         p.delta = d;
-        CU(launch_sweep(v, SW_FINAL, false, K >= 4, p, grid, s));
+        CU(sweep(SW_FINAL, false, K >= 4, p));
         ++*launches;
+        if (renorm) {   // 1/||psi(t_{n+1})|| for the next step's sweeps
+            if (B == 1)
+                CU(launch_renorm_seg(ctx->d_norm + (int64_t)d * p.nslices, p.nslices, ctx->d_seg_off, nseg,
+                                     ctx->d_scale, s));
+            else
+                CU(launch_renorm(ctx->d_norm + (int64_t)d * p.nblk * B, p.nblk, B, ctx->d_scale, s));
+            ++*launches;
+        }
     }
-    CU(launch_reduce(ctx->d_partials, len, 1, ctx->nblk, ctx->d_counter, 1, ctx->d_out, s));
+    if (B == 1)
+        CU(launch_reduce_seg(ctx->d_partials, len, 1, p.nslices, ctx->d_seg_off, nseg, ctx->d_counter, 1,
+                             ctx->d_out, ld, s));
+    else CU(launch_reduce_b16(ctx->d_partials, len, ctx->nblk16, ctx->d_counter, 1, ctx->d_out, ld, s));
     CU(launch_advance(ctx->d_counter, len, s));
     *launches += 2;
     return TBPM_OK;
@@ -443,23 +482,26 @@ int enqueue_kpm_chunk(tbpm_ctx *ctx, int len, cudaStream_t s, int64_t *launches)
         CU(launch_kpm(v, p, ctx->nblk, s));
         ++*launches;
     }
-    CU(launch_reduce(ctx->d_partials, len, 2, ctx->nblk, ctx->d_counter, 1, ctx->d_out, s));
+    CU(launch_reduce_seg(ctx->d_partials, len, 2, p.nslices, nullptr, 1, ctx->d_counter, 1, ctx->d_out,
+                         0, s));
     CU(launch_advance(ctx->d_counter, len, s));
     *launches += 2;
     return TBPM_OK;
 }
 
 // Runs (and on first use captures) the graph of one chunk.
-int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches)
+int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_t ld = 0)
 {
-    const auto key = std::make_tuple(kind, len, K, 1);
+    // kind 0: DOS, one state; 1: KPM, one state; 2: DOS, 16 states; 3: DOS, batch of
+    // instances (ld = n_steps + 1 for kinds 2 and 3)
+    const auto key = std::make_tuple(kind, len, K, (int)ld);
     auto it = ctx->graphs.find(key);
     int64_t nl = 0;
     if (it == ctx->graphs.end()) {
         cudaGraph_t g;
         CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-        int rc = kind == 0 ? enqueue_dos_chunk(ctx, K, len, ctx->cap_stream, &nl)
-                           : enqueue_kpm_chunk(ctx, len, ctx->cap_stream, &nl);
+        int rc = kind == 1 ? enqueue_kpm_chunk(ctx, len, ctx->cap_stream, &nl)
+                           : enqueue_dos_chunk(ctx, K, len, kind == 2 ? 16 : 1, ld, ctx->cap_stream, &nl);
         cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
         if (rc) return rc;
         CU(e);
@@ -469,7 +511,8 @@ int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches)
         CU(ei);
         it = ctx->graphs.emplace(key, ex).first;
     } else {
-        nl = kind == 0 ? (int64_t)len * (K - 1) + 2 : (int64_t)len + 2;
+        nl = kind == 1 ? (int64_t)len + 2 : (int64_t)len * (K - 1) + 2;
+        if (kind != 1 && (ctx->flags & TBPM_F_RENORM)) nl += len;
     }
     CU(cudaGraphLaunch(it->second, ctx->stream));
     *launches += nl;
@@ -537,7 +580,8 @@ static int check_opts(const tbpm_opts *in, tbpm_opts *o)
     if (in) *o = *in;
     if (o->precision != TBPM_FP64 && o->precision != TBPM_FP32) return TBPM_ERR_ARG;
     if (o->path < TBPM_PATH_AUTO || o->path > TBPM_PATH_STENCIL) return TBPM_ERR_ARG;
-    if (o->flags & ~(unsigned)(TBPM_F_NO_HERMITIAN_CHECK | TBPM_F_FORCE_RESCALE | TBPM_F_RENORM))
+    if (o->flags & ~(unsigned)(TBPM_F_NO_HERMITIAN_CHECK | TBPM_F_FORCE_RESCALE | TBPM_F_RENORM |
+                               TBPM_F_NO_CLUSTER))
         return TBPM_ERR_ARG;
     if (o->bessel_tol == 0.0) o->bessel_tol = 1e-12;
     if (!(o->bessel_tol > 0.0 && o->bessel_tol < 1e-2)) return TBPM_ERR_ARG;
@@ -549,6 +593,7 @@ static int finish_create(tbpm_ctx *ctx, const tbpm_opts &o)
     int rc = init_device(ctx, o);
     if (rc) return rc;
     ctx->nblk = sweep_grid(variant(ctx, 1), ctx->num_sms);
+    ctx->nblk16 = sweep_grid_b16(ctx->num_sms);
     return TBPM_OK;
 }
 
@@ -673,48 +718,159 @@ void tbpm_destroy(tbpm_ctx *ctx)
     cudaFree(ctx->d_coef); cudaFree(ctx->d_K); cudaFree(ctx->d_counter);
     cudaFree(ctx->d_psi); cudaFree(ctx->d_b0); cudaFree(ctx->d_b1); cudaFree(ctx->d_psi0);
     cudaFree(ctx->d_partials); cudaFree(ctx->d_out); cudaFree(ctx->d_stage); cudaFree(ctx->d_misc);
+    cudaFree(ctx->d_norm); cudaFree(ctx->d_scale);
+    cudaFree(ctx->d_slice_inst); cudaFree(ctx->d_seg_off); cudaFree(ctx->d_cpart);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     cudaGetLastError();
     delete ctx;
 }
 
-int tbpm_dos_corr(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, int n_steps,
-                  double *corr)
+// Time evolution of nstates states: C(t_n) into corr and/or psi(t_{n_steps})
+// into psi_out (either may be null, not both).
+static int run_dos(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, int n_steps,
+                   double *corr, double *psi_out)
 {
-    if (!ctx || !psi0 || !corr || nstates < 1 || n_steps < 0) return TBPM_ERR_ARG;
+    if (!ctx || !psi0 || (!corr && !psi_out) || nstates < 1 || n_steps < 0) return TBPM_ERR_ARG;
+    if (ctx->ninst > 0) return TBPM_ERR_UNSUPPORTED;
     if (!(dt != 0.0) || !std::isfinite(dt)) return TBPM_ERR_ARG;
     const double x = dt * ctx->rescale;
     if (!(std::fabs(x) <= 40.0)) return TBPM_ERR_ARG;
     CU(cudaSetDevice(ctx->device));
-    bool in_dev, out_dev;
+    bool in_dev, out_dev = true, psi_dev = true;
     int rc;
-    if ((rc = classify(ctx, psi0, &in_dev)) || (rc = classify(ctx, corr, &out_dev))) return rc;
+    if ((rc = classify(ctx, psi0, &in_dev)) || (corr && (rc = classify(ctx, corr, &out_dev))) ||
+        (psi_out && (rc = classify(ctx, psi_out, &psi_dev))))
+        return rc;
+    const bool renorm = (ctx->flags & TBPM_F_RENORM) != 0;
+    // copies state `col` of an interleaved buffer to psi_out (state j)
+    auto store = [&](int B, int col, int j) -> int {
+        double *dst = psi_out + (size_t)2 * ctx->n * j;
+        double *d = psi_dev ? dst : ctx->d_stage;
+        CU(launch_store_column(ctx->precision, ctx->d_psi, ctx->n, B, col, renorm ? ctx->d_scale : nullptr, d,
+                               ctx->stream));
+        if (!psi_dev) {
+            CU(cudaMemcpyAsync(dst, d, sizeof(double2) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+            CU(cudaStreamSynchronize(ctx->stream));
+        }
+        return TBPM_OK;
+    };
     int K;
     if ((rc = ensure_coeffs(ctx, x, &K))) return rc;
     const int Ke = std::max(K, 3);
     const int64_t n = ctx->n;
-    if ((rc = ensure_work(ctx, 1, (size_t)n_steps + 1, in_dev ? 0 : (size_t)2 * n))) return rc;
     int64_t launches = 0;
+    if (ctx->precision == TBPM_FP32 && nstates > 1) {
+        // blocks of 16 states advance together; missing states of the last
+        // block are zero vectors, which stay zero
+        const int B = kMaxBlockStates;
+        const int64_t ld = (int64_t)n_steps + 1;
+        if ((rc = ensure_work(ctx, B, (size_t)B * ld, (in_dev && psi_dev) ? 0 : (size_t)2 * n))) return rc;
+        const size_t vb = vec_bytes(ctx->precision) * (size_t)ctx->n_pad * B;
+        for (int j0 = 0; j0 < nstates; j0 += B) {
+            const int nb = std::min(B, nstates - j0);
+            if (in_dev) {
+                CU(launch_load_states(ctx->precision, psi0, n, ctx->n_pad, nstates, j0, B, ctx->d_psi0,
+                                      ctx->d_psi, ctx->stream));
+                ++launches;
+            } else {
+                CU(cudaMemsetAsync(ctx->d_psi0, 0, vb, ctx->stream));
+                CU(cudaMemsetAsync(ctx->d_psi, 0, vb, ctx->stream));
+                for (int q = 0; q < nb; ++q) {
+                    const double *src;
+                    if ((rc = stage_input(ctx, psi0 + (size_t)2 * n * (j0 + q), false, (size_t)2 * n, &src)))
+                        return rc;
+                    CU(launch_load_column(ctx->precision, src, n, B, q, ctx->d_psi0, ctx->d_psi, ctx->stream));
+                    CU(cudaStreamSynchronize(ctx->stream));        // staging reuse
+                    ++launches;
+                }
+            }
+            CU(launch_dot_b16(ctx->d_psi0, ctx->d_psi0, ctx->n_pad / kSlice, ctx->d_partials, ctx->nblk16,
+                              ctx->stream));
+            CU(launch_reduce_b16(ctx->d_partials, 1, ctx->nblk16, nullptr, 0, ctx->d_out, ld, ctx->stream));
+            CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
+            launches += 2;
+            if (ctx->flags & TBPM_F_RENORM) {
+                CU(launch_renorm(nullptr, 0, B, ctx->d_scale, ctx->stream));
+                ++launches;
+            }
+            int done = 0;
+            while (done < n_steps) {
+                const int len = std::min(kChunk, n_steps - done);
+                if ((rc = run_chunk(ctx, 2, Ke, len, &launches, ld))) return rc;
+                done += len;
+            }
+            if (corr) {
+                CU(cudaMemcpyAsync(corr + (size_t)2 * ld * j0, ctx->d_out, sizeof(double2) * ld * nb,
+                                   out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+                if (!out_dev) CU(cudaStreamSynchronize(ctx->stream));
+            }
+            if (psi_out)
+                for (int q = 0; q < nb; ++q)
+                    if ((rc = store(B, q, j0 + q))) return rc;
+        }
+        if (!out_dev || !in_dev) CU(cudaStreamSynchronize(ctx->stream));
+        CU(cudaGetLastError());
+        ctx->last_K = Ke;
+        ctx->last_passes = (int64_t)((nstates + B - 1) / B) * n_steps * (Ke - 1);
+        ctx->last_launches = launches;
+        return TBPM_OK;
+    }
+    if ((rc = ensure_work(ctx, 1, (size_t)n_steps + 1, (in_dev && psi_dev) ? 0 : (size_t)2 * n))) return rc;
+    int clr, cnc;
+    size_t csm;
+    const bool use_cluster = ctx->op == OP_SELL && !(ctx->flags & (TBPM_F_NO_CLUSTER | TBPM_F_RENORM)) &&
+                             cluster_fits(ctx->precision, ctx->n_pad, &clr, &cnc, &csm);
     for (int j = 0; j < nstates; ++j) {
         const double *src;
         if ((rc = stage_input(ctx, psi0 + (size_t)2 * n * j, in_dev, (size_t)2 * n, &src))) return rc;
         CU(launch_load_states(ctx->precision, src, n, ctx->n_pad, 1, 0, 1, ctx->d_psi0, ctx->d_psi,
                               ctx->stream));
-        CU(launch_dot(ctx->precision, ctx->d_psi0, ctx->d_psi0, ctx->n_pad, ctx->d_partials, ctx->nblk,
+        CU(launch_dot(ctx->precision, ctx->d_psi0, ctx->d_psi0, ctx->n_pad / kSlice, ctx->d_partials, ctx->nblk,
                       ctx->stream));
-        CU(launch_reduce(ctx->d_partials, 1, 1, ctx->nblk, nullptr, 0, ctx->d_out, ctx->stream));
+        CU(launch_reduce_seg(ctx->d_partials, 1, 1, ctx->n_pad / kSlice, nullptr, 1, nullptr, 0, ctx->d_out,
+                             0, ctx->stream));
         CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
         launches += 3;
-        int done = 0;
-        while (done < n_steps) {
-            const int len = std::min(kChunk, n_steps - done);
-            if ((rc = run_chunk(ctx, 0, Ke, len, &launches))) return rc;
-            done += len;
+        if (ctx->flags & TBPM_F_RENORM) {
+            CU(launch_renorm(nullptr, 0, 1, ctx->d_scale, ctx->stream));
+            ++launches;
         }
-        double *dst = corr + (size_t)2 * (n_steps + 1) * j;
-        CU(cudaMemcpyAsync(dst, ctx->d_out, sizeof(double2) * (n_steps + 1),
-                           out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+        int lr, ncta;
+        size_t smem;
+        const int64_t nsl = ctx->n_pad / kSlice;
+        if (use_cluster && n_steps > 0) {
+            // whole evolution in one launch of one cluster, then one reduction
+            const size_t need = (size_t)n_steps * nsl;
+            if (need > ctx->cpart_cap) {
+                cudaFree(ctx->d_cpart);
+                ctx->d_cpart = nullptr;
+                ctx->cpart_cap = 0;
+                CU(cudaMalloc(&ctx->d_cpart, need * sizeof(double2)));
+                ctx->cpart_cap = need;
+            }
+            SweepParams op;
+            fill_operator(ctx, op);
+            CU(launch_cluster_dos(ctx->precision, ctx->sell.real_values, op, ctx->d_psi0, ctx->d_coef, Ke,
+                                  n_steps, ctx->d_cpart, psi_out ? ctx->d_psi : nullptr, ctx->stream));
+            CU(launch_reduce_seg(ctx->d_cpart, n_steps, 1, nsl, nullptr, 1, nullptr, 1, ctx->d_out, 0,
+                                 ctx->stream));
+            launches += 2;
+        } else {
+            int done = 0;
+            while (done < n_steps) {
+                const int len = std::min(kChunk, n_steps - done);
+                if ((rc = run_chunk(ctx, 0, Ke, len, &launches))) return rc;
+                done += len;
+            }
+        }
+        (void)lr; (void)ncta; (void)smem;
+        if (corr) {
+            double *dst = corr + (size_t)2 * (n_steps + 1) * j;
+            CU(cudaMemcpyAsync(dst, ctx->d_out, sizeof(double2) * (n_steps + 1),
+                               out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        if (psi_out && (rc = store(1, 0, j))) return rc;
         if (!in_dev && nstates > 1) CU(cudaStreamSynchronize(ctx->stream));  // staging reuse
     }
     if (!out_dev || !in_dev) CU(cudaStreamSynchronize(ctx->stream));
@@ -725,9 +881,24 @@ int tbpm_dos_corr(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, int
     return TBPM_OK;
 }
 
+int tbpm_dos_corr(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, int n_steps,
+                  double *corr)
+{
+    if (!corr) return TBPM_ERR_ARG;
+    return run_dos(ctx, psi0, nstates, dt, n_steps, corr, nullptr);
+}
+
+int tbpm_propagate(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, int n_steps,
+                   double *psi_out, double *corr)
+{
+    if (!psi_out) return TBPM_ERR_ARG;
+    return run_dos(ctx, psi0, nstates, dt, n_steps, corr, psi_out);
+}
+
 int kpm_moments(tbpm_ctx *ctx, const double *psi0, int nstates, int M, double *mu)
 {
     if (!ctx || !psi0 || !mu || nstates < 1 || M < 1) return TBPM_ERR_ARG;
+    if (ctx->ninst > 0) return TBPM_ERR_UNSUPPORTED;
     CU(cudaSetDevice(ctx->device));
     bool in_dev, out_dev;
     int rc;
@@ -753,7 +924,8 @@ int kpm_moments(tbpm_ctx *ctx, const double *psi0, int nstates, int M, double *m
         p.x = ctx->d_psi; p.y = ctx->d_b0; p.scale = 0.5; p.first = true;
         p.partials = ctx->d_partials; p.delta = 0; p.nblk = ctx->nblk;
         CU(launch_kpm(v, p, ctx->nblk, ctx->stream));
-        CU(launch_reduce(ctx->d_partials, 1, 2, ctx->nblk, nullptr, 0, ctx->d_out, ctx->stream));
+        CU(launch_reduce_seg(ctx->d_partials, 1, 2, ctx->n_pad / kSlice, nullptr, 1, nullptr, 0, ctx->d_out,
+                             0, ctx->stream));
         CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
         launches += 3;
         int done = 0;
@@ -828,6 +1000,171 @@ int kpm_dos_jackson(tbpm_ctx *ctx, const double *mu, int M, int n_e, double *ene
     if (!r_dev) CU(cudaMemcpyAsync(rho_out, dr, n_e * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (!in_dev || !e_dev || !r_dev) CU(cudaStreamSynchronize(ctx->stream));
     ctx->last_launches = 1;
+    return TBPM_OK;
+}
+
+int tbpm_create_batch(tbpm_ctx **out, int ninst, const tbpm_instance *inst, const tbpm_opts *opts)
+{
+    if (!out) return TBPM_ERR_ARG;
+    *out = nullptr;
+    if (ninst < 1 || ninst > 4096 || !inst) return TBPM_ERR_ARG;
+    tbpm_opts o;
+    int rc = check_opts(opts, &o);
+    if (rc) return rc;
+    if (o.path == TBPM_PATH_STENCIL) return TBPM_ERR_ARG;
+    // validate every instance, then assemble the block-diagonal operator
+    HostMatrix all;
+    std::vector<int64_t> rows(ninst + 1, 0);
+    std::vector<double> row_scale;
+    double gmax = 0.0, rmax = 0.0;
+    try {
+        for (int g = 0; g < ninst; ++g) {
+            const tbpm_instance &I = inst[g];
+            if (I.n < 1 || !I.row_ptr || (I.row_ptr[I.n] > 0 && (!I.col || !I.val))) return TBPM_ERR_ARG;
+            if (!(I.rescale > 0.0) || !std::isfinite(I.rescale)) return TBPM_ERR_ARG;
+            rows[g + 1] = rows[g] + (I.n + kSlice - 1) / kSlice * kSlice;
+            if (rows[g + 1] >= ((int64_t)1 << 31) - kSlice) return TBPM_ERR_ARG;
+        }
+        const int64_t ntot = rows[ninst];
+        all.n = ntot;
+        all.rp.assign(ntot + 1, 0);
+        all.diag.assign(ntot, 0.0);
+        all.real_values = true;
+        row_scale.assign(ntot, 0.0);
+        for (int g = 0; g < ninst; ++g) {
+            const tbpm_instance &I = inst[g];
+            HostMatrix m;
+            rc = build_host_matrix(I.n, I.row_ptr, I.col, I.val, !(o.flags & TBPM_F_NO_HERMITIAN_CHECK), m);
+            if (rc) return rc;
+            if (m.gershgorin > I.rescale && !(o.flags & TBPM_F_FORCE_RESCALE)) return TBPM_ERR_RESCALE;
+            gmax = std::max(gmax, m.gershgorin);
+            rmax = std::max(rmax, I.rescale);
+            all.real_values = all.real_values && m.real_values;
+            const int64_t r0 = rows[g];
+            for (int64_t i = 0; i < rows[g + 1] - r0; ++i) {
+                const int64_t r = r0 + i;
+                if (i < I.n) {
+                    for (int64_t q = m.rp[i]; q < m.rp[i + 1]; ++q) {
+                        all.col.push_back((int32_t)(m.col[q] + r0));
+                        all.re.push_back(m.re[q]);
+                        all.im.push_back(m.im[q]);
+                    }
+                    all.diag[r] = m.diag[i];
+                }
+                all.rp[r + 1] = (int64_t)all.col.size();
+                row_scale[r] = 2.0 / I.rescale;
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        return TBPM_ERR_OOM;
+    }
+    tbpm_ctx *ctx = new (std::nothrow) tbpm_ctx;
+    if (!ctx) return TBPM_ERR_OOM;
+    ctx->precision = o.precision;
+    ctx->path = TBPM_PATH_SELL;
+    ctx->flags = o.flags;
+    ctx->tol = o.bessel_tol;
+    ctx->n = rows[ninst];
+    ctx->n_pad = rows[ninst];
+    ctx->rescale = rmax;
+    ctx->gershgorin = gmax;
+    ctx->ninst = ninst;
+    ctx->inst_row = rows;
+    for (int g = 0; g < ninst; ++g) {
+        ctx->inst_n.push_back(inst[g].n);
+        ctx->inst_rescale.push_back(inst[g].rescale);
+    }
+    if ((rc = finish_create(ctx, o)) || (rc = setup_sell(ctx, all, &row_scale))) {
+        tbpm_destroy(ctx);
+        return rc;
+    }
+    // slice -> instance map and the slice range of each instance
+    const int64_t nsl = ctx->n_pad / kSlice;
+    std::vector<int32_t> sinst(nsl);
+    std::vector<int64_t> seg(ninst + 1);
+    for (int g = 0; g <= ninst; ++g) seg[g] = rows[g] / kSlice;
+    for (int g = 0; g < ninst; ++g)
+        for (int64_t q = seg[g]; q < seg[g + 1]; ++q) sinst[q] = g;
+    if ((rc = upload(ctx, (void **)&ctx->d_slice_inst, sinst)) || (rc = upload(ctx, (void **)&ctx->d_seg_off, seg))) {
+        tbpm_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return TBPM_OK;
+}
+
+int tbpm_batch_dos_corr(tbpm_ctx *ctx, const double *psi0, const double *dt, int n_steps, double *corr)
+{
+    if (!ctx || !psi0 || !dt || !corr || n_steps < 0) return TBPM_ERR_ARG;
+    if (ctx->ninst < 1) return TBPM_ERR_UNSUPPORTED;
+    const int G = ctx->ninst;
+    for (int g = 0; g < G; ++g) {
+        if (!(dt[g] != 0.0) || !std::isfinite(dt[g])) return TBPM_ERR_ARG;
+        if (!(std::fabs(dt[g] * ctx->inst_rescale[g]) <= 40.0)) return TBPM_ERR_ARG;
+    }
+    CU(cudaSetDevice(ctx->device));
+    bool in_dev, out_dev;
+    int rc;
+    if ((rc = classify(ctx, psi0, &in_dev)) || (rc = classify(ctx, corr, &out_dev))) return rc;
+    int64_t launches = 0;
+    // per-instance coefficients (read back K once per set of time steps)
+    if (ctx->dt_cached.size() != (size_t)G || !std::equal(ctx->dt_cached.begin(), ctx->dt_cached.end(), dt)) {
+        for (int g = 0; g < G; ++g)
+            CU(launch_bessel(dt[g] * ctx->inst_rescale[g], ctx->tol, ctx->d_coef + (int64_t)g * kMaxTerms,
+                             ctx->d_K + g, ctx->stream));
+        CU(launch_mask_coef(ctx->d_coef, ctx->d_K, G, ctx->stream));
+        std::vector<int> K(G);
+        CU(cudaMemcpyAsync(K.data(), ctx->d_K, sizeof(int) * G, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        int Kmax = 3;
+        for (int g = 0; g < G; ++g) {
+            if (K[g] < 1) return TBPM_ERR_ARG;
+            Kmax = std::max(Kmax, K[g]);
+        }
+        ctx->K_batch = Kmax;
+        ctx->dt_cached.assign(dt, dt + G);
+        launches += G + 1;
+    }
+    const int Ke = ctx->K_batch;
+    const int64_t ld = (int64_t)n_steps + 1;
+    int64_t nmax = 0;
+    for (int g = 0; g < G; ++g) nmax = std::max(nmax, ctx->inst_n[g]);
+    if ((rc = ensure_work(ctx, 1, (size_t)G * ld, in_dev ? 0 : (size_t)2 * nmax))) return rc;
+    const size_t vb = vec_bytes(ctx->precision);
+    int64_t src_off = 0;
+    for (int g = 0; g < G; ++g) {
+        const double *src;
+        if ((rc = stage_input(ctx, psi0 + 2 * src_off, in_dev, (size_t)2 * ctx->inst_n[g], &src))) return rc;
+        char *d0 = static_cast<char *>(ctx->d_psi0) + vb * ctx->inst_row[g];
+        char *d1 = static_cast<char *>(ctx->d_psi) + vb * ctx->inst_row[g];
+        CU(launch_load_states(ctx->precision, src, ctx->inst_n[g], ctx->inst_row[g + 1] - ctx->inst_row[g], 1, 0,
+                              1, d0, d1, ctx->stream));
+        if (!in_dev) CU(cudaStreamSynchronize(ctx->stream));        // staging reuse
+        src_off += ctx->inst_n[g];
+        ++launches;
+    }
+    const int64_t nsl = ctx->n_pad / kSlice;
+    CU(launch_dot(ctx->precision, ctx->d_psi0, ctx->d_psi0, nsl, ctx->d_partials, ctx->nblk, ctx->stream));
+    CU(launch_reduce_seg(ctx->d_partials, 1, 1, nsl, ctx->d_seg_off, G, nullptr, 0, ctx->d_out, ld, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
+    launches += 2;
+    if (ctx->flags & TBPM_F_RENORM) {
+        CU(launch_fill(ctx->d_scale, G, 1.0, ctx->stream));
+        ++launches;
+    }
+    int done = 0;
+    while (done < n_steps) {
+        const int len = std::min(kChunk, n_steps - done);
+        if ((rc = run_chunk(ctx, 3, Ke, len, &launches, ld))) return rc;
+        done += len;
+    }
+    CU(cudaMemcpyAsync(corr, ctx->d_out, sizeof(double2) * ld * G,
+                       out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (!out_dev || !in_dev) CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaGetLastError());
+    ctx->last_K = Ke;
+    ctx->last_passes = (int64_t)n_steps * (Ke - 1);
+    ctx->last_launches = launches;
     return TBPM_OK;
 }
 

@@ -72,6 +72,14 @@ struct SweepParams {
     double2 *partials;
     int delta;
     int nblk;
+    // optional renormalisation: psi is read as scale[j] * psi for state j
+    // (nullptr: no scaling); the final sweep writes sum |y|^2 partials to
+    // norm_partials[(delta * nblk + block) * B + j] (nullptr: none)
+    const double *scale;
+    double2 *norm_partials;
+    // batch of instances: instance of each slice (nullptr: one instance);
+    // coefficients of instance g at coef + g * kMaxTerms, its scale at scale[g]
+    const int32_t *slice_inst;
 };
 
 // KPM sweep: T_{m+1} = 2 H~ T_m - T_{m-1} with <T_m|T_m> and <T_{m+1}|T_m>.
@@ -123,8 +131,9 @@ struct tbpm_ctx {
     tbpm::Sell sell;
     tbpm::Stencil sten;
     int64_t nnz = 0;
-    // sweep grid (fixed per context so the dot partials are deterministic)
-    int nblk = 0;
+    // sweep grids (fixed per context so the dot partials are deterministic)
+    int nblk = 0;                    // single-state kernels
+    int nblk16 = 0;                  // 16-state kernels
     // coefficients
     double2 *d_coef = nullptr;       // [kMaxTerms]
     int *d_K = nullptr;
@@ -141,6 +150,19 @@ struct tbpm_ctx {
     size_t stage_cap = 0;
     int *d_counter = nullptr;        // chunk base counter for graphs
     double *d_misc = nullptr;        // small scratch (norms, moment bases)
+    double *d_scale = nullptr;       // [16] 1/||psi_j|| for the renormalised FP32 path
+    double2 *d_norm = nullptr;       // [kChunk][nblk][B] ||y||^2 partials (renormalisation)
+    double2 *d_cpart = nullptr;      // [n_steps][nslices] partials of the cluster path
+    size_t cpart_cap = 0;
+    // batch of instances (tbpm_create_batch); ninst == 0 for a single instance
+    int ninst = 0;
+    std::vector<int64_t> inst_n;         // orbitals of each instance
+    std::vector<int64_t> inst_row;       // first (padded) row of each instance, size ninst+1
+    std::vector<double> inst_rescale;
+    int32_t *d_slice_inst = nullptr;     // instance of each slice
+    int64_t *d_seg_off = nullptr;        // first slice of each instance, size ninst+1
+    std::vector<double> dt_cached;
+    int K_batch = 0;                     // max over instances of max(K_g, 3)
     // cached executable graphs keyed by (kind, len, K, states)
     std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
     // counters of the last call
@@ -166,9 +188,9 @@ cudaError_t launch_sweep(const SweepVariant &v, SweepKind kind, bool a_imag, boo
 // KPM sweep (cheb_sweep.cu).
 cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cudaStream_t s);
 
-// <a|b> = sum_i conj(a_i) b_i as per-block partials over `rows` rows of one
-// state, written to partials[0..grid) (aux.cu).
-cudaError_t launch_dot(int precision, const void *a, const void *b, int64_t rows,
+// <a|b> = sum_i conj(a_i) b_i of one state, one partial per 32-row slice
+// (partials[s], s < nslices) (aux.cu).
+cudaError_t launch_dot(int precision, const void *a, const void *b, int64_t nslices,
                        double2 *partials, int grid, cudaStream_t s);
 
 // Deterministic reduction of per-block partials laid out [nslot][nterm][nblk]:
@@ -176,6 +198,32 @@ cudaError_t launch_dot(int precision, const void *a, const void *b, int64_t rows
 // with base = *counter (0 when counter is nullptr) (aux.cu).
 cudaError_t launch_reduce(const double2 *partials, int nslot, int nterm, int nblk,
                           const int *counter, int offset, double2 *out, cudaStream_t s);
+
+// Segmented fixed-order reduction of per-slice partials [nslot][nterm][nslices]:
+//   out[g * ld + (base + offset + d) * nterm + q] = sum over slices of segment g,
+// segments [seg_off[g], seg_off[g+1]) (seg_off == nullptr: one segment) (aux.cu).
+cudaError_t launch_reduce_seg(const double2 *partials, int nslot, int nterm, int64_t nslices,
+                              const int64_t *seg_off, int nseg, const int *counter, int offset,
+                              double2 *out, int64_t ld, cudaStream_t s);
+// scale[g] = 1/sqrt(sum of norm[s].x over segment g) (aux.cu).
+cudaError_t launch_renorm_seg(const double2 *norm, int64_t nslices, const int64_t *seg_off, int nseg,
+                              double *scale, cudaStream_t s);
+cudaError_t launch_fill(double *p, int n, double v, cudaStream_t s);
+// Single-launch cluster path for small systems (cheb_cluster.cu): whether n_pad
+// rows fit, and the launch of n_steps steps writing per-slice <psi0|psi>
+// partials [n_steps][nslices] and, if psi_out is not null, the final state.
+bool cluster_fits(int precision, int64_t n_pad, int *log_rows, int *ncta, size_t *smem);
+cudaError_t launch_cluster_dos(int precision, bool real_values, const SweepParams &op,
+                               const void *psi0, const double2 *coef, int K, int n_steps,
+                               double2 *partials, void *psi_out, cudaStream_t s);
+
+// dst (FP64 complex [n]) = scale[col] * column col of an interleaved [n_pad][B]
+// buffer (scale may be null) (aux.cu).
+cudaError_t launch_store_column(int precision, const void *src, int64_t n, int B, int col,
+                                const double *scale, double *dst, cudaStream_t s);
+
+// coef[g * kMaxTerms + k] = 0 for k >= max(K[g], 3) (aux.cu).
+cudaError_t launch_mask_coef(double2 *coef, const int *K, int ninst, cudaStream_t s);
 cudaError_t launch_advance(int *counter, int by, cudaStream_t s);
 
 // State layout conversion: src FP64 complex state-major [nstates][n] ->
@@ -183,6 +231,12 @@ cudaError_t launch_advance(int *counter, int by, cudaStream_t s);
 cudaError_t launch_load_states(int precision, const double *src, int64_t n, int64_t n_pad,
                                int nstates_src, int j0, int B, void *dst0, void *dst1,
                                cudaStream_t s);
+
+// scale[j] = 1 / sqrt(sum_b norm_partials[b * B + j].x) for j < B, from one
+// slot of final-sweep norm partials; with norm_partials == nullptr, scale[j] = 1
+// (aux.cu).
+cudaError_t launch_renorm(const double2 *norm_partials, int nblk, int B, double *scale,
+                          cudaStream_t s);
 
 // KPM moments from the reduced dot products (aux.cu).
 cudaError_t launch_kpm_finalize(const double2 *dots, int M, int states, double2 *mu,
@@ -196,5 +250,21 @@ cudaError_t launch_kpm_dos(const double2 *mu, int M, int n_e, double rescale, do
 
 // Block count of the sweep kernels at full occupancy (cheb_sweep.cu).
 int sweep_grid(const SweepVariant &v, int num_sms);
+
+// Batched FP32 sweeps over 16 interleaved states (cheb_batch.cu).
+cudaError_t launch_sweep_b16(const SweepVariant &v, SweepKind kind, bool a_imag, bool has_z,
+                             const SweepParams &p, int grid, cudaStream_t s);
+// <a_j|b_j> partials [grid][16] over nslices 32-row slices.
+cudaError_t launch_dot_b16(const void *a, const void *b, int64_t nslices, double2 *partials,
+                           int grid, cudaStream_t s);
+// out[j * ld + base + offset + d] = sum_b partials[(d * nblk + b) * 16 + j].
+cudaError_t launch_reduce_b16(const double2 *partials, int nslot, int nblk, const int *counter,
+                              int offset, double2 *out, int64_t ld, cudaStream_t s);
+int sweep_grid_b16(int num_sms);
+
+// One FP64 state (device, [n] complex) into column `col` of an interleaved
+// [n_pad][B] buffer of the given precision, in both dst0 and dst1 (aux.cu).
+cudaError_t launch_load_column(int precision, const double *src, int64_t n, int B, int col,
+                               void *dst0, void *dst1, cudaStream_t s);
 
 }  // namespace tbpm

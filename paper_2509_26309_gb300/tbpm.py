@@ -35,6 +35,7 @@ TBPM_PATH_STENCIL = 2
 TBPM_F_NO_HERMITIAN_CHECK = 0x1
 TBPM_F_FORCE_RESCALE = 0x2
 TBPM_F_RENORM = 0x4
+TBPM_F_NO_CLUSTER = 0x8
 TBPM_LATTICE_GRAPHENE = 0
 TBPM_LATTICE_AB_BILAYER = 1
 
@@ -77,7 +78,16 @@ SIGNATURES = {
     "kpm_dos_jackson": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "tbpm_get_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tbpm_strerror": (C.c_char_p, [C.c_int]),
+    "tbpm_propagate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p,
+                                 C.c_void_p]),
+    "tbpm_create_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "tbpm_batch_dos_corr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
 }
+
+
+class tbpm_instance(C.Structure):
+    _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
+                ("rescale", C.c_double)]
 
 
 def lib(build_if_missing: bool = True) -> C.CDLL:
@@ -209,6 +219,37 @@ def tbpm_create_lattice(kind: int, l1: int, l2: int, t: float, t_perp: float = 0
     return Ctx(h, n, opts.device if opts is not None else -1)
 
 
+def tbpm_create_batch(instances, opts: tbpm_opts | None = None) -> Ctx:
+    """One context for a list of (csr, rescale) instances; csr has n, row_ptr, col, val."""
+    keep = []
+    arr = (tbpm_instance * len(instances))()
+    for g, (h, rescale) in enumerate(instances):
+        rp = np.ascontiguousarray(h.row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(h.col, dtype=np.int32)
+        val = np.ascontiguousarray(h.val, dtype=np.complex128)
+        keep += [rp, col, val]
+        arr[g] = tbpm_instance(int(h.n), rp.ctypes.data, col.ctypes.data, val.ctypes.data, float(rescale))
+    hnd = C.c_void_p()
+    _check(lib().tbpm_create_batch(C.byref(hnd), len(instances), arr,
+                                   C.byref(opts) if opts is not None else None), "tbpm_create_batch")
+    ctx = Ctx(hnd, int(sum(h.n for h, _ in instances)), opts.device if opts is not None else -1)
+    ctx.inst_n = [int(h.n) for h, _ in instances]
+    return ctx
+
+
+def tbpm_batch_dos_corr(ctx: Ctx, psi0, dt, n_steps: int, out=None):
+    """C_g(t_n) for every instance g: shape (ninst, n_steps+1). psi0 is the
+    concatenation of the instances' states (complex128, sum n_g entries)."""
+    a, ns, cuda = _complex_in(psi0, ctx.n)
+    g = len(ctx.inst_n)
+    dt = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (g,)))
+    if out is None:
+        out = _alloc((g, n_steps + 1), np.complex128, cuda, a.device if cuda else None)
+    _check(lib().tbpm_batch_dos_corr(ctx.handle, _ptr(a), dt.ctypes.data_as(C.c_void_p), int(n_steps),
+                                     _ptr(out)), "tbpm_batch_dos_corr")
+    return out
+
+
 def tbpm_destroy(ctx: Ctx) -> None:
     if ctx.handle:
         lib().tbpm_destroy(ctx.handle)
@@ -223,6 +264,20 @@ def tbpm_dos_corr(ctx: Ctx, psi0, dt: float, n_steps: int, out=None):
     _check(lib().tbpm_dos_corr(ctx.handle, _ptr(a), ns, float(dt), int(n_steps), _ptr(out)),
            "tbpm_dos_corr")
     return out[0] if (a.ndim == 1 and out.shape[0] == 1) else out
+
+
+def tbpm_propagate(ctx: Ctx, psi0, dt: float, n_steps: int, with_corr: bool = False):
+    """psi(t_{n_steps}) (same shape as psi0), and C(t_n) too when with_corr."""
+    a, ns, cuda = _complex_in(psi0, ctx.n)
+    dev = a.device if cuda else None
+    psi = _alloc((ns, ctx.n), np.complex128, cuda, dev)
+    corr = _alloc((ns, n_steps + 1), np.complex128, cuda, dev) if with_corr else None
+    _check(lib().tbpm_propagate(ctx.handle, _ptr(a), ns, float(dt), int(n_steps), _ptr(psi),
+                                _ptr(corr) if corr is not None else None), "tbpm_propagate")
+    if a.ndim == 1:
+        psi = psi[0]
+        corr = corr[0] if corr is not None else None
+    return (psi, corr) if with_corr else psi
 
 
 def kpm_moments(ctx: Ctx, psi0, M: int, out=None):

@@ -1,0 +1,100 @@
+"""FP32 paths (complex64 vectors and hoppings; FP64 coefficients and dot sums)
+against the FP64 oracle.
+
+FP32 results are not expected to equal FP64 ones. The bars, derived from the
+arithmetic: each sweep rounds every vector element once at 2^-24 relative, and
+a step makes K-1 = 17 sweeps whose rounding errors add up as a random walk
+over steps; over n steps the correlation error is about
+sqrt(17 n) * 2^-24 * O(1), i.e. ~1e-5 at n = 1024. The tests require
+|dC| <= 3e-5 (n <= 1024) and a DOS L1 relative error <= 1e-4 (the target
+stated for the mixed-precision path).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import tbpm_inputs as ti
+import paper_2509_26309_gb300 as tb
+
+pytestmark = pytest.mark.gpu
+DT = math.pi / 9
+C_TOL = 3e-5
+
+
+def dos_l1(orc, corr, ref, dt):
+    _, d, _ = orc.dos_hann(corr, dt)
+    _, dr, _ = orc.dos_hann(ref, dt)
+    return float(np.sum(np.abs(d - dr)) / np.sum(np.abs(dr)))
+
+
+def fp32(h, rescale=9.0):
+    return tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, rescale, tb.make_opts(precision=tb.TBPM_FP32))
+
+
+def test_fp32_single_state(orc):
+    h = ti.graphene_csr(64, 64, onsite=ti.anderson_onsite(8192, 1.0, 1))
+    psi0 = ti.random_phase_state(h.n, 0)
+    c = tb.tbpm_dos_corr(fp32(h), psi0, DT, 1024)
+    ref = orc.dos_corr(h, 9.0, psi0, DT, 1024)
+    assert np.max(np.abs(c - ref)) <= C_TOL
+    assert dos_l1(orc, c, ref, DT) <= 1e-4
+
+
+@pytest.mark.parametrize("nstates", [16, 3, 17])
+def test_fp32_batched_states(orc, nstates):
+    h = ti.graphene_csr(40, 36, onsite=ti.anderson_onsite(2880, 1.0, 2))
+    psi = ti.random_phase_block(h.n, nstates, seed0=0).T.copy()
+    ctx = fp32(h)
+    c = tb.tbpm_dos_corr(ctx, psi, DT, 300)
+    assert c.shape == (nstates, 301)
+    for j in range(nstates):
+        ref = orc.dos_corr(h, 9.0, psi[j], DT, 300)
+        assert np.max(np.abs(c[j] - ref)) <= C_TOL
+    assert dos_l1(orc, c[nstates - 1], orc.dos_corr(h, 9.0, psi[-1], DT, 300), DT) <= 1e-4
+
+
+def test_fp32_batched_complex_ragged(orc):
+    h = ti.random_hermitian_csr(999, 4, seed=5, scale=1.0)
+    rescale = 1.02 * ti.gershgorin_bound(h)
+    psi = ti.random_phase_block(h.n, 16, seed0=3).T.copy()
+    ctx = fp32(h, rescale)
+    c = tb.tbpm_dos_corr(ctx, psi, math.pi / rescale, 128)
+    for j in (0, 7, 15):
+        ref = orc.dos_corr(h, rescale, psi[j], math.pi / rescale, 128)
+        assert np.max(np.abs(c[j] - ref)) <= C_TOL
+
+
+@pytest.mark.parametrize("kind", [tb.TBPM_LATTICE_GRAPHENE, tb.TBPM_LATTICE_AB_BILAYER])
+def test_fp32_batched_stencil(orc, kind):
+    l1, l2 = 21, 19
+    per = 2 if kind == 0 else 4
+    n = per * l1 * l2
+    eps = ti.anderson_onsite(n, 1.0, 8)
+    h = ti.graphene_csr(l1, l2, onsite=eps) if kind == 0 else ti.bilayer_csr(l1, l2, onsite=eps)
+    rescale = max(9.0, 1.02 * ti.gershgorin_bound(h))
+    psi = ti.random_phase_block(n, 16, seed0=0).T.copy()
+    ctx = tb.tbpm_create_lattice(kind, l1, l2, -2.7, 0.39, eps, rescale, tb.make_opts(precision=tb.TBPM_FP32))
+    c = tb.tbpm_dos_corr(ctx, psi, math.pi / rescale, 200)
+    for j in (0, 9):
+        ref = orc.dos_corr(h, rescale, psi[j], math.pi / rescale, 200)
+        assert np.max(np.abs(c[j] - ref)) <= C_TOL
+
+
+def test_fp32_device_block(orc):
+    torch = pytest.importorskip("torch")
+    h = ti.graphene_csr(32, 32, onsite=ti.anderson_onsite(2048, 1.0, 4))
+    psi = ti.random_phase_block(h.n, 16, seed0=2).T.copy()
+    ctx = fp32(h)
+    dc = tb.tbpm_dos_corr(ctx, torch.from_numpy(psi).cuda(), DT, 64)
+    torch.cuda.synchronize()
+    hc = tb.tbpm_dos_corr(ctx, psi, DT, 64)
+    assert np.array_equal(dc.cpu().numpy(), hc)
+
+
+def test_fp32_kpm(orc):
+    h = ti.graphene_csr(30, 30, onsite=ti.anderson_onsite(1800, 1.0, 6))
+    psi0 = ti.random_phase_state(h.n, 1)
+    mu = tb.kpm_moments(fp32(h), psi0, 1024)
+    ref = orc.kpm_moments(h, 9.0, psi0, 1024)
+    assert np.max(np.abs(mu - ref)) <= 1e-4

@@ -36,6 +36,32 @@ def test_config1_pristine_64x64_full(orc):
     assert np.array_equal(c, c2)                      # deterministic reductions
 
 
+@pytest.mark.parametrize("maker,prec", [
+    (lambda: ti.graphene_csr(64, 64), tb.TBPM_FP64),
+    (lambda: ti.random_hermitian_csr(3000, 4, seed=4, scale=1.0), tb.TBPM_FP64),
+    (lambda: ti.bilayer_csr(64, 64, onsite=ti.anderson_onsite(16384, 1.0, 2)), tb.TBPM_FP64),
+    (lambda: ti.graphene_csr(100, 90, onsite=ti.anderson_onsite(18000, 1.0, 2)), tb.TBPM_FP32),
+])
+def test_cluster_path_matches_graph_path(orc, maker, prec):
+    """Small systems run all steps in one launch of one thread-block cluster; the
+    per-row arithmetic and the per-slice reduction are those of the graph path."""
+    h = maker()
+    rescale = max(9.0, 1.02 * ti.gershgorin_bound(h))
+    dt = math.pi / rescale
+    psi0 = ti.random_phase_state(h.n, 2)
+    a = tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, rescale, tb.make_opts(precision=prec))
+    b = tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, rescale,
+                       tb.make_opts(precision=prec, flags=tb.TBPM_F_NO_CLUSTER))
+    ca = tb.tbpm_dos_corr(a, psi0, dt, 300)
+    la = tb.tbpm_get_info(a)["kernel_launches"]
+    cb = tb.tbpm_dos_corr(b, psi0, dt, 300)
+    lb = tb.tbpm_get_info(b)["kernel_launches"]
+    assert la < 10 < lb                              # one cluster launch vs one per sweep
+    assert np.max(np.abs(ca - cb)) <= (1e-13 if prec == tb.TBPM_FP64 else 1e-6)
+    if prec == tb.TBPM_FP64:
+        assert np.max(np.abs(ca - orc.dos_corr(h, rescale, psi0, dt, 300))) <= TOL
+
+
 @pytest.mark.parametrize("n,steps", [(1, 5), (31, 40), (1000, 200), (4133, 64)])
 def test_ragged_complex_hermitian(orc, n, steps):
     h = ti.random_hermitian_csr(n, 3, seed=n, scale=1.5) if n > 1 else ti.graphene_csr(1, 1)
@@ -138,6 +164,33 @@ def test_stencil_matches_oracle(orc, kind, l1, l2, w):
         assert np.max(np.abs(c - ref)) <= TOL
         mu = tb.kpm_moments(ctx, psi0, 200)
         assert np.max(np.abs(mu - orc.kpm_moments(h, rescale, psi0, 200))) <= TOL
+
+
+@pytest.mark.parametrize("flags", [0, tb.TBPM_F_NO_CLUSTER])
+def test_propagate_wavefunction(orc, flags):
+    """psi(t_N) element by element (cluster path and graph path), with C(t_n)."""
+    h = ti.graphene_csr(20, 18, onsite=ti.anderson_onsite(720, 1.0, 3), bond_phases=[0.2, 0.4, 0.6])
+    psi0 = ti.random_phase_block(h.n, 2, seed0=5).T.copy()
+    ctx = create(h, flags=flags)
+    psi, corr = tb.tbpm_propagate(ctx, psi0, DT, 150, with_corr=True)
+    for j in range(2):
+        K, rc, rpsi = orc.propagate(h, 9.0, psi0[j], DT, 150, want_psi=True)
+        assert np.max(np.abs(psi[j] - rpsi)) <= TOL
+        assert np.max(np.abs(corr[j] - rc)) <= TOL
+
+
+def test_propagate_fp32_renorm_and_batched(orc):
+    h = ti.graphene_csr(30, 26, onsite=ti.anderson_onsite(1560, 1.0, 4))
+    psi0 = ti.random_phase_block(h.n, 16, seed0=0).T.copy()
+    for flags in (0, tb.TBPM_F_RENORM):
+        ctx = tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, 9.0,
+                             tb.make_opts(precision=tb.TBPM_FP32, flags=flags))
+        psi = tb.tbpm_propagate(ctx, psi0, DT, 400)
+        norms = np.linalg.norm(psi, axis=1)
+        if flags:
+            assert np.max(np.abs(norms - 1)) < 1e-6
+        _, _, rpsi = orc.propagate(h, 9.0, psi0[3], DT, 400, want_psi=True)
+        assert np.max(np.abs(psi[3] - rpsi)) < 1e-4
 
 
 def test_dos_transforms(orc):
