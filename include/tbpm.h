@@ -201,6 +201,37 @@ int tbpm_propagate(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, in
  *   psi0  as tbpm_dos_corr;  M >= 1. */
 int kpm_moments(tbpm_ctx *ctx, const double *psi0, int nstates, int M, double *mu);
 
+/* ------------------------------------------- allocation-free variant */
+
+/* Largest orbital count tbpm_dos_corr_noalloc accepts. */
+#define TBPM_NOALLOC_MAX_N 65536
+
+/* tbpm_dos_corr_noalloc: tbpm_dos_corr for one state without any device
+ * allocation. The paper has no counterpart to this call; it exists for
+ * callers that cannot call cudaMalloc: an application that owns a fixed,
+ * pre-planned device-memory budget and hands out every buffer itself, a
+ * plugin whose host forbids allocation after start-up, or code on a path
+ * where an allocation could block or fail at the wrong moment. Such a caller
+ * passes every input and the output as device memory it already owns; the
+ * working vectors live in one static device array of about 3.2 MB that the
+ * library reserves on every GPU it is loaded on, for the life of the process.
+ *   n        1 <= n <= TBPM_NOALLOC_MAX_N, else TBPM_ERR_UNSUPPORTED
+ *   row_ptr, col, val  DEVICE CSR as in tbpm_create (int64[n+1], int32[nnz],
+ *            complex double[nnz]); trusted as given (no structure, Hermiticity
+ *            or Gershgorin check: the matrix is not read on the host)
+ *   rescale  > 0;  psi0 DEVICE double[2n];  dt, n_steps as tbpm_dos_corr
+ *   corr     DEVICE double[2(n_steps+1)]: C(t_0..t_n_steps)
+ *   stream   cudaStream_t, or NULL for the legacy default stream
+ * The call blocks until the number of series terms is known (one 4-byte
+ * device-to-host read), then enqueues the sweeps on `stream` and returns;
+ * synchronise the stream before reading corr. Its first call on a device
+ * looks up the static array's device address, so make that first call before
+ * any stream capture. All calls share the array: calls that overlap on the
+ * GPU (other streams, threads or processes on the same device) race on it. */
+int tbpm_dos_corr_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                          const double *val, double rescale, const double *psi0, double dt,
+                          int n_steps, double *corr, void *stream);
+
 /* ------------------------------------------------------- DOS post-step */
 
 /* tbpm_dos_from_corr: the DOS from one correlation (Analyzer.calc_dos,

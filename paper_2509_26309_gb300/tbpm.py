@@ -82,7 +82,11 @@ SIGNATURES = {
                                  C.c_void_p]),
     "tbpm_create_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "tbpm_batch_dos_corr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "tbpm_dos_corr_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                        C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p]),
 }
+
+TBPM_NOALLOC_MAX_N = 65536
 
 
 class tbpm_instance(C.Structure):
@@ -248,6 +252,20 @@ def tbpm_batch_dos_corr(ctx: Ctx, psi0, dt, n_steps: int, out=None):
     _check(lib().tbpm_batch_dos_corr(ctx.handle, _ptr(a), dt.ctypes.data_as(C.c_void_p), int(n_steps),
                                      _ptr(out)), "tbpm_batch_dos_corr")
     return out
+
+
+def tbpm_dos_corr_noalloc(n: int, row_ptr, col, val, rescale: float, psi0, dt: float,
+                          n_steps: int, corr, stream=None) -> None:
+    """The allocation-free correlation call. Every array is a caller-owned CUDA
+    tensor (int64 row_ptr, int32 col, complex128 val, psi0 and corr); the call
+    allocates nothing and leaves corr to be read after the stream synchronises."""
+    for t in (row_ptr, col, val, psi0, corr):
+        if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
+            raise TypeError("tbpm_dos_corr_noalloc takes contiguous CUDA tensors")
+    s = None if stream is None else C.c_void_p(int(stream))
+    _check(lib().tbpm_dos_corr_noalloc(int(n), _ptr(row_ptr), _ptr(col), _ptr(val), float(rescale),
+                                       _ptr(psi0), float(dt), int(n_steps), _ptr(corr), s),
+           "tbpm_dos_corr_noalloc")
 
 
 def tbpm_destroy(ctx: Ctx) -> None:
