@@ -225,23 +225,37 @@ def run_ours(args, rank, world, local_rank):
     value = units / (ms_max / 1e3)
 
     # roofline of the dominant kernel family (the Clenshaw sweeps), measured
-    # over the timed region: DOS part time / sweeps; algorithmic bytes per row
-    # summed over the K-1 sweeps of one step (stored real matrix, FP64 vectors).
+    # over the timed region: DOS part time / sweeps. ncu shows these FP64
+    # sweeps bound by the FP64 pipe (GB300 issues 2 FP64 FMA lanes per clock
+    # per SM), so the bound is the FP64 ALU; the HBM fraction is reported too.
     info = tb.tbpm_get_info(ctx)
-    # per row: 3 hoppings (int32 column + value), FP64 diagonal, slice offsets
+    sweeps = N_STEPS * (K - 1)
+    sweep_s = dos_ms / 1e3 / sweeps
+    # algorithmic bytes per row over the K-1 sweeps of one step: per row the
+    # matrix (3 hoppings: int32 column + value; FP64 diagonal; slice offsets)
+    # plus the vector streams of FIRST (2), SECOND (3), MID (4), FINAL (5)
     mat = 3 * (4 + (8 if info["real_values"] else 16)) + 8 + 0.5
     per_step_row = ((mat + 32) + (mat + 48) + (K - 4) * (mat + 64) + (mat + 80))
-    sweeps = N_STEPS * (K - 1)
     bytes_per_sweep = n * per_step_row / (K - 1)
-    sweep_s = dos_ms / 1e3 / sweeps
+    # algorithmic FP64 operations per row over one step (FMA, MUL or ADD, each
+    # one FP64 issue slot, counted as 2 flops): FIRST 12, SECOND 10, MID 10,
+    # FINAL 16 (update 12 + the <psi0|psi> dot 4)
+    ops_step_row = 12 + 10 + (K - 4) * 10 + 16
+    flops_per_sweep = 2.0 * n * ops_step_row / (K - 1)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     hbm = float(peaks["hbm_gbs"])
-    achieved = bytes_per_sweep / sweep_s / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": profile_traffic(),
-                "kernel": "Clenshaw sweep (sweep_b1, FP64 SELL real values)",
-                "bytes_per_sweep": round(bytes_per_sweep), "sweep_us": round(sweep_s * 1e6, 2),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    fp64_peak = 2 * 152 * 2.07e9 * 2 / 1e12      # 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2
+    tflops = flops_per_sweep / sweep_s / 1e12
+    gbs = bytes_per_sweep / sweep_s / 1e9
+    roofline = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(fp64_peak, 4),
+                "unit": "TFLOP/s", "frac": round(tflops / fp64_peak, 4), "traffic": profile_traffic(),
+                "kernel": "Clenshaw sweeps (sweep_b1, FP64, SELL, real hoppings)",
+                "peak_source": "FP64 pipe from unit counts and clock (no measured FP64 peak in "
+                               "MEASURED_PEAKS.json): 2 FMA lanes/clk/SM x 152 SMs x 2.07 GHz",
+                "flops_per_sweep": round(flops_per_sweep), "sweep_us": round(sweep_s * 1e6, 2),
+                "hbm": {"achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(gbs / hbm, 4), "bytes_per_sweep": round(bytes_per_sweep),
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}}
 
     # e2e: the same step through the public API with pinned host buffers,
     # H2D of psi0 and D2H of every result inside the timed region
@@ -324,6 +338,19 @@ def run_variants(args, dev, stream):
     import tbpm_inputs as ti
     import paper_2509_26309_gb300 as tb
     res = {}
+    # config 1: 64x64 pristine graphene (N = 8192), FP64, 1024 steps: the
+    # single-launch cluster path against one graph-launched kernel per sweep
+    h1 = ti.graphene_csr(64, 64)
+    p1 = torch.from_numpy(ti.random_phase_state(h1.n, 0).reshape(1, h1.n)).to(dev)
+    o1 = torch.empty((1, 1025), dtype=torch.complex128, device=dev)
+    for name, flags in (("fp64_cluster_64x64", 0), ("fp64_graph_64x64", tb.TBPM_F_NO_CLUSTER)):
+        c1 = tb.tbpm_create(h1.n, h1.row_ptr, h1.col, h1.val, RESCALE,
+                            tb.make_opts(flags=flags, stream=stream.cuda_stream))
+        ms1 = timed_calls(lambda: tb.tbpm_dos_corr(c1, p1, DT, 1024, out=o1), 3, stream)
+        K1 = tb.tbpm_get_info(c1)["num_terms"]
+        res[name] = {"value": h1.n * 1024 * (K1 - 1) / (ms1 / 1e3), "unit": UNIT, "ms_per_call": ms1,
+                     "states": 1, "n_steps": 1024}
+        tb.tbpm_destroy(c1)
     # config 3: FP32 single state, SELL
     n3 = 2 * 2048 * 2048
     h3 = ti.graphene_csr(2048, 2048, onsite=ti.anderson_onsite(n3, W_DISORDER, 1))

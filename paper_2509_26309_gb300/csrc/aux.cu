@@ -100,10 +100,13 @@ __device__ __forceinline__ double2 block_sum2(double re, double im, double2 *sm)
     return r;
 }
 
-// <a|b> per 32-row slice: one warp per slice, fixed butterfly; partials[s].
+// <a|b> over 32-row slices (grid-stride, one warp per slice at a time).
+// per_slice: one fixed-butterfly partial per slice, partials[s] (instances of
+// a batch stay apart); otherwise per-lane sums over the warp's slices and one
+// partial per warp, partials[warp] (as the single-instance final sweep).
 template <typename R>
-__global__ void __launch_bounds__(kBlock) dot_slices(const void *a_, const void *b_, int64_t nslices,
-                                                     double2 *partials)
+__global__ void __launch_bounds__(kBlockB1) dot_slices(const void *a_, const void *b_, int64_t nslices,
+                                                     double2 *partials, bool per_slice)
 {
     typedef typename V2<R>::T V;
     const V *a = reinterpret_cast<const V *>(a_);
@@ -111,16 +114,30 @@ __global__ void __launch_bounds__(kBlock) dot_slices(const void *a_, const void 
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double wr = 0.0, wi = 0.0;
     for (int64_t s = warp; s < nslices; s += nwarps) {
         const V p = a[s * 32 + lane], q = b[s * 32 + lane];
         const double pr = p.x, pi = p.y, qr = q.x, qi = q.y;
-        double re = fma(pr, qr, pi * qi), im = fma(pr, qi, -pi * qr);
+        if (per_slice) {
+            double re = fma(pr, qr, pi * qi), im = fma(pr, qi, -pi * qr);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                re += __shfl_xor_sync(0xffffffffu, re, o);
+                im += __shfl_xor_sync(0xffffffffu, im, o);
+            }
+            if (lane == 0) partials[s] = make_double2(re, im);
+        } else {
+            wr = fma(pr, qr, fma(pi, qi, wr));
+            wi = fma(pr, qi, fma(-pi, qr, wi));
+        }
+    }
+    if (!per_slice) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            re += __shfl_xor_sync(0xffffffffu, re, o);
-            im += __shfl_xor_sync(0xffffffffu, im, o);
+            wr += __shfl_xor_sync(0xffffffffu, wr, o);
+            wi += __shfl_xor_sync(0xffffffffu, wi, o);
         }
-        if (lane == 0) partials[s] = make_double2(re, im);
+        if (lane == 0) partials[warp] = make_double2(wr, wi);
     }
 }
 
@@ -326,10 +343,10 @@ cudaError_t launch_bessel(double x, double tol, double2 *d_coef, int *d_K, cudaS
 }
 
 cudaError_t launch_dot(int precision, const void *a, const void *b, int64_t nslices,
-                       double2 *partials, int grid, cudaStream_t s)
+                       double2 *partials, int grid, bool per_slice, cudaStream_t s)
 {
-    if (precision == TBPM_FP64) dot_slices<double><<<grid, kBlock, 0, s>>>(a, b, nslices, partials);
-    else dot_slices<float><<<grid, kBlock, 0, s>>>(a, b, nslices, partials);
+    if (precision == TBPM_FP64) dot_slices<double><<<grid, kBlockB1, 0, s>>>(a, b, nslices, partials, per_slice);
+    else dot_slices<float><<<grid, kBlockB1, 0, s>>>(a, b, nslices, partials, per_slice);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,17 @@ template <> struct V2<float> { typedef float2 T; };
 
 enum BMode { B_ONE = 0, B_REAL = 1, B_IMAG = 2 };
 
+// Matrix streams are read once per sweep. For FP32 they are loaded with the
+// streaming (evict-first) cache operator so that they do not push the vectors,
+// which the next sweep reads again, out of L2; the FP64 sweeps are bound by the
+// FP64 pipe and keep the default policy.
+template <typename R, typename T>
+__device__ __forceinline__ T ldm(const T *p)
+{
+    if (sizeof(R) == 4) return __ldcs(p);
+    return __ldg(p);
+}
+
 // acc = A x for row `row` of a SELL slice, accumulated onto (ar, ai).
 template <typename R, bool REALV>
 __device__ __forceinline__ void sell_apply(const SweepParams &p, int64_t s, int lane,
@@ -42,17 +53,17 @@ __device__ __forceinline__ void sell_apply(const SweepParams &p, int64_t s, int 
                                            R &ar, R &ai)
 {
     typedef typename V2<R>::T V;
-    const int64_t off = __ldg(p.slice_off + s);
-    const int w = (int)((__ldg(p.slice_off + s + 1) - off) >> 5);
+    const int64_t off = ldm<R>(p.slice_off + s);
+    const int w = (int)((ldm<R>(p.slice_off + s + 1) - off) >> 5);
     const int32_t *cp = p.cols + off + lane;
     if (REALV) {
         const R *vp = reinterpret_cast<const R *>(p.vals) + off + lane;
         int j = 0;
         for (; j + 4 <= w; j += 4) {
-            int c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * (j + 1));
-            int c2 = __ldg(cp + 32 * (j + 2)), c3 = __ldg(cp + 32 * (j + 3));
-            R v0 = __ldg(vp + 32 * j), v1 = __ldg(vp + 32 * (j + 1));
-            R v2 = __ldg(vp + 32 * (j + 2)), v3 = __ldg(vp + 32 * (j + 3));
+            int c0 = ldm<R>(cp + 32 * j), c1 = ldm<R>(cp + 32 * (j + 1));
+            int c2 = ldm<R>(cp + 32 * (j + 2)), c3 = ldm<R>(cp + 32 * (j + 3));
+            R v0 = ldm<R>(vp + 32 * j), v1 = ldm<R>(vp + 32 * (j + 1));
+            R v2 = ldm<R>(vp + 32 * (j + 2)), v3 = ldm<R>(vp + 32 * (j + 3));
             V x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
             ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
             ar = fma(v1, x1.x, ar); ai = fma(v1, x1.y, ai);
@@ -60,16 +71,16 @@ __device__ __forceinline__ void sell_apply(const SweepParams &p, int64_t s, int 
             ar = fma(v3, x3.x, ar); ai = fma(v3, x3.y, ai);
         }
         if (j + 2 <= w) {
-            int c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * (j + 1));
-            R v0 = __ldg(vp + 32 * j), v1 = __ldg(vp + 32 * (j + 1));
+            int c0 = ldm<R>(cp + 32 * j), c1 = ldm<R>(cp + 32 * (j + 1));
+            R v0 = ldm<R>(vp + 32 * j), v1 = ldm<R>(vp + 32 * (j + 1));
             V x0 = __ldg(x + c0), x1 = __ldg(x + c1);
             ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
             ar = fma(v1, x1.x, ar); ai = fma(v1, x1.y, ai);
             j += 2;
         }
         if (j < w) {
-            int c0 = __ldg(cp + 32 * j);
-            R v0 = __ldg(vp + 32 * j);
+            int c0 = ldm<R>(cp + 32 * j);
+            R v0 = ldm<R>(vp + 32 * j);
             V x0 = __ldg(x + c0);
             ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
         }
@@ -77,15 +88,15 @@ __device__ __forceinline__ void sell_apply(const SweepParams &p, int64_t s, int 
         const V *vp = reinterpret_cast<const V *>(p.vals) + off + lane;
         int j = 0;
         for (; j + 2 <= w; j += 2) {
-            int c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * (j + 1));
-            V v0 = __ldg(vp + 32 * j), v1 = __ldg(vp + 32 * (j + 1));
+            int c0 = ldm<R>(cp + 32 * j), c1 = ldm<R>(cp + 32 * (j + 1));
+            V v0 = ldm<R>(vp + 32 * j), v1 = ldm<R>(vp + 32 * (j + 1));
             V x0 = __ldg(x + c0), x1 = __ldg(x + c1);
             ar = fma(v0.x, x0.x, fma(-v0.y, x0.y, ar)); ai = fma(v0.x, x0.y, fma(v0.y, x0.x, ai));
             ar = fma(v1.x, x1.x, fma(-v1.y, x1.y, ar)); ai = fma(v1.x, x1.y, fma(v1.y, x1.x, ai));
         }
         if (j < w) {
-            int c0 = __ldg(cp + 32 * j);
-            V v0 = __ldg(vp + 32 * j);
+            int c0 = ldm<R>(cp + 32 * j);
+            V v0 = ldm<R>(vp + 32 * j);
             V x0 = __ldg(x + c0);
             ar = fma(v0.x, x0.x, fma(-v0.y, x0.y, ar)); ai = fma(v0.x, x0.y, fma(v0.y, x0.x, ai));
         }
@@ -164,11 +175,16 @@ __device__ __forceinline__ void sweep_coeffs(const SweepParams &p, int inst, R &
 }
 
 // One Clenshaw sweep for a single state per row (B = 1). A warp owns one
-// 32-row slice at a time. The final sweep reduces <psi0|y> (and ||y||^2 when
-// renormalising) over each slice in a fixed butterfly and stores one partial
-// per slice, so the reduced values do not depend on the launch configuration.
-template <typename R, int OP, bool REALV, int BM, bool AIMAG, bool HASZ, bool FINAL>
-__global__ void __launch_bounds__(kBlock) sweep_b1(SweepParams p)
+// 32-row slice at a time (grid-stride over slices).
+// The final sweep accumulates <psi0|y> (and ||y||^2 when renormalising) per
+// lane in FP64 across the warp's slices and reduces once per warp, at the end,
+// into partials[delta * W + warp] (W = warps in the grid, fixed per context):
+// FP64 is GB300's scarce pipe, and a butterfly per slice would cost as many FP64
+// instructions as the sparse product. For a batch of instances (MULTI) the
+// coefficients are those of each slice's instance and the partials are stored
+// per slice, partials[delta * nslices + slice], so that instances stay apart.
+template <typename R, int OP, bool REALV, int BM, bool AIMAG, bool HASZ, bool FINAL, bool MULTI>
+__global__ void __launch_bounds__(kBlockB1) sweep_b1(SweepParams p)
 {
     typedef typename V2<R>::T V;
     R a, beta;
@@ -184,17 +200,23 @@ __global__ void __launch_bounds__(kBlock) sweep_b1(SweepParams p)
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double dr = 0.0, di = 0.0, nn = 0.0;
 
     for (int64_t s = warp; s < p.nslices; s += nwarps) {
-        if (p.slice_inst) sweep_coeffs<R, BM, AIMAG>(p, __ldg(p.slice_inst + s), a, beta);
+        if (MULTI) sweep_coeffs<R, BM, AIMAG>(p, __ldg(p.slice_inst + s), a, beta);
         const int64_t row = (s << 5) + lane;
         const V ps = psi[row];
-        // t = a psi - z  (a real: a*psi; a imaginary: i*a*psi)
+        // t = a psi - z  (a real: a*psi; a imaginary: i*a*psi), one FMA per part
         R tr, ti;
-        if (AIMAG) { tr = -a * ps.y; ti = a * ps.x; } else { tr = a * ps.x; ti = a * ps.y; }
-        if (HASZ) { const V zz = z[row]; tr -= zz.x; ti -= zz.y; }
+        if (HASZ) {
+            const V zz = z[row];
+            if (AIMAG) { tr = fma(-a, ps.y, -zz.x); ti = fma(a, ps.x, -zz.y); }
+            else { tr = fma(a, ps.x, -zz.x); ti = fma(a, ps.y, -zz.y); }
+        } else {
+            if (AIMAG) { tr = -a * ps.y; ti = a * ps.x; } else { tr = a * ps.x; ti = a * ps.y; }
+        }
         const V xi = __ldg(x + row);
-        const R d = diag ? __ldg(diag + row) : (R)0;
+        const R d = diag ? ldm<R>(diag + row) : (R)0;
         R ar, ai;
         if (BM == B_ONE) { ar = fma(d, xi.x, tr); ai = fma(d, xi.y, ti); }
         else { ar = d * xi.x; ai = d * xi.y; }
@@ -209,21 +231,37 @@ __global__ void __launch_bounds__(kBlock) sweep_b1(SweepParams p)
             const V q = psi0[row];
             const double qr = (double)q.x, qi = (double)q.y;
             const double orr = (double)out.x, oi = (double)out.y;
-            const double dr = warp_sum(fma(qr, orr, qi * oi));
-            const double di = warp_sum(fma(qr, oi, -qi * orr));
-            if (lane == 0) p.partials[(int64_t)p.delta * p.nslices + s] = make_double2(dr, di);
-            if (p.norm_partials) {
-                const double nn = warp_sum(fma(orr, orr, oi * oi));
-                if (lane == 0) p.norm_partials[(int64_t)p.delta * p.nslices + s] = make_double2(nn, 0.0);
+            if (MULTI) {
+                const double sr = warp_sum(fma(qr, orr, qi * oi));
+                const double si = warp_sum(fma(qr, oi, -qi * orr));
+                if (lane == 0) p.partials[(int64_t)p.delta * p.nslices + s] = make_double2(sr, si);
+                if (p.norm_partials) {
+                    const double sn = warp_sum(fma(orr, orr, oi * oi));
+                    if (lane == 0) p.norm_partials[(int64_t)p.delta * p.nslices + s] = make_double2(sn, 0.0);
+                }
+            } else {
+                dr = fma(qr, orr, fma(qi, oi, dr));
+                di = fma(qr, oi, fma(-qi, orr, di));
+                if (p.norm_partials) nn = fma(orr, orr, fma(oi, oi, nn));
             }
+        }
+    }
+    if (FINAL && !MULTI) {
+        dr = warp_sum(dr);
+        di = warp_sum(di);
+        if (lane == 0) p.partials[(int64_t)p.delta * nwarps + warp] = make_double2(dr, di);
+        if (p.norm_partials) {
+            nn = warp_sum(nn);
+            if (lane == 0) p.norm_partials[(int64_t)p.delta * nwarps + warp] = make_double2(nn, 0.0);
         }
     }
 }
 
-// KPM sweep for B = 1: y = scale * (A x) - [!first] y, with per-slice partials
-// of <x|x> and <y|x> at partials[(2 delta + 0/1) * nslices + slice].
+// KPM sweep for B = 1: y = scale * (A x) - [!first] y. Per lane FP64 sums of
+// <x|x> and <y|x> over the warp's slices, reduced once per warp into
+// partials[(2 delta + 0/1) * W + warp].
 template <typename R, int OP, bool REALV, bool FIRST>
-__global__ void __launch_bounds__(kBlock) kpm_b1(KpmParams p)
+__global__ void __launch_bounds__(kBlockB1) kpm_b1(KpmParams p)
 {
     typedef typename V2<R>::T V;
     SweepParams sp;                     // operator fields for the shared helpers
@@ -236,8 +274,7 @@ __global__ void __launch_bounds__(kBlock) kpm_b1(KpmParams p)
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double2 *pn = p.partials + (int64_t)p.delta * 2 * p.nslices;
-    double2 *pc = pn + p.nslices;
+    double nn = 0.0, cr = 0.0, ci = 0.0;
     for (int64_t s = warp; s < p.nslices; s += nwarps) {
         const int64_t row = (s << 5) + lane;
         const V xi = __ldg(x + row);
@@ -259,37 +296,40 @@ __global__ void __launch_bounds__(kBlock) kpm_b1(KpmParams p)
         y[row] = out;
         const double xr = (double)xi.x, xim = (double)xi.y;
         const double orr = (double)out.x, oi = (double)out.y;
-        const double nn = warp_sum(fma(xr, xr, xim * xim));
+        nn = fma(xr, xr, fma(xim, xim, nn));
         // <y|x> = sum conj(y) x
-        const double cr = warp_sum(fma(orr, xr, oi * xim));
-        const double ci = warp_sum(fma(orr, xim, -oi * xr));
-        if (lane == 0) {
-            pn[s] = make_double2(nn, 0.0);
-            pc[s] = make_double2(cr, ci);
-        }
+        cr = fma(orr, xr, fma(oi, xim, cr));
+        ci = fma(orr, xim, fma(-oi, xr, ci));
+    }
+    nn = warp_sum(nn);
+    cr = warp_sum(cr);
+    ci = warp_sum(ci);
+    if (lane == 0) {
+        p.partials[((int64_t)p.delta * 2) * nwarps + warp] = make_double2(nn, 0.0);
+        p.partials[((int64_t)p.delta * 2 + 1) * nwarps + warp] = make_double2(cr, ci);
     }
 }
 
-template <typename R, int OP, bool REALV>
+template <typename R, int OP, bool REALV, bool MULTI>
 cudaError_t sweep_dispatch(SweepKind kind, bool a_imag, bool has_z, const SweepParams &p,
                            int grid, cudaStream_t s)
 {
     switch (kind) {
     case SW_FIRST:
-        if (a_imag) sweep_b1<R, OP, REALV, B_REAL, true, false, false><<<grid, kBlock, 0, s>>>(p);
-        else sweep_b1<R, OP, REALV, B_IMAG, false, false, false><<<grid, kBlock, 0, s>>>(p);
+        if (a_imag) sweep_b1<R, OP, REALV, B_REAL, true, false, false, MULTI><<<grid, kBlockB1, 0, s>>>(p);
+        else sweep_b1<R, OP, REALV, B_IMAG, false, false, false, MULTI><<<grid, kBlockB1, 0, s>>>(p);
         break;
     case SW_SECOND:
-        if (a_imag) sweep_b1<R, OP, REALV, B_ONE, true, false, false><<<grid, kBlock, 0, s>>>(p);
-        else sweep_b1<R, OP, REALV, B_ONE, false, false, false><<<grid, kBlock, 0, s>>>(p);
+        if (a_imag) sweep_b1<R, OP, REALV, B_ONE, true, false, false, MULTI><<<grid, kBlockB1, 0, s>>>(p);
+        else sweep_b1<R, OP, REALV, B_ONE, false, false, false, MULTI><<<grid, kBlockB1, 0, s>>>(p);
         break;
     case SW_MID:
-        if (a_imag) sweep_b1<R, OP, REALV, B_ONE, true, true, false><<<grid, kBlock, 0, s>>>(p);
-        else sweep_b1<R, OP, REALV, B_ONE, false, true, false><<<grid, kBlock, 0, s>>>(p);
+        if (a_imag) sweep_b1<R, OP, REALV, B_ONE, true, true, false, MULTI><<<grid, kBlockB1, 0, s>>>(p);
+        else sweep_b1<R, OP, REALV, B_ONE, false, true, false, MULTI><<<grid, kBlockB1, 0, s>>>(p);
         break;
     case SW_FINAL:
-        if (has_z) sweep_b1<R, OP, REALV, B_REAL, false, true, true><<<grid, kBlock, 0, s>>>(p);
-        else sweep_b1<R, OP, REALV, B_REAL, false, false, true><<<grid, kBlock, 0, s>>>(p);
+        if (has_z) sweep_b1<R, OP, REALV, B_REAL, false, true, true, MULTI><<<grid, kBlockB1, 0, s>>>(p);
+        else sweep_b1<R, OP, REALV, B_REAL, false, false, true, MULTI><<<grid, kBlockB1, 0, s>>>(p);
         break;
     }
     return cudaGetLastError();
@@ -298,8 +338,8 @@ cudaError_t sweep_dispatch(SweepKind kind, bool a_imag, bool has_z, const SweepP
 template <typename R, int OP, bool REALV>
 cudaError_t kpm_dispatch(const KpmParams &p, int grid, cudaStream_t s)
 {
-    if (p.first) kpm_b1<R, OP, REALV, true><<<grid, kBlock, 0, s>>>(p);
-    else kpm_b1<R, OP, REALV, false><<<grid, kBlock, 0, s>>>(p);
+    if (p.first) kpm_b1<R, OP, REALV, true><<<grid, kBlockB1, 0, s>>>(p);
+    else kpm_b1<R, OP, REALV, false><<<grid, kBlockB1, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -309,20 +349,30 @@ cudaError_t launch_sweep(const SweepVariant &v, SweepKind kind, bool a_imag, boo
                          const SweepParams &p, int grid, cudaStream_t s)
 {
     if (v.states != 1) return cudaErrorInvalidValue;
+    const bool multi = p.slice_inst != nullptr;        // batches of instances: SELL only
+    if (multi && v.op != OP_SELL) return cudaErrorInvalidValue;
     if (v.precision == TBPM_FP64) {
-        if (v.op == OP_SELL)
-            return v.real_values ? sweep_dispatch<double, OP_SELL, true>(kind, a_imag, has_z, p, grid, s)
-                                 : sweep_dispatch<double, OP_SELL, false>(kind, a_imag, has_z, p, grid, s);
+        if (v.op == OP_SELL) {
+            if (multi)
+                return v.real_values ? sweep_dispatch<double, OP_SELL, true, true>(kind, a_imag, has_z, p, grid, s)
+                                     : sweep_dispatch<double, OP_SELL, false, true>(kind, a_imag, has_z, p, grid, s);
+            return v.real_values ? sweep_dispatch<double, OP_SELL, true, false>(kind, a_imag, has_z, p, grid, s)
+                                 : sweep_dispatch<double, OP_SELL, false, false>(kind, a_imag, has_z, p, grid, s);
+        }
         if (v.op == OP_STENCIL_MONO)
-            return sweep_dispatch<double, OP_STENCIL_MONO, true>(kind, a_imag, has_z, p, grid, s);
-        return sweep_dispatch<double, OP_STENCIL_BI, true>(kind, a_imag, has_z, p, grid, s);
+            return sweep_dispatch<double, OP_STENCIL_MONO, true, false>(kind, a_imag, has_z, p, grid, s);
+        return sweep_dispatch<double, OP_STENCIL_BI, true, false>(kind, a_imag, has_z, p, grid, s);
     }
-    if (v.op == OP_SELL)
-        return v.real_values ? sweep_dispatch<float, OP_SELL, true>(kind, a_imag, has_z, p, grid, s)
-                             : sweep_dispatch<float, OP_SELL, false>(kind, a_imag, has_z, p, grid, s);
+    if (v.op == OP_SELL) {
+        if (multi)
+            return v.real_values ? sweep_dispatch<float, OP_SELL, true, true>(kind, a_imag, has_z, p, grid, s)
+                                 : sweep_dispatch<float, OP_SELL, false, true>(kind, a_imag, has_z, p, grid, s);
+        return v.real_values ? sweep_dispatch<float, OP_SELL, true, false>(kind, a_imag, has_z, p, grid, s)
+                             : sweep_dispatch<float, OP_SELL, false, false>(kind, a_imag, has_z, p, grid, s);
+    }
     if (v.op == OP_STENCIL_MONO)
-        return sweep_dispatch<float, OP_STENCIL_MONO, true>(kind, a_imag, has_z, p, grid, s);
-    return sweep_dispatch<float, OP_STENCIL_BI, true>(kind, a_imag, has_z, p, grid, s);
+        return sweep_dispatch<float, OP_STENCIL_MONO, true, false>(kind, a_imag, has_z, p, grid, s);
+    return sweep_dispatch<float, OP_STENCIL_BI, true, false>(kind, a_imag, has_z, p, grid, s);
 }
 
 cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cudaStream_t s)
@@ -348,10 +398,10 @@ int sweep_grid(const SweepVariant &v, int num_sms)
     cudaError_t e;
     if (v.precision == TBPM_FP64)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, sweep_b1<double, OP_SELL, true, B_ONE, false, true, false>, kBlock, 0);
+            &per_sm, sweep_b1<double, OP_SELL, true, B_ONE, false, true, false, false>, kBlockB1, 0);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, sweep_b1<float, OP_SELL, true, B_ONE, false, true, false>, kBlock, 0);
+            &per_sm, sweep_b1<float, OP_SELL, true, B_ONE, false, true, false, false>, kBlockB1, 0);
     if (e != cudaSuccess || per_sm < 1) per_sm = 4;
     return per_sm * num_sms;
 }

@@ -343,7 +343,8 @@ int ensure_work(tbpm_ctx *ctx, int states, size_t out_elems, size_t stage_double
         CU(cudaMemsetAsync(ctx->d_b1, 0, vb, ctx->stream));
         // single-state partials: one per slice; 16-state partials: one per block and state
         const size_t nsl = (size_t)(ctx->n_pad / kSlice);
-        const size_t per_slot = std::max<size_t>(2 * nsl, (size_t)ctx->nblk16 * kMaxBlockStates);
+        const size_t W = (size_t)ctx->nblk * (kBlockB1 / 32);
+        const size_t per_slot = std::max<size_t>(std::max(2 * nsl, 2 * W), (size_t)ctx->nblk16 * kMaxBlockStates);
         ctx->partials_cap = (size_t)(kChunk + 1) * per_slot;
         CU(cudaMalloc(&ctx->d_partials, ctx->partials_cap * sizeof(double2)));
         if (ctx->flags & TBPM_F_RENORM) {
@@ -411,6 +412,8 @@ int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, int B, int64_t ld, cudaStre
     }
     const int nseg = std::max(1, ctx->ninst);
     p.slice_inst = ctx->d_slice_inst;                    // nullptr for a single instance
+    // partials per slot: per slice for a batch, per warp of the grid otherwise
+    const int64_t npart = ctx->ninst > 0 ? p.nslices : (int64_t)ctx->nblk * (kBlockB1 / 32);
     void *Bv[2] = {ctx->d_b0, ctx->d_b1};
     for (int d = 0; d < len; ++d) {
         // FIRST: b_{K-2} = c_{K-2} psi + c_{K-1} A psi  -> B[0]
@@ -444,7 +447,7 @@ int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, int B, int64_t ld, cudaStre
         ++*launches;
         if (renorm) {   // 1/||psi(t_{n+1})|| for the next step's sweeps
             if (B == 1)
-                CU(launch_renorm_seg(ctx->d_norm + (int64_t)d * p.nslices, p.nslices, ctx->d_seg_off, nseg,
+                CU(launch_renorm_seg(ctx->d_norm + (int64_t)d * npart, npart, ctx->d_seg_off, nseg,
                                      ctx->d_scale, s));
             else
                 CU(launch_renorm(ctx->d_norm + (int64_t)d * p.nblk * B, p.nblk, B, ctx->d_scale, s));
@@ -452,7 +455,7 @@ int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, int B, int64_t ld, cudaStre
         }
     }
     if (B == 1)
-        CU(launch_reduce_seg(ctx->d_partials, len, 1, p.nslices, ctx->d_seg_off, nseg, ctx->d_counter, 1,
+        CU(launch_reduce_seg(ctx->d_partials, len, 1, npart, ctx->d_seg_off, nseg, ctx->d_counter, 1,
                              ctx->d_out, ld, s));
     else CU(launch_reduce_b16(ctx->d_partials, len, ctx->nblk16, ctx->d_counter, 1, ctx->d_out, ld, s));
     CU(launch_advance(ctx->d_counter, len, s));
@@ -482,8 +485,8 @@ int enqueue_kpm_chunk(tbpm_ctx *ctx, int len, cudaStream_t s, int64_t *launches)
         CU(launch_kpm(v, p, ctx->nblk, s));
         ++*launches;
     }
-    CU(launch_reduce_seg(ctx->d_partials, len, 2, p.nslices, nullptr, 1, ctx->d_counter, 1, ctx->d_out,
-                         0, s));
+    CU(launch_reduce_seg(ctx->d_partials, len, 2, (int64_t)ctx->nblk * (kBlockB1 / 32), nullptr, 1,
+                         ctx->d_counter, 1, ctx->d_out, 0, s));
     CU(launch_advance(ctx->d_counter, len, s));
     *launches += 2;
     return TBPM_OK;
@@ -827,9 +830,9 @@ static int run_dos(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, in
         CU(launch_load_states(ctx->precision, src, n, ctx->n_pad, 1, 0, 1, ctx->d_psi0, ctx->d_psi,
                               ctx->stream));
         CU(launch_dot(ctx->precision, ctx->d_psi0, ctx->d_psi0, ctx->n_pad / kSlice, ctx->d_partials, ctx->nblk,
-                      ctx->stream));
-        CU(launch_reduce_seg(ctx->d_partials, 1, 1, ctx->n_pad / kSlice, nullptr, 1, nullptr, 0, ctx->d_out,
-                             0, ctx->stream));
+                      false, ctx->stream));
+        CU(launch_reduce_seg(ctx->d_partials, 1, 1, (int64_t)ctx->nblk * (kBlockB1 / 32), nullptr, 1, nullptr, 0,
+                             ctx->d_out, 0, ctx->stream));
         CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
         launches += 3;
         if (ctx->flags & TBPM_F_RENORM) {
@@ -924,8 +927,8 @@ int kpm_moments(tbpm_ctx *ctx, const double *psi0, int nstates, int M, double *m
         p.x = ctx->d_psi; p.y = ctx->d_b0; p.scale = 0.5; p.first = true;
         p.partials = ctx->d_partials; p.delta = 0; p.nblk = ctx->nblk;
         CU(launch_kpm(v, p, ctx->nblk, ctx->stream));
-        CU(launch_reduce_seg(ctx->d_partials, 1, 2, ctx->n_pad / kSlice, nullptr, 1, nullptr, 0, ctx->d_out,
-                             0, ctx->stream));
+        CU(launch_reduce_seg(ctx->d_partials, 1, 2, (int64_t)ctx->nblk * (kBlockB1 / 32), nullptr, 1, nullptr, 0,
+                             ctx->d_out, 0, ctx->stream));
         CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
         launches += 3;
         int done = 0;
@@ -1144,7 +1147,7 @@ int tbpm_batch_dos_corr(tbpm_ctx *ctx, const double *psi0, const double *dt, int
         ++launches;
     }
     const int64_t nsl = ctx->n_pad / kSlice;
-    CU(launch_dot(ctx->precision, ctx->d_psi0, ctx->d_psi0, nsl, ctx->d_partials, ctx->nblk, ctx->stream));
+    CU(launch_dot(ctx->precision, ctx->d_psi0, ctx->d_psi0, nsl, ctx->d_partials, ctx->nblk, true, ctx->stream));
     CU(launch_reduce_seg(ctx->d_partials, 1, 1, nsl, ctx->d_seg_off, G, nullptr, 0, ctx->d_out, ld, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
     launches += 2;

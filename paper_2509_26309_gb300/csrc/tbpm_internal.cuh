@@ -15,7 +15,8 @@
 namespace tbpm {
 
 constexpr int kSlice = 32;          // SELL slice height = warp width
-constexpr int kBlock = 256;         // threads per block of the sweep kernels
+constexpr int kBlock = 256;         // threads per block of the 16-state and helper kernels
+constexpr int kBlockB1 = 512;       // threads per block of the single-state sweeps and dots
 constexpr int kMaxTerms = 128;      // Chebyshev coefficients generated on device
 constexpr int kChunk = 16;          // time steps (or KPM passes) per captured graph
 constexpr int kMaxBlockStates = 16; // states advanced together (FP32 batched)
@@ -67,7 +68,8 @@ struct SweepParams {
     const double2 *coef;
     int ia, ib, ic;
     double bscale;
-    // final sweep: <psi0|y> partials, one per block per state, slot `delta`
+    // final sweep: <psi0|y> partials of slot `delta`: one per warp of the grid
+    // for a single instance, one per slice for a batch (slice_inst != nullptr)
     const void *psi0;
     double2 *partials;
     int delta;
@@ -188,10 +190,11 @@ cudaError_t launch_sweep(const SweepVariant &v, SweepKind kind, bool a_imag, boo
 // KPM sweep (cheb_sweep.cu).
 cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cudaStream_t s);
 
-// <a|b> = sum_i conj(a_i) b_i of one state, one partial per 32-row slice
-// (partials[s], s < nslices) (aux.cu).
+// <a|b> = sum_i conj(a_i) b_i of one state over nslices 32-row slices: one
+// partial per slice (per_slice, partials[s]) or one per warp of the grid
+// (partials[w], w < grid * kBlockB1 / 32) (aux.cu).
 cudaError_t launch_dot(int precision, const void *a, const void *b, int64_t nslices,
-                       double2 *partials, int grid, cudaStream_t s);
+                       double2 *partials, int grid, bool per_slice, cudaStream_t s);
 
 // Deterministic reduction of per-block partials laid out [nslot][nterm][nblk]:
 //   out[(base + offset + d) * nterm + q] = sum_b partials[(d * nterm + q) * nblk + b]
