@@ -404,9 +404,10 @@ def profile_traffic():
     except (OSError, ValueError):
         return None
     import hashlib
-    src = os.path.join(ROOT, "paper_2509_26309_gb300", "csrc", "cheb_sweep.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("cheb_sweep_sha") != digest:
+    h = hashlib.sha256()
+    for f in ("cheb_sweep.cu", "sweep_ops.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2509_26309_gb300", "csrc", f), "rb").read())
+    if rec.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
         return None
     return rec.get("sweep_traffic_bytes")
 

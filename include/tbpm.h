@@ -67,6 +67,10 @@ extern "C" {
                                           systems of up to 16 x 4096 (FP64) or
                                           16 x 8192 (FP32) padded rows; the result
                                           is the same either way                   */
+#define TBPM_F_AUTOTUNE           0x10u /* at create, time middle sweeps of this
+                                          operator for grids of 1 .. occupancy
+                                          blocks per SM (and twice occupancy) and
+                                          keep the fastest for the context's life */
 
 typedef struct tbpm_opts {
     int precision;       /* TBPM_FP64 | TBPM_FP32                                  */
@@ -201,6 +205,39 @@ int tbpm_propagate(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, in
  *   psi0  as tbpm_dos_corr;  M >= 1. */
 int kpm_moments(tbpm_ctx *ctx, const double *psi0, int nstates, int M, double *mu);
 
+/* tbpm_quasi_eigenstates: quasi-eigenstates (QE, a TBPM capability benchmarked
+ * in Sec. 4.2.2), the windowed Fourier transform of the evolved state over
+ * positive and negative times,
+ *   Psi(E_e) = dt/(2 pi) sum_{m=-N}^{N} w_m exp(i E_e t_m) psi(t_m),
+ *   psi(t) = exp(-iHt) psi0, t_m = m dt, w_m = (1 + cos(pi m / N)) / 2,
+ * with psi(t_m) from the same Chebyshev steps as tbpm_dos_corr (one forward
+ * and one backward evolution). Accumulated in FP64.
+ *   psi0      double[2n] one state;  dt > 0;  n_steps = N >= 1
+ *   energies  double[n_e] (eV), 1 <= n_e <= 4096
+ *   qe        double[2 * n_e * n] out, energy-major (Psi(E_e) at offset 2 n e)
+ * Host or device buffers. Not available on batch contexts. */
+int tbpm_quasi_eigenstates(tbpm_ctx *ctx, const double *psi0, double dt, int n_steps,
+                           const double *energies, int n_e, double *qe);
+
+/* tbpm_haydock: the recursion (Lanczos) coefficients of the local density
+ * of states by the Haydock method (the LDOS capability of the TBPM solver,
+ * Sec. 1; the LDOS row of the benchmarks, Sec. 4.2.2). With H not rescaled,
+ * v_0 = psi0/||psi0||, v_{-1} = 0, b_0 = 0, for n = 0..M-1:
+ *   w = H v_n - b_n v_{n-1},  a_n = Re <v_n|w>,  u = w - a_n v_n,
+ *   b_{n+1} = ||u||,  v_{n+1} = u / b_{n+1}.
+ *   psi0  double[2n] start state (a site state e_i gives the LDOS at site i),
+ *         host or device, not necessarily normalised
+ *   M     >= 1 levels;  a, b  double[M] out: a[n] = a_n, b[n] = b_{n+1}
+ * If some b_{n+1} is 0 (an invariant subspace) every later a and b is 0. */
+int tbpm_haydock(tbpm_ctx *ctx, const double *psi0, int M, double *a, double *b);
+
+/* tbpm_haydock_ldos: rho(E_j) = -Im G(E_j + i eta) / pi with the continued
+ * fraction G(z) = 1/(z - a_0 - b_1^2/(z - a_1 - ... b_{M-1}^2/(z - a_{M-1}))),
+ * on the GPU. a, b as returned by tbpm_haydock; energies double[n_e] (eV);
+ * eta > 0 the broadening (eV); ldos double[n_e] out. Host or device. */
+int tbpm_haydock_ldos(tbpm_ctx *ctx, const double *a, const double *b, int M, const double *energies,
+                      int n_e, double eta, double *ldos);
+
 /* ------------------------------------------- allocation-free variant */
 
 /* Largest orbital count tbpm_dos_corr_noalloc accepts. */
@@ -266,6 +303,8 @@ typedef struct tbpm_info {
     int64_t kernel_launches;   /* kernels the last call launched                */
     double gershgorin;         /* max_i sum_j |H_ij|                            */
     double rescale;
+    int grid_blocks;           /* blocks of the single-state sweep grid         */
+    int tuned;                 /* 1 when the grid was chosen by the autotuner   */
 } tbpm_info;
 
 /* Fills *info with the context's layout and the counters of its last call. */

@@ -14,6 +14,9 @@ Parity status per function (what pins it, all in tests/test_oracle_*.py):
   dos_hann                               sum rule, numpy FFT route, delta spectrum
   jackson, kpm_dos                       Gauss-Chebyshev integral, positivity,
                                          delta reconstruction
+  quasi_eigenstates                      exact diagonalisation (windowed spectral sum)
+  haydock, haydock_ldos                  closed-form chain coefficients, moment
+                                         matching, exact diagonalisation
 """
 from __future__ import annotations
 
@@ -46,6 +49,12 @@ def _bind(path: str):
     l.oracle_jackson.argtypes = [i32, p]
     l.oracle_kpm_dos.restype = i32
     l.oracle_kpm_dos.argtypes = [p, i32, d, i32, p, p]
+    l.oracle_haydock.restype = i32
+    l.oracle_haydock.argtypes = [i64, p, p, p, p, i32, p, p]
+    l.oracle_quasi_eigenstates.restype = i32
+    l.oracle_quasi_eigenstates.argtypes = [i64, p, p, p, d, p, d, i32, d, i32, p, p]
+    l.oracle_haydock_ldos.restype = None
+    l.oracle_haydock_ldos.argtypes = [p, p, i32, p, i32, d, p]
     return l
 
 
@@ -146,6 +155,39 @@ class Oracle:
         return e, r
 
 
+    def quasi_eigenstates(self, h, rescale: float, psi0: np.ndarray, dt: float, n_steps: int,
+                          energies, tol: float = TOL) -> np.ndarray:
+        """Psi(E_e) for each energy: complex128 (n_e, n)."""
+        rp, col, val = _csr(h)
+        psi0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+        e = np.ascontiguousarray(energies, dtype=np.float64)
+        out = np.zeros((e.size, h.n), dtype=np.complex128)
+        rc = self._l.oracle_quasi_eigenstates(h.n, _ptr(rp), _ptr(col), _ptr(val), float(rescale), _ptr(psi0),
+                                              float(dt), int(n_steps), float(tol), e.size, _ptr(e), _ptr(out))
+        if rc != 0:
+            raise RuntimeError(f"oracle_quasi_eigenstates failed: {rc}")
+        return out
+
+    def haydock(self, h, psi0: np.ndarray, M: int):
+        """Recursion coefficients (a[M], b[M]) with b[m] = b_{m+1} (H not rescaled)."""
+        rp, col, val = _csr(h)
+        psi0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+        a, b = np.zeros(M), np.zeros(M)
+        rc = self._l.oracle_haydock(h.n, _ptr(rp), _ptr(col), _ptr(val), _ptr(psi0), int(M), _ptr(a), _ptr(b))
+        if rc != 0:
+            raise RuntimeError(f"oracle_haydock failed: {rc}")
+        return a, b
+
+    def haydock_ldos(self, a, b, energies, eta: float) -> np.ndarray:
+        """-Im G(E + i eta)/pi from the continued fraction of (a, b)."""
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        e = np.ascontiguousarray(energies, dtype=np.float64)
+        out = np.zeros(e.size)
+        self._l.oracle_haydock_ldos(_ptr(a), _ptr(b), a.size, _ptr(e), e.size, float(eta), _ptr(out))
+        return out
+
+
 _default = None
 
 
@@ -164,6 +206,7 @@ def lib():
 def __getattr__(name):
     # module-level access to the default instance: oracle.propagate(...), etc.
     if name in ("bessel_j", "cheb_num_terms", "cheb_coeffs", "spmv", "propagate", "dos_corr",
-                "kpm_moments", "dos_hann", "jackson", "kpm_dos"):
+                "kpm_moments", "dos_hann", "jackson", "kpm_dos", "haydock", "haydock_ldos",
+                "quasi_eigenstates"):
         return getattr(default(), name)
     raise AttributeError(name)

@@ -12,7 +12,9 @@
  *     polynomials built by the three-term recurrence T_k = 2 H~ T_{k-1} - T_{k-2}.
  *   - Sec. 3.2.3 (calc_corr_dos): the DOS correlation C(t_n) = <psi0|psi(t_n)>
  *     of a random-phase state, H~ = H / rescale (config.rescale).
- *   - Sec. 1: the kernel polynomial method, mu_n = <psi0|T_n(H~)|psi0>.
+ *   - Sec. 1: the kernel polynomial method, mu_n = <psi0|T_n(H~)|psi0>, and
+ *     the local DOS by the Haydock recursion method (benchmarked as LDOS in
+ *     Sec. 4.2.2).
  * Formulas the paper does not print are taken as their textbook definitions:
  *   - c_0 = J_0(x), c_k = 2 (-i)^k J_k(x), x = dt * rescale: the Jacobi-Anger
  *     expansion of exp(-i x y) on y in [-1, 1] (Abramowitz-Stegun 9.1.44/45),
@@ -180,6 +182,55 @@ int oracle_propagate(int64_t n, const int64_t *rp, const int32_t *col, const cpl
     return K;
 }
 
+/* Quasi-eigenstates (a TBPM capability of Sec. 4.2.2): the windowed Fourier
+ * transform of the evolved state over positive and negative times,
+ *   Psi(E_e) = dt/(2 pi) sum_{m=-N}^{N} w_m exp(i E_e t_m) psi(t_m),
+ *   psi(t) = exp(-iHt) psi0,  t_m = m dt,  w_m = (1 + cos(pi m / N)) / 2,
+ * with psi(t_m) from the Chebyshev steps of oracle_propagate (forward with
+ * dt, backward with -dt). qe_out: n_e x n complex, energy-major. */
+int oracle_quasi_eigenstates(int64_t n, const int64_t *rp, const int32_t *col, const cplx *val,
+                             double rescale, const cplx *psi0, double dt, int n_steps, double tol,
+                             int n_e, const double *energies, cplx *qe_out)
+{
+    if (n <= 0 || !rp || !col || !val || !psi0 || n_steps < 1 || !(rescale > 0) || !(dt > 0) ||
+        n_e < 1 || !energies || !qe_out)
+        return ORACLE_ERR_ARG;
+    int N = n_steps;
+    double pre = dt / (2.0 * PI);
+    for (int e = 0; e < n_e; ++e)
+        for (int64_t i = 0; i < n; ++i) qe_out[(int64_t)e * n + i] = pre * psi0[i];   /* m = 0, w_0 = 1 */
+    for (int dir = 0; dir < 2; ++dir) {
+        double h = dir == 0 ? dt : -dt;
+        double x = h * rescale;
+        int K = oracle_cheb_num_terms(x, tol);
+        if (K < 1) return ORACLE_ERR_ARG;
+        cplx *c = malloc((size_t)K * sizeof(cplx));
+        cplx *psi = malloc((size_t)n * sizeof(cplx));
+        cplx *out = malloc((size_t)n * sizeof(cplx));
+        cplx *t0 = malloc((size_t)n * sizeof(cplx));
+        cplx *t1 = malloc((size_t)n * sizeof(cplx));
+        cplx *t2 = malloc((size_t)n * sizeof(cplx));
+        if (!c || !psi || !out || !t0 || !t1 || !t2) {
+            free(c); free(psi); free(out); free(t0); free(t1); free(t2);
+            return ORACLE_ERR_OOM;
+        }
+        oracle_cheb_coeffs(x, K, c);
+        memcpy(psi, psi0, (size_t)n * sizeof(cplx));
+        for (int s = 1; s <= N; ++s) {
+            cheb_step(n, rp, col, val, rescale, K, c, psi, out, t0, t1, t2);
+            cplx *tmp = psi; psi = out; out = tmp;
+            double t = s * h;
+            double w = 0.5 * (1.0 + cos(PI * (double)s / (double)N));
+            for (int e = 0; e < n_e; ++e) {
+                cplx ph = pre * w * cexp(I * energies[e] * t);
+                for (int64_t i = 0; i < n; ++i) qe_out[(int64_t)e * n + i] += ph * psi[i];
+            }
+        }
+        free(c); free(psi); free(out); free(t0); free(t1); free(t2);
+    }
+    return ORACLE_OK;
+}
+
 /* ------------------------------------------------------------------- KPM */
 
 /* mu_m = <psi0|T_m(H~)|psi0>, m = 0..M-1, by the plain recurrence (no doubling). */
@@ -206,6 +257,65 @@ int oracle_kpm_moments(int64_t n, const int64_t *rp, const int32_t *col, const c
     }
     free(t0); free(t1); free(t2);
     return ORACLE_OK;
+}
+
+/* ------------------------------------------------------- Haydock / LDOS */
+
+/* Haydock recursion (the Lanczos tridiagonalisation used for the local DOS;
+ * Haydock, Heine, Kelly, J. Phys. C 8, 2591 (1975)) of H (not rescaled) from
+ * v_0 = psi0/||psi0||, v_{-1} = 0, b_0 = 0, for n = 0..M-1:
+ *   w = H v_n - b_n v_{n-1},  a_n = Re <v_n|w>,  u = w - a_n v_n,
+ *   b_{n+1} = ||u||,  v_{n+1} = u / b_{n+1}.
+ * Writes a[n] = a_n and b[n] = b_{n+1}. If b_{n+1} <= 1e-12 (|a_n| + b_n) the
+ * recursion has found an invariant subspace (up to rounding): b_{n+1} is set
+ * to 0 and every later a and b is 0. */
+int oracle_haydock(int64_t n, const int64_t *rp, const int32_t *col, const cplx *val,
+                   const cplx *psi0, int M, double *a, double *b)
+{
+    if (n <= 0 || !rp || !col || !val || !psi0 || M < 1 || !a || !b) return ORACLE_ERR_ARG;
+    cplx *vp = calloc((size_t)n, sizeof(cplx));
+    cplx *v = malloc((size_t)n * sizeof(cplx));
+    cplx *w = malloc((size_t)n * sizeof(cplx));
+    if (!vp || !v || !w) { free(vp); free(v); free(w); return ORACLE_ERR_OOM; }
+    double nrm = sqrt(creal(dot(n, psi0, psi0)));
+    if (!(nrm > 0)) { free(vp); free(v); free(w); return ORACLE_ERR_ARG; }
+    for (int64_t i = 0; i < n; ++i) v[i] = psi0[i] / nrm;
+    double bn = 0.0;
+    int stopped = 0;
+    for (int m = 0; m < M; ++m) {
+        if (stopped) { a[m] = 0.0; b[m] = 0.0; continue; }
+        spmv(n, rp, col, val, 1.0, v, w);
+        for (int64_t i = 0; i < n; ++i) w[i] -= bn * vp[i];
+        double am = creal(dot(n, v, w));
+        for (int64_t i = 0; i < n; ++i) w[i] -= am * v[i];
+        double bm = sqrt(creal(dot(n, w, w)));
+        /* the chain ends when b_{n+1} is rounding noise against the level's scale */
+        if (bm <= 1e-12 * (fabs(am) + bn)) bm = 0.0;
+        a[m] = am;
+        b[m] = bm;
+        if (bm == 0.0) { stopped = 1; continue; }
+        for (int64_t i = 0; i < n; ++i) { vp[i] = v[i]; v[i] = w[i] / bm; }
+        bn = bm;
+    }
+    free(vp); free(v); free(w);
+    return ORACLE_OK;
+}
+
+/* Local DOS from the recursion coefficients: rho(E) = -Im G(E + i eta) / pi,
+ * G(z) = 1 / (z - a_0 - b_1^2 / (z - a_1 - b_2^2 / ( ... / (z - a_{M-1})))),
+ * evaluated from the bottom level up (b[m] = b_{m+1}). */
+void oracle_haydock_ldos(const double *a, const double *b, int M, const double *energies, int n_e,
+                         double eta, double *ldos)
+{
+    for (int j = 0; j < n_e; ++j) {
+        cplx z = energies[j] + I * eta;
+        cplx g = 0.0;                       /* 1 / (z - a_m - b_{m+1}^2 g_{m+1}) */
+        for (int m = M - 1; m >= 0; --m) {
+            cplx tail = (m == M - 1) ? 0.0 : b[m] * b[m] * g;
+            g = 1.0 / (z - a[m] - tail);
+        }
+        ldos[j] = -cimag(g) / PI;
+    }
 }
 
 /* ------------------------------------------------------------------- DOS */

@@ -206,6 +206,51 @@ __global__ void store_column_kernel(const void *src_, int64_t n, int B, int col,
     }
 }
 
+// Quasi-eigenstate accumulation after time step m = *counter + delta + 1:
+//   Q_e += pre * w_m * exp(i E_e t_m) * psi,  t_m = m h,  w_m = (1 + cos(pi m / N)) / 2,
+// Q: FP64 complex [n_e][n_pad]. The phases are formed once per block.
+template <typename R>
+__global__ void qe_accumulate_kernel(const void *psi_, double2 *Q, const double *energies, int n_e,
+                                     int64_t n_pad, const int *counter, int delta, double h, int N,
+                                     double pre)
+{
+    typedef typename V2<R>::T V;
+    extern __shared__ double2 ph[];
+    const int m = (counter ? *counter : 0) + delta + 1;
+    const double w = 0.5 * (1.0 + cospi((double)m / (double)N));
+    for (int e = threadIdx.x; e < n_e; e += blockDim.x) {
+        double sn, cs;
+        sincos(energies[e] * (double)m * h, &sn, &cs);
+        ph[e] = make_double2(pre * w * cs, pre * w * sn);
+    }
+    __syncthreads();
+    const V *psi = reinterpret_cast<const V *>(psi_);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += stride) {
+        const V v = psi[i];
+        const double vr = (double)v.x, vi = (double)v.y;
+        for (int e = 0; e < n_e; ++e) {
+            double2 q = Q[(int64_t)e * n_pad + i];
+            q.x = fma(ph[e].x, vr, fma(-ph[e].y, vi, q.x));
+            q.y = fma(ph[e].x, vi, fma(ph[e].y, vr, q.y));
+            Q[(int64_t)e * n_pad + i] = q;
+        }
+    }
+}
+
+// Q_e = pre * psi0 for every energy (the m = 0 term, w_0 = 1).
+template <typename R>
+__global__ void qe_init_kernel(const void *psi_, double2 *Q, int n_e, int64_t n_pad, double pre)
+{
+    typedef typename V2<R>::T V;
+    const V *psi = reinterpret_cast<const V *>(psi_);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += stride) {
+        const V v = psi[i];
+        for (int e = 0; e < n_e; ++e) Q[(int64_t)e * n_pad + i] = make_double2(pre * (double)v.x, pre * (double)v.y);
+    }
+}
+
 // Batch coefficients: zero c_k for k >= max(K_g, 3) of every instance g, so
 // that running more terms than an instance needs changes nothing (the
 // Clenshaw terms b_k of those orders stay exactly zero).
@@ -378,6 +423,30 @@ cudaError_t launch_store_column(int precision, const void *src, int64_t n, int B
         store_column_kernel<double><<<(int)blocks, 256, 0, s>>>(src, n, B, col, scale, d);
     else
         store_column_kernel<float><<<(int)blocks, 256, 0, s>>>(src, n, B, col, scale, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qe_accumulate(int precision, const void *psi, double2 *Q, const double *energies, int n_e,
+                                 int64_t n_pad, const int *counter, int delta, double h, int N, double pre,
+                                 cudaStream_t s)
+{
+    int64_t blocks = (n_pad + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    const size_t sm = sizeof(double2) * (size_t)n_e;
+    if (precision == TBPM_FP64)
+        qe_accumulate_kernel<double><<<(int)blocks, 256, sm, s>>>(psi, Q, energies, n_e, n_pad, counter, delta, h, N, pre);
+    else
+        qe_accumulate_kernel<float><<<(int)blocks, 256, sm, s>>>(psi, Q, energies, n_e, n_pad, counter, delta, h, N, pre);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qe_init(int precision, const void *psi, double2 *Q, int n_e, int64_t n_pad, double pre,
+                           cudaStream_t s)
+{
+    int64_t blocks = (n_pad + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (precision == TBPM_FP64) qe_init_kernel<double><<<(int)blocks, 256, 0, s>>>(psi, Q, n_e, n_pad, pre);
+    else qe_init_kernel<float><<<(int)blocks, 256, 0, s>>>(psi, Q, n_e, n_pad, pre);
     return cudaGetLastError();
 }
 

@@ -24,137 +24,12 @@
 // and the final sweep also accumulates <psi0|y> into per-block partials.
 // The KPM sweep (Sec. 1) is T_{m+1} = A T_m - T_{m-1} with the two dots that
 // the doubling identities need.
-#include "tbpm_internal.cuh"
+#include "sweep_ops.cuh"
 
 namespace tbpm {
 namespace {
 
-template <typename R> struct V2;
-template <> struct V2<double> { typedef double2 T; };
-template <> struct V2<float> { typedef float2 T; };
-
 enum BMode { B_ONE = 0, B_REAL = 1, B_IMAG = 2 };
-
-// Matrix streams are read once per sweep. For FP32 they are loaded with the
-// streaming (evict-first) cache operator so that they do not push the vectors,
-// which the next sweep reads again, out of L2; the FP64 sweeps are bound by the
-// FP64 pipe and keep the default policy.
-template <typename R, typename T>
-__device__ __forceinline__ T ldm(const T *p)
-{
-    if (sizeof(R) == 4) return __ldcs(p);
-    return __ldg(p);
-}
-
-// acc = A x for row `row` of a SELL slice, accumulated onto (ar, ai).
-template <typename R, bool REALV>
-__device__ __forceinline__ void sell_apply(const SweepParams &p, int64_t s, int lane,
-                                           const typename V2<R>::T *__restrict__ x,
-                                           R &ar, R &ai)
-{
-    typedef typename V2<R>::T V;
-    const int64_t off = ldm<R>(p.slice_off + s);
-    const int w = (int)((ldm<R>(p.slice_off + s + 1) - off) >> 5);
-    const int32_t *cp = p.cols + off + lane;
-    if (REALV) {
-        const R *vp = reinterpret_cast<const R *>(p.vals) + off + lane;
-        int j = 0;
-        for (; j + 4 <= w; j += 4) {
-            int c0 = ldm<R>(cp + 32 * j), c1 = ldm<R>(cp + 32 * (j + 1));
-            int c2 = ldm<R>(cp + 32 * (j + 2)), c3 = ldm<R>(cp + 32 * (j + 3));
-            R v0 = ldm<R>(vp + 32 * j), v1 = ldm<R>(vp + 32 * (j + 1));
-            R v2 = ldm<R>(vp + 32 * (j + 2)), v3 = ldm<R>(vp + 32 * (j + 3));
-            V x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
-            ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
-            ar = fma(v1, x1.x, ar); ai = fma(v1, x1.y, ai);
-            ar = fma(v2, x2.x, ar); ai = fma(v2, x2.y, ai);
-            ar = fma(v3, x3.x, ar); ai = fma(v3, x3.y, ai);
-        }
-        if (j + 2 <= w) {
-            int c0 = ldm<R>(cp + 32 * j), c1 = ldm<R>(cp + 32 * (j + 1));
-            R v0 = ldm<R>(vp + 32 * j), v1 = ldm<R>(vp + 32 * (j + 1));
-            V x0 = __ldg(x + c0), x1 = __ldg(x + c1);
-            ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
-            ar = fma(v1, x1.x, ar); ai = fma(v1, x1.y, ai);
-            j += 2;
-        }
-        if (j < w) {
-            int c0 = ldm<R>(cp + 32 * j);
-            R v0 = ldm<R>(vp + 32 * j);
-            V x0 = __ldg(x + c0);
-            ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
-        }
-    } else {
-        const V *vp = reinterpret_cast<const V *>(p.vals) + off + lane;
-        int j = 0;
-        for (; j + 2 <= w; j += 2) {
-            int c0 = ldm<R>(cp + 32 * j), c1 = ldm<R>(cp + 32 * (j + 1));
-            V v0 = ldm<R>(vp + 32 * j), v1 = ldm<R>(vp + 32 * (j + 1));
-            V x0 = __ldg(x + c0), x1 = __ldg(x + c1);
-            ar = fma(v0.x, x0.x, fma(-v0.y, x0.y, ar)); ai = fma(v0.x, x0.y, fma(v0.y, x0.x, ai));
-            ar = fma(v1.x, x1.x, fma(-v1.y, x1.y, ar)); ai = fma(v1.x, x1.y, fma(v1.y, x1.x, ai));
-        }
-        if (j < w) {
-            int c0 = ldm<R>(cp + 32 * j);
-            V v0 = ldm<R>(vp + 32 * j);
-            V x0 = __ldg(x + c0);
-            ar = fma(v0.x, x0.x, fma(-v0.y, x0.y, ar)); ai = fma(v0.x, x0.y, fma(v0.y, x0.x, ai));
-        }
-    }
-}
-
-// acc = A x - (on-site part excluded) for a periodic lattice row, onto (ar, ai).
-// Monolayer, row = 2 cell + s, cell = m1 L2 + m2:
-//   A(m) couples to B(m), B(m - a1), B(m - a2); B(m) to A(m), A(m + a1), A(m + a2).
-// Bilayer, row = 4 cell + o (o = A1, B1, A2, B2): each layer as above, plus the
-// dimer bond A1(m) - B2(m).
-template <typename R, int OP>
-__device__ __forceinline__ void stencil_apply(const SweepParams &p, int64_t row,
-                                              const typename V2<R>::T *__restrict__ x,
-                                              R &ar, R &ai)
-{
-    typedef typename V2<R>::T V;
-    // orbital counts are below 2^31, so the index arithmetic is 32-bit
-    const unsigned per = (OP == OP_STENCIL_MONO) ? 2u : 4u;
-    const unsigned r = (unsigned)row, L1 = (unsigned)p.l1, L2 = (unsigned)p.l2;
-    const unsigned cell = r / per;
-    const unsigned o = r - cell * per;
-    const unsigned m1 = cell / L2;
-    const unsigned m2 = cell - m1 * L2;
-    const unsigned base_o = o & 2u;                     // orbital of A in this layer
-    unsigned n0, n1, n2;                                // the three in-layer neighbours
-    if ((o & 1u) == 0) {                                // A: B(m), B(m-a1), B(m-a2)
-        const unsigned mm1 = (m1 == 0) ? L1 - 1 : m1 - 1;
-        const unsigned mm2 = (m2 == 0) ? L2 - 1 : m2 - 1;
-        n0 = cell * per + base_o + 1;
-        n1 = (mm1 * L2 + m2) * per + base_o + 1;
-        n2 = (m1 * L2 + mm2) * per + base_o + 1;
-    } else {                                            // B: A(m), A(m+a1), A(m+a2)
-        const unsigned pm1 = (m1 == L1 - 1) ? 0 : m1 + 1;
-        const unsigned pm2 = (m2 == L2 - 1) ? 0 : m2 + 1;
-        n0 = cell * per + base_o;
-        n1 = (pm1 * L2 + m2) * per + base_o;
-        n2 = (m1 * L2 + pm2) * per + base_o;
-    }
-    const V x0 = __ldg(x + n0), x1 = __ldg(x + n1), x2 = __ldg(x + n2);
-    const R t = (R)p.t;
-    ar = fma(t, x0.x + x1.x + x2.x, ar);
-    ai = fma(t, x0.y + x1.y + x2.y, ai);
-    if (OP == OP_STENCIL_BI && (o == 0 || o == 3)) {
-        const V xd = __ldg(x + (o == 0 ? cell * 4 + 3 : cell * 4));
-        const R tp = (R)p.t_perp;
-        ar = fma(tp, xd.x, ar);
-        ai = fma(tp, xd.y, ai);
-    }
-}
-
-// Warp-wide sum in a fixed butterfly order; every lane gets the result.
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // Coefficients of one sweep: a on psi (real, or imaginary if AIMAG), beta on A x.
 // For a batch of instances, coefficients and the renormalisation scale are

@@ -199,6 +199,7 @@ int init_device(tbpm_ctx *ctx, const tbpm_opts &o)
     CU(cudaMalloc(&ctx->d_coef, sizeof(double2) * kMaxTerms * ncoef));
     CU(cudaMalloc(&ctx->d_K, sizeof(int) * ncoef));
     CU(cudaMalloc(&ctx->d_counter, sizeof(int) * 4));
+    CU(cudaMalloc(&ctx->d_misc, sizeof(double) * 8));
     return TBPM_OK;
 }
 
@@ -391,7 +392,7 @@ int ensure_coeffs(tbpm_ctx *ctx, double x, int *K)
 // chunk writes dot partials to slot d, then one reduction stores
 // C(t_{base+1..base+len}) and the base counter advances.
 int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, int B, int64_t ld, cudaStream_t s,
-                      int64_t *launches)
+                      int64_t *launches, bool qe = false)
 {
     const SweepVariant v = variant(ctx, B);
     auto sweep = [&](SweepKind kind, bool a_imag, bool has_z, const SweepParams &p) {
@@ -445,6 +446,12 @@ int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, int B, int64_t ld, cudaStre
         p.delta = d;
         CU(sweep(SW_FINAL, false, K >= 4, p));
         ++*launches;
+        if (qe) {       // quasi-eigenstates: Q_e += dt/(2 pi) w_m exp(i E_e t_m) psi(t_m)
+            CU(launch_qe_accumulate(ctx->precision, ctx->d_psi, ctx->d_qe, ctx->d_qe_e, ctx->qe_ne, ctx->n_pad,
+                                    ctx->d_counter, d, ctx->qe_h, ctx->qe_N,
+                                    std::fabs(ctx->qe_h) / (2.0 * 3.141592653589793238462643383279502884), s));
+            ++*launches;
+        }
         if (renorm) {   // 1/||psi(t_{n+1})|| for the next step's sweeps
             if (B == 1)
                 CU(launch_renorm_seg(ctx->d_norm + (int64_t)d * npart, npart, ctx->d_seg_off, nseg,
@@ -492,19 +499,48 @@ int enqueue_kpm_chunk(tbpm_ctx *ctx, int len, cudaStream_t s, int64_t *launches)
     return TBPM_OK;
 }
 
+// Enqueues `len` Haydock iterations starting at an even index n (u_n in
+// d_psi for even n, in d_b0 for odd n); a_n and b_{n+1} go to d_out viewed as
+// double[2 M] (a at [0, M), b at [M, 2 M)).
+int enqueue_hay_chunk(tbpm_ctx *ctx, int len, int M, cudaStream_t s, int64_t *launches)
+{
+    const SweepVariant v = variant(ctx, 1);
+    SweepParams p;
+    fill_operator(ctx, p);
+    p.partials = ctx->d_partials;
+    const int64_t W = (int64_t)ctx->nblk * (kBlockB1 / 32);
+    double *aout = reinterpret_cast<double *>(ctx->d_out);
+    double *bout = aout + M;
+    void *U[2] = {ctx->d_psi, ctx->d_b0};
+    for (int d = 0; d < len; ++d) {
+        p.x = U[d & 1];
+        p.y = U[(d + 1) & 1];
+        CU(launch_hay_apply(v, p, ctx->d_misc, 0.5 * ctx->rescale, ctx->nblk, s));
+        CU(launch_hay_scalar(1, ctx->d_partials, W, ctx->d_misc, aout, ctx->d_counter, s));
+        CU(launch_hay_update(ctx->precision, U[d & 1], U[(d + 1) & 1], p.nslices, ctx->d_misc, ctx->d_partials,
+                             ctx->nblk, s));
+        CU(launch_hay_scalar(2, ctx->d_partials, W, ctx->d_misc, bout, ctx->d_counter, s));
+        *launches += 4;
+    }
+    return TBPM_OK;
+}
+
 // Runs (and on first use captures) the graph of one chunk.
 int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_t ld = 0)
 {
     // kind 0: DOS, one state; 1: KPM, one state; 2: DOS, 16 states; 3: DOS, batch of
-    // instances (ld = n_steps + 1 for kinds 2 and 3)
+    // instances (ld = n_steps + 1 for kinds 2 and 3); 4: Haydock (ld = M); 5: DOS with
+    // quasi-eigenstate accumulation (one state; dropped at the end of the call)
     const auto key = std::make_tuple(kind, len, K, (int)ld);
     auto it = ctx->graphs.find(key);
     int64_t nl = 0;
     if (it == ctx->graphs.end()) {
         cudaGraph_t g;
         CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-        int rc = kind == 1 ? enqueue_kpm_chunk(ctx, len, ctx->cap_stream, &nl)
-                           : enqueue_dos_chunk(ctx, K, len, kind == 2 ? 16 : 1, ld, ctx->cap_stream, &nl);
+        int rc = kind == 1   ? enqueue_kpm_chunk(ctx, len, ctx->cap_stream, &nl)
+                 : kind == 4 ? enqueue_hay_chunk(ctx, len, (int)ld, ctx->cap_stream, &nl)
+                             : enqueue_dos_chunk(ctx, K, len, kind == 2 ? 16 : 1, ld, ctx->cap_stream, &nl,
+                                                 kind == 5);
         cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
         if (rc) return rc;
         CU(e);
@@ -514,8 +550,9 @@ int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_
         CU(ei);
         it = ctx->graphs.emplace(key, ex).first;
     } else {
-        nl = kind == 1 ? (int64_t)len + 2 : (int64_t)len * (K - 1) + 2;
-        if (kind != 1 && (ctx->flags & TBPM_F_RENORM)) nl += len;
+        nl = kind == 1 ? (int64_t)len + 2 : kind == 4 ? 4 * (int64_t)len : (int64_t)len * (K - 1) + 2;
+        if (kind != 1 && kind != 4 && (ctx->flags & TBPM_F_RENORM)) nl += len;
+        if (kind == 5) nl += len;
     }
     CU(cudaGraphLaunch(it->second, ctx->stream));
     *launches += nl;
@@ -584,7 +621,7 @@ static int check_opts(const tbpm_opts *in, tbpm_opts *o)
     if (o->precision != TBPM_FP64 && o->precision != TBPM_FP32) return TBPM_ERR_ARG;
     if (o->path < TBPM_PATH_AUTO || o->path > TBPM_PATH_STENCIL) return TBPM_ERR_ARG;
     if (o->flags & ~(unsigned)(TBPM_F_NO_HERMITIAN_CHECK | TBPM_F_FORCE_RESCALE | TBPM_F_RENORM |
-                               TBPM_F_NO_CLUSTER))
+                               TBPM_F_NO_CLUSTER | TBPM_F_AUTOTUNE))
         return TBPM_ERR_ARG;
     if (o->bessel_tol == 0.0) o->bessel_tol = 1e-12;
     if (!(o->bessel_tol > 0.0 && o->bessel_tol < 1e-2)) return TBPM_ERR_ARG;
@@ -597,6 +634,59 @@ static int finish_create(tbpm_ctx *ctx, const tbpm_opts &o)
     if (rc) return rc;
     ctx->nblk = sweep_grid(variant(ctx, 1), ctx->num_sms);
     ctx->nblk16 = sweep_grid_b16(ctx->num_sms);
+    return TBPM_OK;
+}
+
+// Autotuner (TBPM_F_AUTOTUNE): times middle sweeps of this context's operator
+// for grids of 1 .. occupancy blocks per SM (and twice the occupancy) and
+// keeps the fastest. The dot partials are per warp of the chosen grid, which
+// is then fixed for the life of the context, so results stay reproducible
+// from call to call. Runs once, before any graph is captured.
+static int autotune(tbpm_ctx *ctx)
+{
+    if (ctx->tuned) return TBPM_OK;
+    int rc;
+    if ((rc = ensure_work(ctx, 1, 1, 0))) return rc;
+    const int occ = std::max(1, ctx->nblk / ctx->num_sms);
+    CU(cudaMemsetAsync(ctx->d_coef, 0, sizeof(double2) * kMaxTerms * std::max(1, ctx->ninst), ctx->stream));
+    ctx->K_cached = -1;
+    ctx->dt_cached.clear();
+    SweepParams p;
+    fill_operator(ctx, p);
+    p.coef = ctx->d_coef;
+    p.psi = ctx->d_psi;
+    p.x = ctx->d_b0;
+    p.y = ctx->d_b1;
+    p.z = ctx->d_b1;
+    p.ia = 1; p.ib = -1; p.ic = -1; p.bscale = 1.0;
+    p.slice_inst = ctx->d_slice_inst;
+    const SweepVariant v = variant(ctx, 1);
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_g = ctx->nblk;
+    ctx->tune_ms.clear();
+    for (int k = 1; k <= 2 * occ; ++k) {
+        if (k > occ && k != 2 * occ) continue;
+        const int grid = k * ctx->num_sms;
+        CU(launch_sweep(v, SW_MID, true, true, p, grid, ctx->stream));        // warm
+        CU(cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < 3; ++r) CU(launch_sweep(v, SW_MID, true, true, p, grid, ctx->stream));
+        CU(cudaEventRecord(e1, ctx->stream));
+        CU(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        ctx->tune_ms.emplace_back(k, ms / 3);
+        if (ms < best) { best = ms; best_g = grid; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // work buffers and graphs depend on the grid: rebuild them for the new one
+    destroy_graphs(ctx);
+    ctx->nblk = best_g;
+    ctx->cap_states = 0;
+    ctx->tuned = true;
     return TBPM_OK;
 }
 
@@ -630,7 +720,8 @@ int tbpm_create(tbpm_ctx **out, int64_t n, const int64_t *row_ptr, const int32_t
     ctx->n_pad = (n + kSlice - 1) / kSlice * kSlice;
     ctx->rescale = rescale;
     ctx->gershgorin = m.gershgorin;
-    if ((rc = finish_create(ctx, o)) || (rc = setup_sell(ctx, m))) {
+    if ((rc = finish_create(ctx, o)) || (rc = setup_sell(ctx, m)) ||
+        ((o.flags & TBPM_F_AUTOTUNE) && (rc = autotune(ctx)))) {
         tbpm_destroy(ctx);
         return rc;
     }
@@ -703,6 +794,7 @@ int tbpm_create_lattice(tbpm_ctx **out, const tbpm_lattice *lat, double rescale,
             }
         }
     }
+    if (!rc && (o.flags & TBPM_F_AUTOTUNE)) rc = autotune(ctx);
     if (rc) {
         tbpm_destroy(ctx);
         return rc;
@@ -723,6 +815,7 @@ void tbpm_destroy(tbpm_ctx *ctx)
     cudaFree(ctx->d_partials); cudaFree(ctx->d_out); cudaFree(ctx->d_stage); cudaFree(ctx->d_misc);
     cudaFree(ctx->d_norm); cudaFree(ctx->d_scale);
     cudaFree(ctx->d_slice_inst); cudaFree(ctx->d_seg_off); cudaFree(ctx->d_cpart);
+    cudaFree(ctx->d_qe); cudaFree(ctx->d_qe_e);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     cudaGetLastError();
@@ -1088,7 +1181,8 @@ int tbpm_create_batch(tbpm_ctx **out, int ninst, const tbpm_instance *inst, cons
     for (int g = 0; g <= ninst; ++g) seg[g] = rows[g] / kSlice;
     for (int g = 0; g < ninst; ++g)
         for (int64_t q = seg[g]; q < seg[g + 1]; ++q) sinst[q] = g;
-    if ((rc = upload(ctx, (void **)&ctx->d_slice_inst, sinst)) || (rc = upload(ctx, (void **)&ctx->d_seg_off, seg))) {
+    if ((rc = upload(ctx, (void **)&ctx->d_slice_inst, sinst)) || (rc = upload(ctx, (void **)&ctx->d_seg_off, seg)) ||
+        ((o.flags & TBPM_F_AUTOTUNE) && (rc = autotune(ctx)))) {
         tbpm_destroy(ctx);
         return rc;
     }
@@ -1171,6 +1265,152 @@ int tbpm_batch_dos_corr(tbpm_ctx *ctx, const double *psi0, const double *dt, int
     return TBPM_OK;
 }
 
+int tbpm_quasi_eigenstates(tbpm_ctx *ctx, const double *psi0, double dt, int n_steps, const double *energies,
+                           int n_e, double *qe)
+{
+    if (!ctx || !psi0 || !energies || !qe || n_steps < 1 || n_e < 1 || n_e > 4096) return TBPM_ERR_ARG;
+    if (ctx->ninst > 0) return TBPM_ERR_UNSUPPORTED;
+    if (!(dt > 0.0) || !std::isfinite(dt) || !(dt * ctx->rescale <= 40.0)) return TBPM_ERR_ARG;
+    CU(cudaSetDevice(ctx->device));
+    bool in_dev, e_dev, q_dev;
+    int rc;
+    if ((rc = classify(ctx, psi0, &in_dev)) || (rc = classify(ctx, energies, &e_dev)) || (rc = classify(ctx, qe, &q_dev)))
+        return rc;
+    const int64_t n = ctx->n, n_pad = ctx->n_pad;
+    if ((rc = ensure_work(ctx, 1, (size_t)n_steps + 1, in_dev ? 0 : (size_t)2 * n))) return rc;
+    const size_t qcap = (size_t)n_e * n_pad;
+    if (qcap > ctx->qe_cap) {
+        destroy_graphs(ctx);
+        cudaFree(ctx->d_qe);
+        ctx->d_qe = nullptr;
+        ctx->qe_cap = 0;
+        CU(cudaMalloc(&ctx->d_qe, qcap * sizeof(double2)));
+        ctx->qe_cap = qcap;
+    }
+    if ((size_t)n_e > ctx->qe_e_cap) {
+        destroy_graphs(ctx);
+        cudaFree(ctx->d_qe_e);
+        ctx->d_qe_e = nullptr;
+        ctx->qe_e_cap = 0;
+        CU(cudaMalloc(&ctx->d_qe_e, sizeof(double) * n_e));
+        ctx->qe_e_cap = n_e;
+    }
+    CU(cudaMemcpyAsync(ctx->d_qe_e, energies, sizeof(double) * n_e,
+                       e_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    const double *src;
+    if ((rc = stage_input(ctx, psi0, in_dev, (size_t)2 * n, &src))) return rc;
+    CU(launch_load_states(ctx->precision, src, n, n_pad, 1, 0, 1, ctx->d_psi0, ctx->d_psi, ctx->stream));
+    const double pre = dt / (2.0 * 3.141592653589793238462643383279502884);
+    CU(launch_qe_init(ctx->precision, ctx->d_psi0, ctx->d_qe, n_e, n_pad, pre, ctx->stream));
+    int64_t launches = 2, passes = 0;
+    for (int dir = 0; dir < 2; ++dir) {
+        const double h = dir == 0 ? dt : -dt;
+        int K;
+        if ((rc = ensure_coeffs(ctx, h * ctx->rescale, &K))) return rc;
+        const int Ke = std::max(K, 3);
+        passes += (int64_t)n_steps * (Ke - 1);
+        CU(cudaMemcpyAsync(ctx->d_psi, ctx->d_psi0, vec_bytes(ctx->precision) * n_pad, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
+        if (ctx->flags & TBPM_F_RENORM) {
+            CU(launch_renorm(nullptr, 0, 1, ctx->d_scale, ctx->stream));
+            ++launches;
+        }
+        ctx->qe_h = h;
+        ctx->qe_N = n_steps;
+        ctx->qe_ne = n_e;
+        int done = 0;
+        while (done < n_steps) {
+            const int len = std::min(kChunk, n_steps - done);
+            if ((rc = run_chunk(ctx, 5, Ke, len, &launches, 2 * (int64_t)n_steps + dir))) return rc;
+            done += len;
+        }
+    }
+    CU(cudaMemcpy2DAsync(qe, sizeof(double2) * n, ctx->d_qe, sizeof(double2) * n_pad, sizeof(double2) * n, n_e,
+                         q_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    // the quasi-eigenstate graphs bake this call's dt and energies
+    for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
+        if (std::get<0>(it->first) == 5) {
+            cudaGraphExecDestroy(it->second);
+            it = ctx->graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    CU(cudaGetLastError());
+    ctx->last_passes = passes;
+    ctx->last_launches = launches;
+    return TBPM_OK;
+}
+
+int tbpm_haydock(tbpm_ctx *ctx, const double *psi0, int M, double *a, double *b)
+{
+    if (!ctx || !psi0 || !a || !b || M < 1) return TBPM_ERR_ARG;
+    if (ctx->ninst > 0) return TBPM_ERR_UNSUPPORTED;
+    CU(cudaSetDevice(ctx->device));
+    bool in_dev, a_dev, b_dev;
+    int rc;
+    if ((rc = classify(ctx, psi0, &in_dev)) || (rc = classify(ctx, a, &a_dev)) || (rc = classify(ctx, b, &b_dev)))
+        return rc;
+    const int64_t n = ctx->n;
+    if ((rc = ensure_work(ctx, 1, (size_t)M, in_dev ? 0 : (size_t)2 * n))) return rc;
+    const size_t vb = vec_bytes(ctx->precision) * (size_t)ctx->n_pad;
+    const double *src;
+    if ((rc = stage_input(ctx, psi0, in_dev, (size_t)2 * n, &src))) return rc;
+    CU(launch_load_states(ctx->precision, src, n, ctx->n_pad, 1, 0, 1, ctx->d_psi0, ctx->d_psi, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_b0, 0, vb, ctx->stream));                 // u_{-1} = 0
+    const int64_t W = (int64_t)ctx->nblk * (kBlockB1 / 32);
+    CU(launch_dot(ctx->precision, ctx->d_psi, ctx->d_psi, ctx->n_pad / kSlice, ctx->d_partials, ctx->nblk, false,
+                  ctx->stream));
+    CU(launch_hay_scalar(0, ctx->d_partials, W, ctx->d_misc, nullptr, ctx->d_counter, ctx->stream));
+    int64_t launches = 3;
+    int done = 0;
+    while (done < M) {
+        const int len = std::min(kChunk, M - done);
+        if ((rc = run_chunk(ctx, 4, 0, len, &launches, M))) return rc;
+        done += len;
+    }
+    const double *dout = reinterpret_cast<const double *>(ctx->d_out);
+    CU(cudaMemcpyAsync(a, dout, sizeof(double) * M, a_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaMemcpyAsync(b, dout + M, sizeof(double) * M, b_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    if (!in_dev || !a_dev || !b_dev) CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaGetLastError());
+    ctx->last_passes = 2 * (int64_t)M;
+    ctx->last_launches = launches;
+    return TBPM_OK;
+}
+
+int tbpm_haydock_ldos(tbpm_ctx *ctx, const double *a, const double *b, int M, const double *energies, int n_e,
+                      double eta, double *ldos)
+{
+    if (!ctx || !a || !b || !energies || !ldos || M < 1 || n_e < 1) return TBPM_ERR_ARG;
+    if (!(eta > 0.0) || !std::isfinite(eta)) return TBPM_ERR_ARG;
+    CU(cudaSetDevice(ctx->device));
+    bool a_dev, b_dev, e_dev, l_dev;
+    int rc;
+    if ((rc = classify(ctx, a, &a_dev)) || (rc = classify(ctx, b, &b_dev)) || (rc = classify(ctx, energies, &e_dev)) ||
+        (rc = classify(ctx, ldos, &l_dev)))
+        return rc;
+    if ((rc = ensure_work(ctx, 1, 0, 2 * (size_t)M + 2 * (size_t)n_e))) return rc;
+    double *st = ctx->d_stage;
+    const double *da = a, *db = b, *de = energies;
+    if (!a_dev) { CU(cudaMemcpyAsync(st, a, sizeof(double) * M, cudaMemcpyHostToDevice, ctx->stream)); da = st; }
+    if (!b_dev) { CU(cudaMemcpyAsync(st + M, b, sizeof(double) * M, cudaMemcpyHostToDevice, ctx->stream)); db = st + M; }
+    if (!e_dev) {
+        CU(cudaMemcpyAsync(st + 2 * M, energies, sizeof(double) * n_e, cudaMemcpyHostToDevice, ctx->stream));
+        de = st + 2 * M;
+    }
+    double *dl = l_dev ? ldos : st + 2 * M + n_e;
+    CU(launch_hay_ldos(da, db, M, de, n_e, eta, dl, ctx->stream));
+    if (!l_dev) CU(cudaMemcpyAsync(ldos, dl, sizeof(double) * n_e, cudaMemcpyDeviceToHost, ctx->stream));
+    if (!a_dev || !b_dev || !e_dev || !l_dev) CU(cudaStreamSynchronize(ctx->stream));
+    ctx->last_launches = 1;
+    return TBPM_OK;
+}
+
 int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info)
 {
     if (!ctx || !info) return TBPM_ERR_ARG;
@@ -1184,6 +1424,8 @@ int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info)
     info->kernel_launches = ctx->last_launches;
     info->gershgorin = ctx->gershgorin;
     info->rescale = ctx->rescale;
+    info->grid_blocks = ctx->nblk;
+    info->tuned = ctx->tuned ? 1 : 0;
     return TBPM_OK;
 }
 

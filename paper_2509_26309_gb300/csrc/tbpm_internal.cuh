@@ -165,6 +165,15 @@ struct tbpm_ctx {
     int64_t *d_seg_off = nullptr;        // first slice of each instance, size ninst+1
     std::vector<double> dt_cached;
     int K_batch = 0;                     // max over instances of max(K_g, 3)
+    // quasi-eigenstates of the current call (enqueued after each final sweep)
+    double2 *d_qe = nullptr;             // [n_e][n_pad]
+    double *d_qe_e = nullptr;            // energies [n_e]
+    size_t qe_cap = 0, qe_e_cap = 0;
+    int qe_ne = 0, qe_N = 0;
+    double qe_h = 0.0;
+    // autotuner: (blocks per SM, ms per middle sweep) of each candidate grid
+    bool tuned = false;
+    std::vector<std::pair<int, float>> tune_ms;
     // cached executable graphs keyed by (kind, len, K, states)
     std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
     // counters of the last call
@@ -224,6 +233,30 @@ cudaError_t launch_cluster_dos(int precision, bool real_values, const SweepParam
 // buffer (scale may be null) (aux.cu).
 cudaError_t launch_store_column(int precision, const void *src, int64_t n, int B, int col,
                                 const double *scale, double *dst, cudaStream_t s);
+
+// Haydock recursion (haydock.cu). Device scalars sc[4] = {s_n, b_n, s_{n-1}, a_n}.
+// apply: w = (rescale/2) s_n A u_n - b_n s_{n-1} u_{n-1} into p.y (= u_{n-1}),
+//        per-warp <u_n|w> partials into p.partials (p.x = u_n);
+// update: w <- w - a_n s_n u (in place), per-warp ||w||^2 partials;
+// scalar: 0 init from ||psi0||^2 partials, 1 a_n (to out[*counter]),
+//         2 b_{n+1} (to out[*counter]) and counter + 1.
+cudaError_t launch_hay_apply(const SweepVariant &v, const SweepParams &p, const double *sc,
+                             double half_rescale, int grid, cudaStream_t s);
+cudaError_t launch_hay_update(int precision, const void *u, void *w, int64_t nslices, const double *sc,
+                              double2 *partials, int grid, cudaStream_t s);
+cudaError_t launch_hay_scalar(int which, const double2 *partials, int64_t W, double *sc, double *out,
+                              int *counter, cudaStream_t s);
+cudaError_t launch_hay_ldos(const double *a, const double *b, int M, const double *energies, int n_e,
+                            double eta, double *ldos, cudaStream_t s);
+
+// Quasi-eigenstates (aux.cu): Q [n_e][n_pad] FP64 complex.
+//   init: Q_e = pre psi;  accumulate after step m = *counter + delta + 1:
+//   Q_e += pre w_m exp(i E_e m h) psi, w_m = (1 + cos(pi m / N)) / 2.
+cudaError_t launch_qe_accumulate(int precision, const void *psi, double2 *Q, const double *energies, int n_e,
+                                 int64_t n_pad, const int *counter, int delta, double h, int N, double pre,
+                                 cudaStream_t s);
+cudaError_t launch_qe_init(int precision, const void *psi, double2 *Q, int n_e, int64_t n_pad, double pre,
+                           cudaStream_t s);
 
 // coef[g * kMaxTerms + k] = 0 for k >= max(K[g], 3) (aux.cu).
 cudaError_t launch_mask_coef(double2 *coef, const int *K, int ninst, cudaStream_t s);

@@ -36,6 +36,7 @@ TBPM_F_NO_HERMITIAN_CHECK = 0x1
 TBPM_F_FORCE_RESCALE = 0x2
 TBPM_F_RENORM = 0x4
 TBPM_F_NO_CLUSTER = 0x8
+TBPM_F_AUTOTUNE = 0x10
 TBPM_LATTICE_GRAPHENE = 0
 TBPM_LATTICE_AB_BILAYER = 1
 
@@ -53,7 +54,8 @@ class tbpm_lattice(C.Structure):
 class tbpm_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("path", C.c_int), ("precision", C.c_int),
                 ("real_values", C.c_int), ("num_terms", C.c_int), ("passes", C.c_int64),
-                ("kernel_launches", C.c_int64), ("gershgorin", C.c_double), ("rescale", C.c_double)]
+                ("kernel_launches", C.c_int64), ("gershgorin", C.c_double), ("rescale", C.c_double),
+                ("grid_blocks", C.c_int), ("tuned", C.c_int)]
 
 
 class TbpmError(RuntimeError):
@@ -80,6 +82,11 @@ SIGNATURES = {
     "tbpm_strerror": (C.c_char_p, [C.c_int]),
     "tbpm_propagate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p,
                                  C.c_void_p]),
+    "tbpm_haydock": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "tbpm_quasi_eigenstates": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_int,
+                                         C.c_void_p]),
+    "tbpm_haydock_ldos": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                    C.c_double, C.c_void_p]),
     "tbpm_create_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "tbpm_batch_dos_corr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "tbpm_dos_corr_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
@@ -305,6 +312,45 @@ def kpm_moments(ctx: Ctx, psi0, M: int, out=None):
         out = _alloc((ns, M), np.complex128, cuda, a.device if cuda else None)
     _check(lib().kpm_moments(ctx.handle, _ptr(a), ns, int(M), _ptr(out)), "kpm_moments")
     return out[0] if (a.ndim == 1 and out.shape[0] == 1) else out
+
+
+def tbpm_quasi_eigenstates(ctx: Ctx, psi0, dt: float, n_steps: int, energies):
+    """Psi(E_e) for each energy: complex128 (n_e, n)."""
+    a, ns, cuda = _complex_in(psi0, ctx.n)
+    if ns != 1:
+        raise ValueError("tbpm_quasi_eigenstates takes one state")
+    if not _is_torch(energies):
+        energies = np.ascontiguousarray(energies, dtype=np.float64)
+    n_e = int(energies.shape[0])
+    out = _alloc((n_e, ctx.n), np.complex128, cuda, a.device if cuda else None)
+    _check(lib().tbpm_quasi_eigenstates(ctx.handle, _ptr(a), float(dt), int(n_steps), _ptr(energies), n_e,
+                                        _ptr(out)), "tbpm_quasi_eigenstates")
+    return out
+
+
+def tbpm_haydock(ctx: Ctx, psi0, M: int):
+    """Haydock recursion coefficients (a[M], b[M]) from psi0, b[n] = b_{n+1}."""
+    a_, ns, cuda = _complex_in(psi0, ctx.n)
+    if ns != 1:
+        raise ValueError("tbpm_haydock takes one start state")
+    dev = a_.device if cuda else None
+    a = _alloc((M,), np.float64, cuda, dev)
+    b = _alloc((M,), np.float64, cuda, dev)
+    _check(lib().tbpm_haydock(ctx.handle, _ptr(a_), int(M), _ptr(a), _ptr(b)), "tbpm_haydock")
+    return a, b
+
+
+def tbpm_haydock_ldos(ctx: Ctx, a, b, energies, eta: float):
+    """LDOS -Im G(E + i eta)/pi from the recursion coefficients (numpy or torch)."""
+    cuda = _is_torch(a) and a.is_cuda
+    if not _is_torch(a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        energies = np.ascontiguousarray(energies, dtype=np.float64)
+    out = _alloc((energies.shape[0],), np.float64, cuda, a.device if cuda else None)
+    _check(lib().tbpm_haydock_ldos(ctx.handle, _ptr(a), _ptr(b), int(a.shape[0]), _ptr(energies),
+                                   int(energies.shape[0]), float(eta), _ptr(out)), "tbpm_haydock_ldos")
+    return out
 
 
 def tbpm_dos_from_corr(ctx: Ctx, corr, dt: float):

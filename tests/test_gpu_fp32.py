@@ -81,6 +81,22 @@ def test_fp32_batched_stencil(orc, kind):
         assert np.max(np.abs(c[j] - ref)) <= C_TOL
 
 
+@pytest.mark.parametrize("stencil", [False, True])
+def test_fp32_batched_large(orc, stencil):
+    """16 states on 512x512 graphene (N = 524,288; 268 MB of state vectors, beyond L2)."""
+    l = 512
+    n = 2 * l * l
+    eps = ti.anderson_onsite(n, 1.0, 1)
+    h = ti.graphene_csr(l, l, onsite=eps)
+    opts = tb.make_opts(precision=tb.TBPM_FP32)
+    ctx = (tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l, l, -2.7, 0.0, eps, 9.0, opts) if stencil
+           else tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, 9.0, opts))
+    psi = np.stack([ti.random_phase_state(n, j) for j in range(16)])
+    c = tb.tbpm_dos_corr(ctx, psi, DT, 6)
+    for j in (0, 15):
+        assert np.max(np.abs(c[j] - orc.dos_corr(h, 9.0, psi[j], DT, 6))) <= C_TOL
+
+
 def test_fp32_device_block(orc):
     torch = pytest.importorskip("torch")
     h = ti.graphene_csr(32, 32, onsite=ti.anderson_onsite(2048, 1.0, 4))

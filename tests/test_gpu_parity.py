@@ -193,6 +193,23 @@ def test_propagate_fp32_renorm_and_batched(orc):
         assert np.max(np.abs(psi[3] - rpsi)) < 1e-4
 
 
+def test_autotuned_grid(orc):
+    """The autotuner picks a grid (whole blocks per SM) once at create;
+    results match the oracle and repeat bit for bit on the context."""
+    h = ti.graphene_csr(128, 100, onsite=ti.anderson_onsite(25600, 1.0, 2))
+    psi0 = ti.random_phase_state(h.n, 1)
+    ctx = create(h, flags=tb.TBPM_F_AUTOTUNE | tb.TBPM_F_NO_CLUSTER)
+    info = tb.tbpm_get_info(ctx)
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert info["tuned"] == 1 and info["grid_blocks"] % sms == 0
+    c = tb.tbpm_dos_corr(ctx, psi0, DT, 40)
+    assert np.max(np.abs(c - orc.dos_corr(h, 9.0, psi0, DT, 40))) <= TOL
+    assert np.array_equal(c, tb.tbpm_dos_corr(ctx, psi0, DT, 40))
+    mu = tb.kpm_moments(ctx, psi0, 100)
+    assert np.max(np.abs(mu - orc.kpm_moments(h, 9.0, psi0, 100))) <= TOL
+
+
 def test_dos_transforms(orc):
     h = ti.graphene_csr(16, 16, onsite=ti.anderson_onsite(512, 1.0, 1))
     psi0 = ti.random_phase_state(h.n, 0)

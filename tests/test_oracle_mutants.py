@@ -12,7 +12,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
-PINS = ["tests/test_oracle_bessel.py", "tests/test_oracle_propagation.py",
+PINS = ["tests/test_oracle_bessel.py", "tests/test_oracle_propagation.py", "tests/test_oracle_haydock.py",
+        "tests/test_oracle_qe.py",
         "tests/test_oracle_kpm.py", "tests/test_oracle_dos.py"]
 
 # name: [(original text, planted text)], each original must occur in oracle.c
@@ -33,7 +34,7 @@ MUTANTS = {
                           "if (corr) corr[s + 1] = dot(n, psi0, out);")],
     "kpm_index": [("mu[m] = dot(n, psi0, t2);", "mu[m] = dot(n, psi0, t1);")],
     "kpm_recurrence_sign": [("t2[i] -= t0[i];\n        mu[m]", "t2[i] += t0[i];\n        mu[m]")],
-    "hann_window_sign": [("double w = 0.5 * (1.0 + cos(", "double w = 0.5 * (1.0 - cos(")],
+    "hann_window_sign": [("double w = 0.5 * (1.0 + cos(PI * (double)m", "double w = 0.5 * (1.0 - cos(PI * (double)m")],
     "hann_no_conj": [("cplx cm = m < 0 ? conj(corr[a]) : corr[a];", "cplx cm = corr[a];")],
     "hann_norm": [("acc *= dt / (2.0 * PI);", "acc *= dt / PI;")],
     "hann_phase_sign": [("acc += w * cm * cexp(I * e * t);", "acc += w * cm * cexp(-I * e * t);")],
@@ -41,6 +42,14 @@ MUTANTS = {
     "kpm_dos_factor_two": [("s += 2.0 * g[m] * mu_re[m]", "s += g[m] * mu_re[m]")],
     "kpm_dos_rescale": [("rho[j] = s / (PI * sqrt(1.0 - x * x)) / rescale;",
                          "rho[j] = s / (PI * sqrt(1.0 - x * x));")],
+    "haydock_tail_not_squared": [("b[m] * b[m] * g;", "b[m] * g;")],
+    "haydock_no_previous_term": [("w[i] -= bn * vp[i];", "w[i] -= 0.0 * vp[i];")],
+    "haydock_eta_sign": [("cplx z = energies[j] + I * eta;", "cplx z = energies[j] - I * eta;")],
+    "haydock_stale_vector": [("vp[i] = v[i]; v[i] = w[i] / bm;", "vp[i] = v[i]; v[i] = w[i];")],
+    "qe_phase_sign": [("cplx ph = pre * w * cexp(I * energies[e] * t);",
+                       "cplx ph = pre * w * cexp(-I * energies[e] * t);")],
+    "qe_forward_only": [("for (int dir = 0; dir < 2; ++dir) {", "for (int dir = 0; dir < 1; ++dir) {")],
+    "qe_no_window": [("double w = 0.5 * (1.0 + cos(PI * (double)s / (double)N));", "double w = 1.0;")],
 }
 
 
