@@ -324,74 +324,149 @@ def timed_calls(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
+def dos_l1(ctx, corr, ref, dt):
+    """DOS L1 relative error of corr against ref (both C(t_n) rows), through the
+    library's Hann-windowed transform."""
+    import numpy as np
+    import paper_2509_26309_gb300 as tb
+    _, d = tb.tbpm_dos_from_corr(ctx, np.asarray(corr), dt)
+    _, r = tb.tbpm_dos_from_corr(ctx, np.asarray(ref), dt)
+    return float(np.sum(np.abs(d - r)) / np.sum(np.abs(r)))
+
+
 def run_variants(args, dev, stream):
     """The precision and batching patterns, each timed with CUDA events on
     device-resident inputs (not part of the headline value):
-      - FP32 single state, stored matrix: graphene 2048x2048, W = 1 (N = 8,388,608),
-        1024 steps;
+      - FP64 64x64 pristine graphene (N = 8192), 1024 steps: one cluster launch
+        against one graph-launched kernel per sweep;
+      - FP64 uneven batch of 40 lattices in one context (autotuned grid),
+        dt_g = pi/rescale_g (K = 18 for every instance), 256 steps, against the
+        same instances one context at a time;
+      - FP32 single state, stored matrix: graphene 2048x2048, W = 1
+        (N = 8,388,608), 1024 steps, with and without renormalisation, DOS L1
+        error against the FP64 run of the same state;
       - FP32 block of 16 states vs FP64 single state on graphene 4096x4096,
-        W = 1 (N = 33,554,432, the paper's benchmark lattice), stencil path,
-        32 steps each (the speedup is a throughput ratio, so the step count
-        only sets the sample length)."""
+        W = 1 (N = 33,554,432, the paper's benchmark lattice), stencil and
+        stored-matrix paths, 32 steps each (the speedup is a throughput ratio,
+        so the step count only sets the sample length); DOS L1 of state 0.
+    The FP64 runs the errors are taken against are the path the parity tests
+    hold to 1e-10 of the oracle."""
     import numpy as np
     import torch
     import tbpm_inputs as ti
     import paper_2509_26309_gb300 as tb
     res = {}
+    so = stream.cuda_stream
     # config 1: 64x64 pristine graphene (N = 8192), FP64, 1024 steps: the
     # single-launch cluster path against one graph-launched kernel per sweep
     h1 = ti.graphene_csr(64, 64)
     p1 = torch.from_numpy(ti.random_phase_state(h1.n, 0).reshape(1, h1.n)).to(dev)
     o1 = torch.empty((1, 1025), dtype=torch.complex128, device=dev)
     for name, flags in (("fp64_cluster_64x64", 0), ("fp64_graph_64x64", tb.TBPM_F_NO_CLUSTER)):
-        c1 = tb.tbpm_create(h1.n, h1.row_ptr, h1.col, h1.val, RESCALE,
-                            tb.make_opts(flags=flags, stream=stream.cuda_stream))
+        c1 = tb.tbpm_create(h1.n, h1.row_ptr, h1.col, h1.val, RESCALE, tb.make_opts(flags=flags, stream=so))
         ms1 = timed_calls(lambda: tb.tbpm_dos_corr(c1, p1, DT, 1024, out=o1), 3, stream)
         K1 = tb.tbpm_get_info(c1)["num_terms"]
         res[name] = {"value": h1.n * 1024 * (K1 - 1) / (ms1 / 1e3), "unit": UNIT, "ms_per_call": ms1,
                      "states": 1, "n_steps": 1024}
         tb.tbpm_destroy(c1)
-    # config 3: FP32 single state, SELL
+    # config 5: uneven batch of 40 lattices (monolayer / AB bilayer, N log-uniform
+    # 1e4..4e6, per-instance W and rescale), FP64, one block-diagonal operator
+    # with an autotuned grid, against the same 40 instances one context at a time
+    insts = ti.batch_instances()
+    n5 = sum(i.csr.n for i in insts)
+    steps5 = 256
+    dts = [math.pi / i.rescale for i in insts]
+    psi5 = torch.from_numpy(np.concatenate([ti.random_phase_state(i.csr.n, k)
+                                            for k, i in enumerate(insts)])).to(dev)
+    cb = tb.tbpm_create_batch([(i.csr, i.rescale) for i in insts],
+                              tb.make_opts(flags=tb.TBPM_F_AUTOTUNE, stream=so))
+    ob = torch.empty((len(insts), steps5 + 1), dtype=torch.complex128, device=dev)
+    msb = timed_calls(lambda: tb.tbpm_batch_dos_corr(cb, psi5, dts, steps5, out=ob), 1, stream)
+    ib = tb.tbpm_get_info(cb)
+    tb.tbpm_destroy(cb)
+    seq_ms = 0.0
+    off = 0
+    dev_max = 0.0
+    for k, i in enumerate(insts):
+        ci = tb.tbpm_create(i.csr.n, i.csr.row_ptr, i.csr.col, i.csr.val, i.rescale, tb.make_opts(stream=so))
+        pi = psi5[off:off + i.csr.n].reshape(1, i.csr.n)
+        oi = torch.empty((1, steps5 + 1), dtype=torch.complex128, device=dev)
+        seq_ms += timed_calls(lambda: tb.tbpm_dos_corr(ci, pi, dts[k], steps5, out=oi), 1, stream)
+        dev_max = max(dev_max, float((oi[0] - ob[k]).abs().max()))
+        tb.tbpm_destroy(ci)
+        off += i.csr.n
+    units5 = steps5 * 17 * n5                          # K = 18 at dt * rescale = pi
+    res["fp64_batch40_uneven"] = {"value": units5 / (msb / 1e3), "unit": UNIT, "ms_per_call": msb,
+                                  "instances": len(insts), "orbitals": n5, "n_steps": steps5,
+                                  "num_terms": ib["num_terms"], "grid_blocks": ib["grid_blocks"],
+                                  "tuned": bool(ib["tuned"]), "max_abs_dC_vs_sequential": dev_max}
+    res["fp64_batch40_sequential"] = {"value": units5 / (seq_ms / 1e3), "unit": UNIT, "ms_per_call": seq_ms,
+                                      "instances": len(insts), "n_steps": steps5}
+    del insts, psi5
+    # config 3: FP32 single state, SELL, against FP64 on the same state
     n3 = 2 * 2048 * 2048
     h3 = ti.graphene_csr(2048, 2048, onsite=ti.anderson_onsite(n3, W_DISORDER, 1))
-    ctx = tb.tbpm_create(n3, h3.row_ptr, h3.col, h3.val, RESCALE,
-                         tb.make_opts(precision=tb.TBPM_FP32, stream=stream.cuda_stream))
-    del h3
     psi = torch.from_numpy(ti.random_phase_state(n3, 0).reshape(1, n3)).to(dev)
+    c64 = tb.tbpm_create(n3, h3.row_ptr, h3.col, h3.val, RESCALE, tb.make_opts(stream=so))
+    ref3 = torch.empty((1, 1025), dtype=torch.complex128, device=dev)
+    tb.tbpm_dos_corr(c64, psi, DT, 1024, out=ref3)
+    ref3h = ref3[0].cpu().numpy()
     out = torch.empty((1, 1025), dtype=torch.complex128, device=dev)
-    ms = timed_calls(lambda: tb.tbpm_dos_corr(ctx, psi, DT, 1024, out=out), 2, stream)
-    K = tb.tbpm_get_info(ctx)["num_terms"]
-    res["fp32_sell_2048x2048"] = {"value": n3 * 1024 * (K - 1) / (ms / 1e3), "unit": UNIT,
-                                  "ms_per_call": ms, "states": 1, "n_steps": 1024}
-    tb.tbpm_destroy(ctx)
-    del psi
-    # config 4 lattice: FP32 x16 states vs FP64 x1, stencil
+    for name, flags in (("fp32_sell_2048x2048", 0), ("fp32_sell_renorm_2048x2048", tb.TBPM_F_RENORM)):
+        ctx = tb.tbpm_create(n3, h3.row_ptr, h3.col, h3.val, RESCALE,
+                             tb.make_opts(precision=tb.TBPM_FP32, flags=flags, stream=so))
+        ms = timed_calls(lambda: tb.tbpm_dos_corr(ctx, psi, DT, 1024, out=out), 1, stream)
+        K = tb.tbpm_get_info(ctx)["num_terms"]
+        res[name] = {"value": n3 * 1024 * (K - 1) / (ms / 1e3), "unit": UNIT, "ms_per_call": ms,
+                     "states": 1, "n_steps": 1024,
+                     "dos_l1_vs_fp64": dos_l1(c64, out[0].cpu().numpy(), ref3h, DT),
+                     "max_abs_dC_vs_fp64": float(np.max(np.abs(out[0].cpu().numpy() - ref3h)))}
+        tb.tbpm_destroy(ctx)
+    tb.tbpm_destroy(c64)
+    del psi, h3
+    # config 4 lattice: FP32 x16 states vs FP64 x1, stencil and stored matrix
     l4 = 4096
     n4 = 2 * l4 * l4
     eps = ti.anderson_onsite(n4, W_DISORDER, 1)
     steps = 32
-    ctx32 = tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l4, l4, ti.T_GRAPHENE, 0.0, eps, RESCALE,
-                                   tb.make_opts(precision=tb.TBPM_FP32, stream=stream.cuda_stream))
     blk = torch.empty((16, n4), dtype=torch.complex128, device=dev)
     for j in range(16):
         blk[j].copy_(torch.from_numpy(ti.random_phase_state(n4, j)))
+    one = blk[0:1].clone()
     o16 = torch.empty((16, steps + 1), dtype=torch.complex128, device=dev)
-    ms32 = timed_calls(lambda: tb.tbpm_dos_corr(ctx32, blk, DT, steps, out=o16), 2, stream)
-    tb.tbpm_destroy(ctx32)
-    v32 = n4 * 16 * steps * (K - 1) / (ms32 / 1e3)
-    ctx64 = tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l4, l4, ti.T_GRAPHENE, 0.0, eps, RESCALE,
-                                   tb.make_opts(precision=tb.TBPM_FP64, stream=stream.cuda_stream))
-    one = blk[0:1].contiguous()
-    del blk
     o1 = torch.empty((1, steps + 1), dtype=torch.complex128, device=dev)
-    ms64 = timed_calls(lambda: tb.tbpm_dos_corr(ctx64, one, DT, steps, out=o1), 2, stream)
-    tb.tbpm_destroy(ctx64)
-    v64 = n4 * steps * (K - 1) / (ms64 / 1e3)
-    res["fp32_x16_stencil_4096x4096"] = {"value": v32, "unit": "orbital-term-states/s",
-                                         "ms_per_call": ms32, "states": 16, "n_steps": steps}
-    res["fp64_x1_stencil_4096x4096"] = {"value": v64, "unit": UNIT, "ms_per_call": ms64, "states": 1,
-                                        "n_steps": steps}
-    res["fp32_batched_speedup_vs_fp64"] = v32 / v64
+    ref4 = None
+    for path in ("stencil", "sell"):
+        if path == "stencil":
+            mk = lambda prec: tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l4, l4, ti.T_GRAPHENE, 0.0, eps,
+                                                     RESCALE, tb.make_opts(precision=prec, stream=so))
+        else:
+            h4 = ti.graphene_csr(l4, l4, onsite=eps)
+            mk = lambda prec: tb.tbpm_create(n4, h4.row_ptr, h4.col, h4.val, RESCALE,
+                                             tb.make_opts(precision=prec, path=tb.TBPM_PATH_SELL, stream=so))
+        ctx64 = mk(tb.TBPM_FP64)
+        ms64 = timed_calls(lambda: tb.tbpm_dos_corr(ctx64, one, DT, steps, out=o1), 1, stream)
+        K = tb.tbpm_get_info(ctx64)["num_terms"]            # set by the first call
+        r = o1[0].cpu().numpy()
+        if ref4 is None:
+            ref4 = r
+        ctx32 = mk(tb.TBPM_FP32)
+        ms32 = timed_calls(lambda: tb.tbpm_dos_corr(ctx32, blk, DT, steps, out=o16), 1, stream)
+        tb.tbpm_destroy(ctx32)
+        if path == "sell":
+            del h4
+        v32 = n4 * 16 * steps * (K - 1) / (ms32 / 1e3)
+        v64 = n4 * steps * (K - 1) / (ms64 / 1e3)
+        s0 = o16[0].cpu().numpy()
+        res[f"fp32_x16_{path}_4096x4096"] = {"value": v32, "unit": "orbital-term-states/s", "ms_per_call": ms32,
+                                             "states": 16, "n_steps": steps,
+                                             "dos_l1_vs_fp64_state0": dos_l1(ctx64, s0, r, DT)}
+        res[f"fp64_x1_{path}_4096x4096"] = {"value": v64, "unit": UNIT, "ms_per_call": ms64, "states": 1,
+                                            "n_steps": steps,
+                                            "max_abs_dC_vs_stencil": float(np.max(np.abs(r - ref4)))}
+        res[f"fp32_batched_speedup_vs_fp64_{path}"] = v32 / v64
+        tb.tbpm_destroy(ctx64)
+    res["fp32_batched_speedup_vs_fp64"] = res["fp32_batched_speedup_vs_fp64_stencil"]
     return res
 
 

@@ -37,26 +37,43 @@ struct ClusterParams {
     int log_rows;              // rows per CTA = 1 << log_rows
     double2 *partials;         // [n_steps][nslices] <psi0|psi(t_{n+1})> per slice
     void *psi_out;             // global, [n_pad]: final state (may be null)
+    int max_width;             // widest slice (entries per row), for the shared copy
 };
 
-template <typename R, bool REALV>
-__device__ __forceinline__ void gather_row(const ClusterParams &p, cg::cluster_group &cl,
-                                           typename V2<R>::T *xs, int64_t s, int lane, R &ar, R &ai)
+// Where a CTA reads its matrix rows: its own slices, copied once into shared
+// memory (SMAT), or global memory. off is relative to `cols`/`vals`.
+struct MatView {
+    const int32_t *cols;
+    const void *vals;
+    const void *diag;          // indexed by the CTA-local row (SMAT) or the global row
+    const int32_t *loff;       // SMAT: local slice offsets (rows/32 + 1 entries)
+};
+
+template <typename R, bool REALV, bool SMAT>
+__device__ __forceinline__ void gather_row(const ClusterParams &p, const MatView &m, cg::cluster_group &cl,
+                                           typename V2<R>::T *xs, int64_t s, int ls, int lane, R &ar, R &ai)
 {
     typedef typename V2<R>::T V;
-    const int64_t off = __ldg(p.slice_off + s);
-    const int w = (int)((__ldg(p.slice_off + s + 1) - off) >> 5);
+    int64_t off;
+    int w;
+    if (SMAT) {
+        off = m.loff[ls];
+        w = (m.loff[ls + 1] - m.loff[ls]) >> 5;
+    } else {
+        off = __ldg(p.slice_off + s);
+        w = (int)((__ldg(p.slice_off + s + 1) - off) >> 5);
+    }
     const int mask = (1 << p.log_rows) - 1;
     for (int j = 0; j < w; ++j) {
-        const int c = __ldg(p.cols + off + 32 * j + lane);
+        const int c = m.cols[off + 32 * j + lane];
         const V *rx = cl.map_shared_rank(xs, (unsigned)(c >> p.log_rows));
         const V xv = rx[c & mask];
         if (REALV) {
-            const R v = __ldg(reinterpret_cast<const R *>(p.vals) + off + 32 * j + lane);
+            const R v = reinterpret_cast<const R *>(m.vals)[off + 32 * j + lane];
             ar = fma(v, xv.x, ar);
             ai = fma(v, xv.y, ai);
         } else {
-            const V v = __ldg(reinterpret_cast<const V *>(p.vals) + off + 32 * j + lane);
+            const V v = reinterpret_cast<const V *>(m.vals)[off + 32 * j + lane];
             ar = fma(v.x, xv.x, fma(-v.y, xv.y, ar));
             ai = fma(v.x, xv.y, fma(v.y, xv.x, ai));
         }
@@ -71,8 +88,8 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 // kind: 0 FIRST (x = psi, y = b_{K-2}), 1 SECOND, 2 MID, 3 FINAL
-template <typename R, bool REALV>
-__device__ void cluster_sweep(const ClusterParams &p, cg::cluster_group &cl, int kind, int k,
+template <typename R, bool REALV, bool SMAT>
+__device__ void cluster_sweep(const ClusterParams &p, const MatView &mv, cg::cluster_group &cl, int kind, int k,
                               typename V2<R>::T *xs, typename V2<R>::T *psi, typename V2<R>::T *y,
                               const typename V2<R>::T *z, int step)
 {
@@ -100,7 +117,7 @@ __device__ void cluster_sweep(const ClusterParams &p, cg::cluster_group &cl, int
     const int rows = 1 << p.log_rows;
     const int64_t row0 = (int64_t)rank * rows;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const R *diag = reinterpret_cast<const R *>(p.diag);
+    const R *diag = reinterpret_cast<const R *>(mv.diag);
     const V *psi0 = reinterpret_cast<const V *>(p.psi0);
     for (int ls = warp; ls < (rows >> 5); ls += nw) {
         const int64_t s = (row0 >> 5) + ls;
@@ -112,11 +129,11 @@ __device__ void cluster_sweep(const ClusterParams &p, cg::cluster_group &cl, int
         if (aimag) { tr = -a * ps.y; ti = a * ps.x; } else { tr = a * ps.x; ti = a * ps.y; }
         if (z) { const V zz = z[li]; tr -= zz.x; ti -= zz.y; }
         const V xi = xs[li];
-        const R d = diag ? __ldg(diag + row) : (R)0;
+        const R d = diag ? diag[SMAT ? (int64_t)li : row] : (R)0;
         R ar, ai;
         if (fold) { ar = fma(d, xi.x, tr); ai = fma(d, xi.y, ti); }
         else { ar = d * xi.x; ai = d * xi.y; }
-        gather_row<R, REALV>(p, cl, xs, s, lane, ar, ai);
+        gather_row<R, REALV, SMAT>(p, mv, cl, xs, s, ls, lane, ar, ai);
         V out;
         if (fold) { out.x = ar; out.y = ai; }
         else if (!bimag) { out.x = fma(beta, ar, tr); out.y = fma(beta, ai, ti); }
@@ -133,7 +150,7 @@ __device__ void cluster_sweep(const ClusterParams &p, cg::cluster_group &cl, int
     }
 }
 
-template <typename R, bool REALV>
+template <typename R, bool REALV, bool SMAT>
 __global__ void __launch_bounds__(1024) cluster_dos_kernel(ClusterParams p)
 {
     typedef typename V2<R>::T V;
@@ -144,6 +161,44 @@ __global__ void __launch_bounds__(1024) cluster_dos_kernel(ClusterParams p)
     V *b0 = psi + rows;
     V *b1 = b0 + rows;
     const int64_t row0 = (int64_t)cl.block_rank() * rows;
+    MatView mv;
+    mv.cols = p.cols;
+    mv.vals = p.vals;
+    mv.diag = p.diag;
+    mv.loff = nullptr;
+    if (SMAT) {
+        // this CTA's slices: [s0, s1); entries [e0, e1) of the global SELL arrays
+        const int64_t s0 = row0 >> 5;
+        const int64_t s1 = min(s0 + (rows >> 5), p.nslices);
+        const int64_t e0 = p.slice_off[min(s0, p.nslices)];
+        const int64_t e1 = p.slice_off[s1];              // s1 >= min(s0, nslices)
+        const int ent = rows * p.max_width;
+        const int vsz = REALV ? (int)sizeof(R) : (int)sizeof(V);
+        unsigned char *q = reinterpret_cast<unsigned char *>(b1 + rows);
+        void *svals = q;
+        q += (size_t)ent * vsz;
+        R *sdiag = reinterpret_cast<R *>(q);
+        q += (size_t)rows * sizeof(R);
+        int32_t *scols = reinterpret_cast<int32_t *>(q);
+        q += (size_t)ent * sizeof(int32_t);
+        int32_t *sloff = reinterpret_cast<int32_t *>(q);
+        for (int64_t i = threadIdx.x; i < e1 - e0; i += blockDim.x) {
+            scols[i] = p.cols[e0 + i];
+            if (REALV) reinterpret_cast<R *>(svals)[i] = reinterpret_cast<const R *>(p.vals)[e0 + i];
+            else reinterpret_cast<V *>(svals)[i] = reinterpret_cast<const V *>(p.vals)[e0 + i];
+        }
+        for (int i = threadIdx.x; i <= (rows >> 5); i += blockDim.x) {
+            const int64_t sg = s0 + i;
+            sloff[i] = (int32_t)((sg <= s1 ? p.slice_off[sg] : e1) - e0);
+        }
+        const R *gd = reinterpret_cast<const R *>(p.diag);
+        for (int i = threadIdx.x; i < rows; i += blockDim.x)
+            sdiag[i] = (gd && row0 + i < p.n_pad) ? gd[row0 + i] : (R)0;
+        mv.cols = scols;
+        mv.vals = svals;
+        mv.diag = p.diag ? sdiag : nullptr;
+        mv.loff = sloff;
+    }
     const V *g0 = reinterpret_cast<const V *>(p.psi0);
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
         const int64_t r = row0 + i;
@@ -157,19 +212,19 @@ __global__ void __launch_bounds__(1024) cluster_dos_kernel(ClusterParams p)
     const int K = p.K;
     V *B[2] = {b0, b1};
     for (int step = 0; step < p.n_steps; ++step) {
-        cluster_sweep<R, REALV>(p, cl, 0, K - 2, psi, psi, B[0], nullptr, step);
+        cluster_sweep<R, REALV, SMAT>(p, mv, cl, 0, K - 2, psi, psi, B[0], nullptr, step);
         cl.sync();
         if (K >= 4) {
-            cluster_sweep<R, REALV>(p, cl, 1, K - 3, B[0], psi, B[1], nullptr, step);
+            cluster_sweep<R, REALV, SMAT>(p, mv, cl, 1, K - 3, B[0], psi, B[1], nullptr, step);
             cl.sync();
         }
         for (int k = K - 4; k >= 1; --k) {
             V *yk = B[(K - 2 - k) & 1];
-            cluster_sweep<R, REALV>(p, cl, 2, k, B[(K - 3 - k) & 1], psi, yk, yk, step);
+            cluster_sweep<R, REALV, SMAT>(p, mv, cl, 2, k, B[(K - 3 - k) & 1], psi, yk, yk, step);
             cl.sync();
         }
-        cluster_sweep<R, REALV>(p, cl, 3, 0, B[(K - 3) & 1], psi, psi, K >= 4 ? B[(K - 4) & 1] : nullptr,
-                                step);
+        cluster_sweep<R, REALV, SMAT>(p, mv, cl, 3, 0, B[(K - 3) & 1], psi, psi, K >= 4 ? B[(K - 4) & 1] : nullptr,
+                                      step);
         cl.sync();
     }
     if (p.psi_out) {
@@ -179,10 +234,10 @@ __global__ void __launch_bounds__(1024) cluster_dos_kernel(ClusterParams p)
     }
 }
 
-template <typename R, bool REALV>
+template <typename R, bool REALV, bool SMAT>
 cudaError_t launch_t(const ClusterParams &p, int ncta, int threads, size_t smem, cudaStream_t s)
 {
-    auto kern = cluster_dos_kernel<R, REALV>;
+    auto kern = cluster_dos_kernel<R, REALV, SMAT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -225,7 +280,7 @@ bool cluster_fits(int precision, int64_t n_pad, int *log_rows, int *ncta, size_t
     return false;
 }
 
-cudaError_t launch_cluster_dos(int precision, bool real_values, const SweepParams &op,
+cudaError_t launch_cluster_dos(int precision, bool real_values, const SweepParams &op, int max_width,
                                const void *psi0, const double2 *coef, int K, int n_steps,
                                double2 *partials, void *psi_out, cudaStream_t s)
 {
@@ -246,13 +301,25 @@ cudaError_t launch_cluster_dos(int precision, bool real_values, const SweepParam
     p.log_rows = lr;
     p.partials = partials;
     p.psi_out = psi_out;
+    p.max_width = max_width;
     const int rows = 1 << lr;
     const int threads = rows >= 1024 ? 1024 : (rows < 64 ? 64 : rows);
-    if (precision == TBPM_FP64)
-        return real_values ? launch_t<double, true>(p, ncta, threads, smem, s)
-                           : launch_t<double, false>(p, ncta, threads, smem, s);
-    return real_values ? launch_t<float, true>(p, ncta, threads, smem, s)
-                       : launch_t<float, false>(p, ncta, threads, smem, s);
+    // the CTA's matrix rows in shared memory too, when they fit beside the vectors
+    const size_t rsz = precision == TBPM_FP64 ? 8 : 4;
+    const size_t vsz = real_values ? rsz : 2 * rsz;
+    const size_t msm = (size_t)rows * max_width * (vsz + 4) + (size_t)rows * rsz + ((size_t)(rows >> 5) + 1) * 4;
+    const bool smat = smem + msm <= 200 * 1024;
+    if (smat) smem += msm;
+    if (precision == TBPM_FP64) {
+        if (smat) return real_values ? launch_t<double, true, true>(p, ncta, threads, smem, s)
+                                     : launch_t<double, false, true>(p, ncta, threads, smem, s);
+        return real_values ? launch_t<double, true, false>(p, ncta, threads, smem, s)
+                           : launch_t<double, false, false>(p, ncta, threads, smem, s);
+    }
+    if (smat) return real_values ? launch_t<float, true, true>(p, ncta, threads, smem, s)
+                                 : launch_t<float, false, true>(p, ncta, threads, smem, s);
+    return real_values ? launch_t<float, true, false>(p, ncta, threads, smem, s)
+                       : launch_t<float, false, false>(p, ncta, threads, smem, s);
 }
 
 }  // namespace tbpm

@@ -947,7 +947,8 @@ static int run_dos(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, in
             }
             SweepParams op;
             fill_operator(ctx, op);
-            CU(launch_cluster_dos(ctx->precision, ctx->sell.real_values, op, ctx->d_psi0, ctx->d_coef, Ke,
+            CU(launch_cluster_dos(ctx->precision, ctx->sell.real_values, op, ctx->sell.max_width, ctx->d_psi0,
+                                  ctx->d_coef, Ke,
                                   n_steps, ctx->d_cpart, psi_out ? ctx->d_psi : nullptr, ctx->stream));
             CU(launch_reduce_seg(ctx->d_cpart, n_steps, 1, nsl, nullptr, 1, nullptr, 1, ctx->d_out, 0,
                                  ctx->stream));

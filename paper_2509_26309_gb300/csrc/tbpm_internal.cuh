@@ -225,7 +225,7 @@ cudaError_t launch_fill(double *p, int n, double v, cudaStream_t s);
 // rows fit, and the launch of n_steps steps writing per-slice <psi0|psi>
 // partials [n_steps][nslices] and, if psi_out is not null, the final state.
 bool cluster_fits(int precision, int64_t n_pad, int *log_rows, int *ncta, size_t *smem);
-cudaError_t launch_cluster_dos(int precision, bool real_values, const SweepParams &op,
+cudaError_t launch_cluster_dos(int precision, bool real_values, const SweepParams &op, int max_width,
                                const void *psi0, const double2 *coef, int K, int n_steps,
                                double2 *partials, void *psi_out, cudaStream_t s);
 

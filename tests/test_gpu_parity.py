@@ -41,6 +41,8 @@ def test_config1_pristine_64x64_full(orc):
     (lambda: ti.random_hermitian_csr(3000, 4, seed=4, scale=1.0), tb.TBPM_FP64),
     (lambda: ti.bilayer_csr(64, 64, onsite=ti.anderson_onsite(16384, 1.0, 2)), tb.TBPM_FP64),
     (lambda: ti.graphene_csr(100, 90, onsite=ti.anderson_onsite(18000, 1.0, 2)), tb.TBPM_FP32),
+    # 4096 rows per CTA: the vectors fill shared memory, the matrix stays in global memory
+    (lambda: ti.graphene_csr(160, 160, onsite=ti.anderson_onsite(51200, 1.0, 5)), tb.TBPM_FP64),
 ])
 def test_cluster_path_matches_graph_path(orc, maker, prec):
     """Small systems run all steps in one launch of one thread-block cluster; the
