@@ -17,6 +17,10 @@ Parity status per function (what pins it, all in tests/test_oracle_*.py):
   quasi_eigenstates                      exact diagonalisation (windowed spectral sum)
   haydock, haydock_ldos                  closed-form chain coefficients, moment
                                          matching, exact diagonalisation
+  fermi_coeffs                           the Fermi function off the quadrature nodes,
+                                         adaptive quadrature, particle-hole symmetry
+  ac_corr                                exact diagonalisation, C(0) and symmetry relations
+  ac_cond                                spectral weight of a single transition
 """
 from __future__ import annotations
 
@@ -55,10 +59,18 @@ def _bind(path: str):
     l.oracle_quasi_eigenstates.argtypes = [i64, p, p, p, d, p, d, i32, d, i32, p, p]
     l.oracle_haydock_ldos.restype = None
     l.oracle_haydock_ldos.argtypes = [p, p, i32, p, i32, d, p]
+    l.oracle_fermi_coeffs.restype = i32
+    l.oracle_fermi_coeffs.argtypes = [d, d, d, d, i32, p]
+    l.oracle_ac_corr.restype = i32
+    l.oracle_ac_corr.argtypes = [i64, p, p, p, p, p, p, p, d, p, d, d, d, i32, d, d, i32, p]
+    l.oracle_ac_cond.restype = i32
+    l.oracle_ac_cond.argtypes = [p, i32, d, d, d, i32, p, p]
     return l
 
 
 TOL = 1e-12
+FERMI_TOL = 1e-12
+FERMI_CAP = 8192
 
 
 def _ptr(a: np.ndarray):
@@ -187,6 +199,44 @@ class Oracle:
         self._l.oracle_haydock_ldos(_ptr(a), _ptr(b), a.size, _ptr(e), e.size, float(eta), _ptr(out))
         return out
 
+    def fermi_coeffs(self, beta: float, mu: float, rescale: float, tol: float = FERMI_TOL,
+                     kcap: int = FERMI_CAP):
+        """(K, a[kcap]): Chebyshev coefficients of the Fermi-Dirac function on the
+        rescaled spectrum and the number of terms kept at ``tol``."""
+        a = np.zeros(kcap)
+        K = self._l.oracle_fermi_coeffs(float(beta), float(mu), float(rescale), float(tol), int(kcap), _ptr(a))
+        if K < 0:
+            raise RuntimeError(f"oracle_fermi_coeffs failed: {K}")
+        return K, a
+
+    def ac_corr(self, h, current, rescale: float, psi0: np.ndarray, beta: float, mu: float, dt: float,
+                n_steps: int, tol: float = TOL, ftol: float = FERMI_TOL, kcap: int = FERMI_CAP):
+        """(K_F, corr[4, n_steps+1]) for (xx, xy, yx, yy); current = (row_ptr, col, jx, jy)."""
+        rp, col, val = _csr(h)
+        jrp = np.ascontiguousarray(current[0], dtype=np.int64)
+        jcol = np.ascontiguousarray(current[1], dtype=np.int32)
+        jx = np.ascontiguousarray(current[2], dtype=np.complex128)
+        jy = np.ascontiguousarray(current[3], dtype=np.complex128)
+        psi0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+        corr = np.zeros((4, n_steps + 1), dtype=np.complex128)
+        K = self._l.oracle_ac_corr(h.n, _ptr(rp), _ptr(col), _ptr(val), _ptr(jrp), _ptr(jcol), _ptr(jx), _ptr(jy),
+                                   float(rescale), _ptr(psi0), float(beta), float(mu), float(dt), int(n_steps),
+                                   float(tol), float(ftol), int(kcap), _ptr(corr))
+        if K < 0:
+            raise RuntimeError(f"oracle_ac_corr failed: {K}")
+        return K, corr
+
+    def ac_cond(self, corr: np.ndarray, dt: float, beta: float, area: float, omegas) -> np.ndarray:
+        """Re sigma(w) of one correlation row."""
+        corr = np.ascontiguousarray(corr, dtype=np.complex128)
+        w = np.ascontiguousarray(omegas, dtype=np.float64)
+        out = np.zeros(w.size)
+        rc = self._l.oracle_ac_cond(_ptr(corr), corr.size - 1, float(dt), float(beta), float(area), w.size,
+                                    _ptr(w), _ptr(out))
+        if rc != 0:
+            raise RuntimeError(f"oracle_ac_cond failed: {rc}")
+        return out
+
 
 _default = None
 
@@ -207,6 +257,6 @@ def __getattr__(name):
     # module-level access to the default instance: oracle.propagate(...), etc.
     if name in ("bessel_j", "cheb_num_terms", "cheb_coeffs", "spmv", "propagate", "dos_corr",
                 "kpm_moments", "dos_hann", "jackson", "kpm_dos", "haydock", "haydock_ldos",
-                "quasi_eigenstates"):
+                "quasi_eigenstates", "fermi_coeffs", "ac_corr", "ac_cond"):
         return getattr(default(), name)
     raise AttributeError(name)

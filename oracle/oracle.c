@@ -380,3 +380,137 @@ int oracle_kpm_dos(const double *mu_re, int M, double rescale, int n_e, double *
     free(g);
     return ORACLE_OK;
 }
+
+/* ------------------------------------------------------ AC conductivity */
+/*
+ * Optical (AC) conductivity is one of the TBPM capabilities the paper lists
+ * (Sec. 1) and benchmarks (Sec. 4.2.2); TBPM solvers take the Hamiltonian and
+ * the current operators as sparse matrices (Sec. 2.3.4). The paper prints no
+ * formula, so the definitions are the standard TBPM ones (Yuan, De Raedt and
+ * Katsnelson, Phys. Rev. B 82, 115448 (2010)), with hbar = e = 1:
+ *
+ *   f(E) = 1 / (exp(beta (E - mu)) + 1)                    Fermi-Dirac
+ *   C_ab(t) = <phi| f(H) J_a(t) [1 - f(H)] J_b |phi>,     J_a(t) = e^{iHt} J_a e^{-iHt}
+ *           = <phi2(t)| J_a |phi1_b(t)>,
+ *   phi2(t) = e^{-iHt} f(H) phi,  phi1_b(t) = e^{-iHt} [1 - f(H)] J_b phi,
+ *   Re sigma_ab(w) = (exp(-beta w) - 1) / (w s) * int_0^T w(t) sin(w t) 2 Im C_ab(t) dt,
+ *
+ * s the area per orbital, the time integral a Hann-windowed sum over the
+ * steps t_n = n dt, n < N. f(H) is the Chebyshev series of f on the rescaled
+ * spectrum, with coefficients from Chebyshev-Gauss quadrature.
+ */
+
+/* Fermi-Dirac occupation, evaluated on the side where the exponential is <= 1. */
+static double fermi(double beta, double mu, double e)
+{
+    double z = beta * (e - mu);
+    if (z > 0.0) {
+        double q = exp(-z);
+        return q / (1.0 + q);
+    }
+    return 1.0 / (1.0 + exp(z));
+}
+
+/* a_k, k < kcap, of f(rescale * y) = sum_k a_k T_k(y) on [-1, 1]:
+ *   a_k = (2 - delta_k0) / M sum_{j<M} f(rescale cos th_j) cos(k th_j),
+ *   th_j = pi (j + 1/2) / M,  M = 2 kcap nodes.
+ * Returns K = 1 + the last k with |a_k| >= tol, or ORACLE_ERR_ARG when the
+ * series has not fallen below tol by k = kcap - 1 (temperature too low for
+ * kcap terms). */
+int oracle_fermi_coeffs(double beta, double mu, double rescale, double tol, int kcap, double *a)
+{
+    if (!(beta > 0) || !(rescale > 0) || !(tol > 0) || kcap < 2 || !a) return ORACLE_ERR_ARG;
+    int M = 2 * kcap;
+    double *fj = malloc((size_t)M * sizeof(double));
+    if (!fj) return ORACLE_ERR_OOM;
+    for (int j = 0; j < M; ++j) fj[j] = fermi(beta, mu, rescale * cos(PI * (j + 0.5) / M));
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < kcap; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < M; ++j) s += fj[j] * cos(k * (PI * (j + 0.5) / M));
+        a[k] = (k == 0 ? 1.0 : 2.0) * s / M;
+    }
+    free(fj);
+    int K = 0;
+    for (int k = 0; k < kcap; ++k)
+        if (fabs(a[k]) >= tol) K = k + 1;
+    if (K >= kcap) return ORACLE_ERR_ARG;
+    return K < 1 ? 1 : K;
+}
+
+/* C_ab(t_n), n = 0..n_steps, for (a, b) = (x, x), (x, y), (y, x), (y, y):
+ * corr is 4 x (n_steps + 1), correlation-major. The current operators J_x,
+ * J_y share one CSR pattern (jrp, jcol) with values jx, jy. f(H~) is applied
+ * by the forward Chebyshev recurrence with the a_k of oracle_fermi_coeffs
+ * (kcap terms at most, cut at ftol), 1 - f(H~) as v - f(H~) v; each step is
+ * the propagation step of oracle_propagate. Returns the Fermi term count. */
+int oracle_ac_corr(int64_t n, const int64_t *rp, const int32_t *col, const cplx *val,
+                   const int64_t *jrp, const int32_t *jcol, const cplx *jx, const cplx *jy,
+                   double rescale, const cplx *psi0, double beta, double mu, double dt, int n_steps,
+                   double tol, double ftol, int kcap, cplx *corr)
+{
+    if (n <= 0 || !rp || !col || !val || !jrp || !jcol || !jx || !jy || !psi0 || !corr || n_steps < 0 ||
+        !(rescale > 0))
+        return ORACLE_ERR_ARG;
+    double *a = malloc((size_t)kcap * sizeof(double));
+    if (!a) return ORACLE_ERR_OOM;
+    int KF = oracle_fermi_coeffs(beta, mu, rescale, ftol, kcap, a);
+    if (KF < 1) { free(a); return KF; }
+    int K = oracle_cheb_num_terms(dt * rescale, tol);
+    if (K < 1) { free(a); return ORACLE_ERR_ARG; }
+    cplx *fc = malloc((size_t)KF * sizeof(cplx));
+    cplx *c = malloc((size_t)K * sizeof(cplx));
+    cplx *v[3], *u = malloc((size_t)n * sizeof(cplx)), *out = malloc((size_t)n * sizeof(cplx));
+    cplx *t0 = malloc((size_t)n * sizeof(cplx)), *t1 = malloc((size_t)n * sizeof(cplx));
+    cplx *t2 = malloc((size_t)n * sizeof(cplx));
+    for (int q = 0; q < 3; ++q) v[q] = malloc((size_t)n * sizeof(cplx));
+    int ok = fc && c && u && out && t0 && t1 && t2 && v[0] && v[1] && v[2];
+    if (ok) {
+        for (int k = 0; k < KF; ++k) fc[k] = a[k];
+        oracle_cheb_coeffs(dt * rescale, K, c);
+        /* v[0] = phi2 = f(H~) phi */
+        cheb_step(n, rp, col, val, rescale, KF, fc, psi0, v[0], t0, t1, t2);
+        /* v[1] = phi1_x = [1 - f(H~)] J_x phi, v[2] = phi1_y */
+        for (int b = 0; b < 2; ++b) {
+            spmv(n, jrp, jcol, b == 0 ? jx : jy, 1.0, psi0, u);
+            cheb_step(n, rp, col, val, rescale, KF, fc, u, out, t0, t1, t2);
+            for (int64_t i = 0; i < n; ++i) v[1 + b][i] = u[i] - out[i];
+        }
+        for (int s = 0; s <= n_steps; ++s) {
+            for (int al = 0; al < 2; ++al) {
+                spmv(n, jrp, jcol, al == 0 ? jx : jy, 1.0, v[0], u);     /* J_a phi2 (J_a Hermitian) */
+                for (int b = 0; b < 2; ++b)
+                    corr[(size_t)(2 * al + b) * (n_steps + 1) + s] = dot(n, u, v[1 + b]);
+            }
+            if (s == n_steps) break;
+            for (int q = 0; q < 3; ++q) {
+                cheb_step(n, rp, col, val, rescale, K, c, v[q], out, t0, t1, t2);
+                memcpy(v[q], out, (size_t)n * sizeof(cplx));
+            }
+        }
+    }
+    free(a); free(fc); free(c); free(u); free(out); free(t0); free(t1); free(t2);
+    for (int q = 0; q < 3; ++q) free(v[q]);
+    return ok ? KF : ORACLE_ERR_OOM;
+}
+
+/* Re sigma(w_j) from one correlation row C(t_n), n = 0..n_steps:
+ *   sigma(w) = (exp(-beta w) - 1) / (w s) sum_{n=0}^{N-1} dt w_n sin(w t_n) 2 Im C(t_n),
+ *   w_n = (1 + cos(pi n / N)) / 2,  N = n_steps;  sigma(0) = 0 (the limit w -> 0). */
+int oracle_ac_cond(const cplx *corr, int n_steps, double dt, double beta, double s, int n_w,
+                   const double *omegas, double *sigma)
+{
+    if (!corr || n_steps < 1 || !(dt > 0) || !(s > 0) || n_w < 1 || !omegas || !sigma) return ORACLE_ERR_ARG;
+    int N = n_steps;
+    for (int j = 0; j < n_w; ++j) {
+        double w = omegas[j];
+        if (w == 0.0) { sigma[j] = 0.0; continue; }
+        double acc = 0.0;
+        for (int m = 0; m < N; ++m) {
+            double win = 0.5 * (1.0 + cos(PI * (double)m / (double)N));
+            acc += dt * win * sin(w * m * dt) * 2.0 * cimag(corr[m]);
+        }
+        sigma[j] = (exp(-beta * w) - 1.0) / (w * s) * acc;
+    }
+    return ORACLE_OK;
+}

@@ -192,3 +192,124 @@ def gershgorin_bound(h: CSR) -> float:
     rows = np.repeat(np.arange(h.n), np.diff(h.row_ptr))
     s = np.bincount(rows, weights=np.abs(h.val), minlength=h.n)
     return float(s.max()) if h.n else 0.0
+
+
+# ------------------------------------------------------------ current operators
+
+A_LATTICE = 0.246          # graphene lattice constant, nm (bond length a / sqrt(3) = 0.142 nm)
+
+
+@dataclass
+class Current:
+    """Current operators J_x, J_y on one CSR pattern (row_ptr int64[n+1],
+    col int32[nnz]) with complex128 values jx, jy."""
+
+    n: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    jx: np.ndarray
+    jy: np.ndarray
+
+    def as_tuple(self):
+        return self.row_ptr, self.col, self.jx, self.jy
+
+    def to_dense(self):
+        out = []
+        for v in (self.jx, self.jy):
+            out.append(CSR(self.n, self.row_ptr, self.col, v).to_dense())
+        return out
+
+
+def graphene_geometry(a: float = A_LATTICE):
+    """Lattice vectors a1, a2 and the A, B positions (nm) of the primitive cell."""
+    a1 = np.array([a, 0.0])
+    a2 = np.array([0.5 * a, 0.5 * np.sqrt(3.0) * a])
+    return a1, a2, np.zeros(2), (a1 + a2) / 3.0
+
+
+def _current_from_bonds(n, cols, hvals, disp, valid) -> Current:
+    """J_a with (J_a)_ij = i (r_j - r_i)_a H_ij per bond, r_j - r_i the bond
+    vector (not the wrapped coordinate difference); duplicates summed."""
+    jx = _assemble(n, cols, 1j * disp[..., 0] * hvals, valid)
+    jy = _assemble(n, cols, 1j * disp[..., 1] * hvals, valid)
+    return Current(n, jx.row_ptr, jx.col, jx.val, jy.val)
+
+
+def graphene_current(l1: int, l2: int, t: complex = T_GRAPHENE, bond_phases: np.ndarray | None = None,
+                     a: float = A_LATTICE) -> Current:
+    """Current operators of graphene_csr(l1, l2, t, bond_phases=...)."""
+    ncell = l1 * l2
+    n = 2 * ncell
+    th = np.zeros(3) if bond_phases is None else np.asarray(bond_phases, dtype=np.float64)
+    t0, t1, t2 = (complex(t) * np.exp(1j * th[b]) for b in range(3))
+    a1, a2, ra, rb = graphene_geometry(a)
+    m1, m2 = np.divmod(np.arange(ncell, dtype=np.int64), l2)
+
+    def cell(p, q):
+        return (p % l1) * l2 + (q % l2)
+
+    cols = np.zeros((n, 3), dtype=np.int64)
+    vals = np.zeros((n, 3), dtype=np.complex128)
+    disp = np.zeros((n, 3, 2))
+    ia = 2 * cell(m1, m2)
+    ib = ia + 1
+    cols[ia, 0], vals[ia, 0], disp[ia, 0] = ib, t0, rb - ra
+    cols[ia, 1], vals[ia, 1], disp[ia, 1] = 2 * cell(m1 - 1, m2) + 1, np.conj(t1), rb - a1 - ra
+    cols[ia, 2], vals[ia, 2], disp[ia, 2] = 2 * cell(m1, m2 - 1) + 1, np.conj(t2), rb - a2 - ra
+    cols[ib, 0], vals[ib, 0], disp[ib, 0] = ia, np.conj(t0), ra - rb
+    cols[ib, 1], vals[ib, 1], disp[ib, 1] = 2 * cell(m1 + 1, m2), t1, ra + a1 - rb
+    cols[ib, 2], vals[ib, 2], disp[ib, 2] = 2 * cell(m1, m2 + 1), t2, ra + a2 - rb
+    return _current_from_bonds(n, cols, vals, disp, np.ones((n, 3), dtype=bool))
+
+
+def bilayer_current(l1: int, l2: int, t: float = T_GRAPHENE, t_perp: float = T_PERP_AB,
+                    a: float = A_LATTICE) -> Current:
+    """Current operators of bilayer_csr(l1, l2, t, t_perp): in-plane bonds as in
+    each layer, the vertical dimer bond carries no in-plane current (its
+    entries are kept, with value 0)."""
+    ncell = l1 * l2
+    n = 4 * ncell
+    a1, a2, ra, rb = graphene_geometry(a)
+    m1, m2 = np.divmod(np.arange(ncell, dtype=np.int64), l2)
+
+    def cell(p, q):
+        return (p % l1) * l2 + (q % l2)
+
+    cols = np.zeros((n, 4), dtype=np.int64)
+    vals = np.zeros((n, 4), dtype=np.complex128)
+    disp = np.zeros((n, 4, 2))
+    valid = np.zeros((n, 4), dtype=bool)
+    base = 4 * cell(m1, m2)
+    for layer in (0, 1):
+        ia = base + 2 * layer
+        ib = ia + 1
+        cols[ia, 0], vals[ia, 0], disp[ia, 0] = ib, t, rb - ra
+        cols[ia, 1], vals[ia, 1], disp[ia, 1] = 4 * cell(m1 - 1, m2) + 2 * layer + 1, t, rb - a1 - ra
+        cols[ia, 2], vals[ia, 2], disp[ia, 2] = 4 * cell(m1, m2 - 1) + 2 * layer + 1, t, rb - a2 - ra
+        cols[ib, 0], vals[ib, 0], disp[ib, 0] = ia, t, ra - rb
+        cols[ib, 1], vals[ib, 1], disp[ib, 1] = 4 * cell(m1 + 1, m2) + 2 * layer, t, ra + a1 - rb
+        cols[ib, 2], vals[ib, 2], disp[ib, 2] = 4 * cell(m1, m2 + 1) + 2 * layer, t, ra + a2 - rb
+        valid[ia, :3] = True
+        valid[ib, :3] = True
+    a1r, b2r = base, base + 3
+    cols[a1r, 3], vals[a1r, 3] = b2r, t_perp
+    cols[b2r, 3], vals[b2r, 3] = a1r, t_perp
+    valid[a1r, 3] = True
+    valid[b2r, 3] = True
+    return _current_from_bonds(n, cols, vals, disp, valid)
+
+
+def graphene_positions(l1: int, l2: int, a: float = A_LATTICE) -> np.ndarray:
+    """float64[n, 2] orbital positions (nm) of the graphene supercell, unwrapped."""
+    a1, a2, ra, rb = graphene_geometry(a)
+    m1, m2 = np.divmod(np.arange(l1 * l2, dtype=np.int64), l2)
+    base = m1[:, None] * a1 + m2[:, None] * a2
+    out = np.zeros((2 * l1 * l2, 2))
+    out[0::2] = base + ra
+    out[1::2] = base + rb
+    return out
+
+
+def graphene_area_per_orbital(a: float = A_LATTICE) -> float:
+    """Cell area |a1 x a2| / 2 orbitals, nm^2."""
+    return 0.5 * (np.sqrt(3.0) / 2.0) * a * a

@@ -13,7 +13,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
 PINS = ["tests/test_oracle_bessel.py", "tests/test_oracle_propagation.py", "tests/test_oracle_haydock.py",
-        "tests/test_oracle_qe.py",
+        "tests/test_oracle_qe.py", "tests/test_oracle_ac.py",
         "tests/test_oracle_kpm.py", "tests/test_oracle_dos.py"]
 
 # name: [(original text, planted text)], each original must occur in oracle.c
@@ -50,6 +50,17 @@ MUTANTS = {
                        "cplx ph = pre * w * cexp(-I * energies[e] * t);")],
     "qe_forward_only": [("for (int dir = 0; dir < 2; ++dir) {", "for (int dir = 0; dir < 1; ++dir) {")],
     "qe_no_window": [("double w = 0.5 * (1.0 + cos(PI * (double)s / (double)N));", "double w = 1.0;")],
+    "fermi_exp_sign": [("double q = exp(-z);", "double q = exp(z);")],
+    "fermi_a0_doubled": [("a[k] = (k == 0 ? 1.0 : 2.0) * s / M;", "a[k] = 2.0 * s / M;")],
+    "fermi_node_offset": [("fj[j] = fermi(beta, mu, rescale * cos(PI * (j + 0.5) / M));",
+                           "fj[j] = fermi(beta, mu, rescale * cos(PI * j / M));")],
+    "ac_f_instead_of_one_minus_f": [("v[1 + b][i] = u[i] - out[i];", "v[1 + b][i] = out[i];")],
+    "ac_current_swapped": [("spmv(n, jrp, jcol, al == 0 ? jx : jy, 1.0, v[0], u);",
+                            "spmv(n, jrp, jcol, al == 0 ? jy : jx, 1.0, v[0], u);")],
+    "ac_cond_sign": [("sigma[j] = (exp(-beta * w) - 1.0) / (w * s) * acc;",
+                      "sigma[j] = (1.0 - exp(-beta * w)) / (w * s) * acc;")],
+    "ac_cond_real_part": [("sin(w * m * dt) * 2.0 * cimag(corr[m]);", "sin(w * m * dt) * 2.0 * creal(corr[m]);")],
+    "ac_cond_no_window": [("double win = 0.5 * (1.0 + cos(PI * (double)m / (double)N));", "double win = 1.0;")],
 }
 
 
