@@ -238,6 +238,59 @@ int tbpm_haydock(tbpm_ctx *ctx, const double *psi0, int M, double *a, double *b)
 int tbpm_haydock_ldos(tbpm_ctx *ctx, const double *a, const double *b, int M, const double *energies,
                       int n_e, double eta, double *ldos);
 
+/* ------------------------------------------------- AC conductivity */
+
+/* Longest Fermi-operator series; its coefficients come from Chebyshev-Gauss
+ * quadrature on 2 * TBPM_FERMI_MAX_TERMS nodes. */
+#define TBPM_FERMI_MAX_TERMS 8192
+
+/* tbpm_set_current: the current operators J_x, J_y of the context's
+ * Hamiltonian (TBPM solvers take the Hamiltonian and the current operators as
+ * sparse matrices, Sec. 2.3.4), used by tbpm_ac_corr. One CSR pattern, two
+ * value arrays; with hbar = e = 1, (J_a)_ij = i (r_j - r_i)_a H_ij for each
+ * hopping, r_j - r_i its bond vector.
+ *   row_ptr  int64[n+1], col int32[nnz] (nnz = row_ptr[n]), host memory
+ *   jx, jy   double[2*nnz] complex values, host memory
+ * Duplicate (row, col) entries are summed. Each J_a must be Hermitian
+ * (checked unless TBPM_F_NO_HERMITIAN_CHECK; TBPM_ERR_NOT_HERMITIAN).
+ * Replaces earlier current operators. Copies the arrays; FP64 contexts of one
+ * Hamiltonian only (batches: TBPM_ERR_UNSUPPORTED). */
+int tbpm_set_current(tbpm_ctx *ctx, const int64_t *row_ptr, const int32_t *col, const double *jx,
+                     const double *jy);
+
+/* tbpm_ac_corr: the current-current correlation of the AC (optical)
+ * conductivity, a TBPM capability of Sec. 1 benchmarked in Sec. 4.2.2, in the
+ * standard TBPM form (hbar = e = 1):
+ *   C_ab(t_m) = <phi| f(H) e^{iHt} J_a e^{-iHt} [1 - f(H)] J_b |phi>
+ *             = <phi2(t_m)| J_a |phi1_b(t_m)>,   t_m = m dt,  m = 0..n_steps,
+ *   phi2(t) = e^{-iHt} f(H) phi,  phi1_b(t) = e^{-iHt} [1 - f(H)] J_b phi,
+ *   f(E) = 1 / (exp(beta (E - mu)) + 1).
+ * f(H~) is the Chebyshev series f(rescale y) = sum_k a_k T_k(y) with
+ *   a_k = (2 - delta_k0)/M sum_{j<M} f(rescale cos th_j) cos(k th_j),
+ *   th_j = pi (j + 1/2) / M,  M = 2 TBPM_FERMI_MAX_TERMS,
+ * cut after the last k with |a_k| >= 1e-12; the time steps are those of
+ * tbpm_dos_corr (same dt, same Bessel cut-off).
+ *   psi0   double[2n] one state (host or device), normally a random-phase state
+ *   beta   > 0 (1/eV), mu the chemical potential (eV); dt != 0, n_steps >= 0
+ *   corr   double[2 * 4 * (n_steps+1)] out (host or device): the rows C_xx,
+ *          C_xy, C_yx, C_yy, each n_steps+1 complex values
+ * TBPM_ERR_ARG when no current operators are set or when the Fermi series
+ * needs more than TBPM_FERMI_MAX_TERMS terms (beta * rescale too large);
+ * TBPM_ERR_UNSUPPORTED on FP32 or batch contexts. */
+int tbpm_ac_corr(tbpm_ctx *ctx, const double *psi0, double beta, double mu, double dt, int n_steps,
+                 double *corr);
+
+/* tbpm_ac_cond: Re sigma_ab(w) from the correlations of tbpm_ac_corr, on the
+ * GPU, with N = n_steps and the Hann window w_m = (1 + cos(pi m / N)) / 2:
+ *   sigma_ab(w) = (exp(-beta w) - 1) / (w s) sum_{m=0}^{N-1} dt w_m sin(w t_m) 2 Im C_ab(t_m),
+ * and sigma = 0 at w = 0 (the limit of this expression).
+ *   corr    double[2 * 4 * (n_steps+1)] as written by tbpm_ac_corr; n_steps >= 1
+ *   area    s > 0, the sample area per orbital (nm^2 when bond vectors are in nm)
+ *   omegas  double[n_w] frequencies (eV); sigma double[4 * n_w] out, rows xx, xy, yx, yy
+ * Host or device buffers. */
+int tbpm_ac_cond(tbpm_ctx *ctx, const double *corr, int n_steps, double dt, double beta, double area,
+                 const double *omegas, int n_w, double *sigma);
+
 /* ------------------------------------------- allocation-free variant */
 
 /* Largest orbital count tbpm_dos_corr_noalloc accepts. */
@@ -305,6 +358,7 @@ typedef struct tbpm_info {
     double rescale;
     int grid_blocks;           /* blocks of the single-state sweep grid         */
     int tuned;                 /* 1 when the grid was chosen by the autotuner   */
+    int fermi_terms;           /* Fermi series length of the last tbpm_ac_corr  */
 } tbpm_info;
 
 /* Fills *info with the context's layout and the counters of its last call. */

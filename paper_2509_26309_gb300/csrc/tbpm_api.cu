@@ -525,12 +525,130 @@ int enqueue_hay_chunk(tbpm_ctx *ctx, int len, int M, cudaStream_t s, int64_t *la
     return TBPM_OK;
 }
 
+// out = sum_{k<K} c_k T_k(H~) in by Clenshaw sweeps (K >= 3), one state.
+// alt: the coefficients alternate between real (even k) and imaginary (odd
+// k), as the time-step series c_k = (2 - delta_k0)(-i)^k J_k(x) does;
+// otherwise all are real (the Fermi series), and the top coefficient c_{K-1}
+// must be zero: the first sweep takes its beta from the imaginary part of
+// c_{K-1}. in and out may be the same vector. The final sweep's <in|out>
+// partials go to partial slot `slot`.
+int enqueue_series(tbpm_ctx *ctx, const double2 *coef, int K, bool alt, void *in, void *out, int slot,
+                   cudaStream_t s, int64_t *launches)
+{
+    const SweepVariant v = variant(ctx, 1);
+    SweepParams p;
+    fill_operator(ctx, p);
+    p.coef = coef;
+    p.psi = in;
+    p.psi0 = in;
+    p.partials = ctx->d_partials;
+    p.nblk = ctx->nblk;
+    void *Bv[2] = {ctx->d_b0, ctx->d_b1};
+    auto im = [alt](int k) { return alt && (k & 1) != 0; };
+    p.x = in; p.z = nullptr; p.y = Bv[0];
+    p.ia = K - 2; p.ib = -1; p.ic = K - 1; p.bscale = 1.0;
+    CU(launch_sweep(v, SW_FIRST, im(K - 2), false, p, ctx->nblk, s));
+    if (K >= 4) {
+        p.x = Bv[0]; p.z = nullptr; p.y = Bv[1];
+        p.ia = K - 3; p.ib = K - 1; p.ic = -1;
+        CU(launch_sweep(v, SW_SECOND, im(K - 3), false, p, ctx->nblk, s));
+    }
+    for (int k = K - 4; k >= 1; --k) {
+        p.x = Bv[(K - 3 - k) & 1];
+        p.y = Bv[(K - 2 - k) & 1];
+        p.z = p.y;
+        p.ia = k; p.ib = -1; p.ic = -1;
+        CU(launch_sweep(v, SW_MID, im(k), true, p, ctx->nblk, s));
+    }
+    p.x = Bv[(K - 3) & 1];
+    p.z = K >= 4 ? Bv[(K - 4) & 1] : nullptr;
+    p.y = out;
+    p.ia = 0; p.ib = K == 3 ? 2 : -1; p.ic = -1; p.bscale = 0.5;
+    p.delta = slot;
+    CU(launch_sweep(v, SW_FINAL, false, K >= 4, p, ctx->nblk, s));
+    *launches += K - 1;
+    return TBPM_OK;
+}
+
+// The three AC vectors phi2, phi1_x, phi1_y (n_pad rows each) in d_ac.
+void ac_vectors(tbpm_ctx *ctx, void *v[3])
+{
+    char *b = static_cast<char *>(ctx->d_ac);
+    const size_t vb = sizeof(double2) * (size_t)ctx->n_pad;
+    v[0] = b;
+    v[1] = b + vb;
+    v[2] = b + 2 * vb;
+}
+
+// `len` AC time steps: each advances phi2, phi1_x and phi1_y by one time
+// step (K terms) and writes the four <phi2|J_a|phi1_b> partials of the new
+// time to slot d; one reduction then stores C(t_{base+1..base+len}) into
+// d_out as [step][4] and the base counter advances.
+int enqueue_ac_chunk(tbpm_ctx *ctx, int K, int len, cudaStream_t s, int64_t *launches)
+{
+    void *v[3];
+    ac_vectors(ctx, v);
+    const int64_t W = (int64_t)ctx->nblk * (kBlockB1 / 32);
+    int rc;
+    for (int d = 0; d < len; ++d) {
+        for (int q = 0; q < 3; ++q)
+            if ((rc = enqueue_series(ctx, ctx->d_coef, K, true, v[q], v[q], kChunk, s, launches))) return rc;
+        CU(launch_jdot(ctx->cur, v[0], v[1], v[2], ctx->d_acpart, d, ctx->nblk, s));
+        ++*launches;
+    }
+    CU(launch_reduce_seg(ctx->d_acpart, len, 4, W, nullptr, 1, ctx->d_counter, 1, ctx->d_out, 0, s));
+    CU(launch_advance(ctx->d_counter, len, s));
+    *launches += 2;
+    return TBPM_OK;
+}
+
+void free_ac(tbpm_ctx *ctx)
+{
+    cudaFree(ctx->d_ac); cudaFree(ctx->d_fnodes); cudaFree(ctx->d_fc); cudaFree(ctx->d_gc);
+    cudaFree(ctx->d_kmax); cudaFree(ctx->d_acpart);
+    ctx->d_ac = nullptr; ctx->d_fnodes = nullptr; ctx->d_fc = ctx->d_gc = nullptr;
+    ctx->d_kmax = nullptr; ctx->d_acpart = nullptr;
+    ctx->fermi_K = 0;
+}
+
+void free_current(tbpm_ctx *ctx)
+{
+    cudaFree(const_cast<int64_t *>(ctx->cur.slice_off));
+    cudaFree(const_cast<int32_t *>(ctx->cur.cols));
+    cudaFree(const_cast<double2 *>(ctx->cur.jx));
+    cudaFree(const_cast<double2 *>(ctx->cur.jy));
+    ctx->cur = CurrentOp();
+    ctx->cur_nnz = 0;
+}
+
+// AC work buffers, allocated once per context.
+int ensure_ac(tbpm_ctx *ctx)
+{
+    if (ctx->d_ac) return TBPM_OK;
+    const size_t W = (size_t)ctx->nblk * (kBlockB1 / 32);
+    const size_t vb = 3 * sizeof(double2) * (size_t)ctx->n_pad;
+    cudaError_t e = cudaMalloc(&ctx->d_ac, vb);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_fnodes, sizeof(double) * 2 * kFermiCap);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_fc, sizeof(double2) * kFermiCap);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_gc, sizeof(double2) * kFermiCap);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_kmax, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_acpart, sizeof(double2) * (kChunk + 1) * 4 * W);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_ac, 0, vb, ctx->stream);
+    if (e != cudaSuccess) {
+        free_ac(ctx);
+        ctx->last_error = std::string("AC buffers: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? TBPM_ERR_OOM : TBPM_ERR_CUDA;
+    }
+    return TBPM_OK;
+}
+
 // Runs (and on first use captures) the graph of one chunk.
 int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_t ld = 0)
 {
     // kind 0: DOS, one state; 1: KPM, one state; 2: DOS, 16 states; 3: DOS, batch of
     // instances (ld = n_steps + 1 for kinds 2 and 3); 4: Haydock (ld = M); 5: DOS with
-    // quasi-eigenstate accumulation (one state; dropped at the end of the call)
+    // quasi-eigenstate accumulation (one state; dropped at the end of the call);
+    // 6: AC correlation (three states and the current-operator dots)
     const auto key = std::make_tuple(kind, len, K, (int)ld);
     auto it = ctx->graphs.find(key);
     int64_t nl = 0;
@@ -539,6 +657,7 @@ int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_
         CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
         int rc = kind == 1   ? enqueue_kpm_chunk(ctx, len, ctx->cap_stream, &nl)
                  : kind == 4 ? enqueue_hay_chunk(ctx, len, (int)ld, ctx->cap_stream, &nl)
+                 : kind == 6 ? enqueue_ac_chunk(ctx, K, len, ctx->cap_stream, &nl)
                              : enqueue_dos_chunk(ctx, K, len, kind == 2 ? 16 : 1, ld, ctx->cap_stream, &nl,
                                                  kind == 5);
         cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
@@ -550,7 +669,10 @@ int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_
         CU(ei);
         it = ctx->graphs.emplace(key, ex).first;
     } else {
-        nl = kind == 1 ? (int64_t)len + 2 : kind == 4 ? 4 * (int64_t)len : (int64_t)len * (K - 1) + 2;
+        nl = kind == 1   ? (int64_t)len + 2
+             : kind == 4 ? 4 * (int64_t)len
+             : kind == 6 ? (int64_t)len * (3 * (K - 1) + 1) + 2
+                         : (int64_t)len * (K - 1) + 2;
         if (kind != 1 && kind != 4 && (ctx->flags & TBPM_F_RENORM)) nl += len;
         if (kind == 5) nl += len;
     }
@@ -816,6 +938,8 @@ void tbpm_destroy(tbpm_ctx *ctx)
     cudaFree(ctx->d_norm); cudaFree(ctx->d_scale);
     cudaFree(ctx->d_slice_inst); cudaFree(ctx->d_seg_off); cudaFree(ctx->d_cpart);
     cudaFree(ctx->d_qe); cudaFree(ctx->d_qe_e);
+    free_ac(ctx);
+    free_current(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     cudaGetLastError();
@@ -1412,6 +1536,234 @@ int tbpm_haydock_ldos(tbpm_ctx *ctx, const double *a, const double *b, int M, co
     return TBPM_OK;
 }
 
+int tbpm_set_current(tbpm_ctx *ctx, const int64_t *row_ptr, const int32_t *col, const double *jx,
+                     const double *jy)
+{
+    if (!ctx || !row_ptr) return TBPM_ERR_ARG;
+    if (ctx->ninst > 0 || ctx->precision != TBPM_FP64) return TBPM_ERR_UNSUPPORTED;
+    const int64_t n = ctx->n;
+    if (row_ptr[0] != 0) return TBPM_ERR_CSR;
+    for (int64_t i = 0; i < n; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return TBPM_ERR_CSR;
+    const int64_t nnz = row_ptr[n];
+    if (nnz > 0 && (!col || !jx || !jy)) return TBPM_ERR_ARG;
+    for (int64_t q = 0; q < nnz; ++q)
+        if (col[q] < 0 || (int64_t)col[q] >= n) return TBPM_ERR_CSR;
+    for (int64_t q = 0; q < 2 * nnz; ++q)
+        if (!std::isfinite(jx[q]) || !std::isfinite(jy[q])) return TBPM_ERR_ARG;
+    // rows sorted by column, duplicates summed
+    std::vector<int64_t> rp(n + 1, 0);
+    std::vector<int32_t> cc;
+    std::vector<double2> vx, vy;
+    cc.reserve(nnz); vx.reserve(nnz); vy.reserve(nnz);
+    std::vector<std::pair<int32_t, int64_t>> row;
+    for (int64_t i = 0; i < n; ++i) {
+        row.clear();
+        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) row.emplace_back(col[q], q);
+        std::sort(row.begin(), row.end());
+        size_t a = 0;
+        while (a < row.size()) {
+            const int32_t c = row[a].first;
+            double2 x = make_double2(0.0, 0.0), y = make_double2(0.0, 0.0);
+            for (; a < row.size() && row[a].first == c; ++a) {
+                const int64_t q = row[a].second;
+                x.x += jx[2 * q]; x.y += jx[2 * q + 1];
+                y.x += jy[2 * q]; y.y += jy[2 * q + 1];
+            }
+            cc.push_back(c); vx.push_back(x); vy.push_back(y);
+        }
+        rp[i + 1] = (int64_t)cc.size();
+    }
+    if (!(ctx->flags & TBPM_F_NO_HERMITIAN_CHECK)) {
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+                const int32_t j = cc[q];
+                const int32_t *b = cc.data() + rp[j], *e = cc.data() + rp[j + 1];
+                const int32_t *f = std::lower_bound(b, e, (int32_t)i);
+                double2 tx = make_double2(0.0, 0.0), ty = make_double2(0.0, 0.0);
+                if (f != e && *f == (int32_t)i) {
+                    const int64_t r = f - cc.data();
+                    tx = make_double2(vx[r].x, -vx[r].y);
+                    ty = make_double2(vy[r].x, -vy[r].y);
+                }
+                const double sx = std::hypot(vx[q].x, vx[q].y) + std::hypot(tx.x, tx.y);
+                const double sy = std::hypot(vy[q].x, vy[q].y) + std::hypot(ty.x, ty.y);
+                if (std::hypot(vx[q].x - tx.x, vx[q].y - tx.y) > 1e-13 * sx ||
+                    std::hypot(vy[q].x - ty.x, vy[q].y - ty.y) > 1e-13 * sy)
+                    return TBPM_ERR_NOT_HERMITIAN;
+            }
+    }
+    // SELL-32, padding entries: own row, value 0
+    const int64_t nsl = ctx->n_pad / kSlice;
+    std::vector<int64_t> off(nsl + 1, 0);
+    for (int64_t sl = 0; sl < nsl; ++sl) {
+        int64_t w = 0;
+        for (int l = 0; l < kSlice; ++l) {
+            const int64_t r = sl * kSlice + l;
+            if (r < n) w = std::max(w, rp[r + 1] - rp[r]);
+        }
+        off[sl + 1] = off[sl] + w * kSlice;
+    }
+    const int64_t nent = off[nsl];
+    std::vector<int32_t> scol(nent);
+    std::vector<double2> sx(nent, make_double2(0.0, 0.0)), sy(nent, make_double2(0.0, 0.0));
+    for (int64_t sl = 0; sl < nsl; ++sl) {
+        const int64_t w = (off[sl + 1] - off[sl]) / kSlice;
+        for (int l = 0; l < kSlice; ++l) {
+            const int64_t r = sl * kSlice + l;
+            const int64_t len = r < n ? rp[r + 1] - rp[r] : 0;
+            for (int64_t q = 0; q < w; ++q) {
+                const int64_t e = off[sl] + q * kSlice + l;
+                if (q < len) {
+                    scol[e] = cc[rp[r] + q];
+                    sx[e] = vx[rp[r] + q];
+                    sy[e] = vy[rp[r] + q];
+                } else {
+                    scol[e] = (int32_t)r;
+                }
+            }
+        }
+    }
+    CU(cudaSetDevice(ctx->device));
+    if (ctx->stream) CU(cudaStreamSynchronize(ctx->stream));
+    free_current(ctx);
+    int rc;
+    void *d_off = nullptr, *d_col = nullptr, *d_x = nullptr, *d_y = nullptr;
+    if ((rc = upload(ctx, &d_off, off)) || (rc = upload(ctx, &d_col, scol)) || (rc = upload(ctx, &d_x, sx)) ||
+        (rc = upload(ctx, &d_y, sy))) {
+        cudaFree(d_off); cudaFree(d_col); cudaFree(d_x); cudaFree(d_y);
+        return rc;
+    }
+    ctx->cur.nslices = nsl;
+    ctx->cur.slice_off = static_cast<int64_t *>(d_off);
+    ctx->cur.cols = static_cast<int32_t *>(d_col);
+    ctx->cur.jx = static_cast<double2 *>(d_x);
+    ctx->cur.jy = static_cast<double2 *>(d_y);
+    ctx->cur_nnz = (int64_t)cc.size();
+    destroy_graphs(ctx);
+    return TBPM_OK;
+}
+
+int tbpm_ac_corr(tbpm_ctx *ctx, const double *psi0, double beta, double mu, double dt, int n_steps,
+                 double *corr)
+{
+    if (!ctx || !psi0 || !corr || n_steps < 0) return TBPM_ERR_ARG;
+    if (ctx->ninst > 0 || ctx->precision != TBPM_FP64) return TBPM_ERR_UNSUPPORTED;
+    if (!ctx->cur.slice_off) {
+        ctx->last_error = "tbpm_ac_corr: no current operators (tbpm_set_current)";
+        return TBPM_ERR_ARG;
+    }
+    if (!(beta > 0.0) || !std::isfinite(beta) || !std::isfinite(mu)) return TBPM_ERR_ARG;
+    if (!(dt != 0.0) || !std::isfinite(dt)) return TBPM_ERR_ARG;
+    const double x = dt * ctx->rescale;
+    if (!(std::fabs(x) <= 40.0)) return TBPM_ERR_ARG;
+    CU(cudaSetDevice(ctx->device));
+    bool in_dev, out_dev;
+    int rc;
+    if ((rc = classify(ctx, psi0, &in_dev)) || (rc = classify(ctx, corr, &out_dev))) return rc;
+    const int64_t n = ctx->n, np1 = (int64_t)n_steps + 1;
+    int K;
+    if ((rc = ensure_coeffs(ctx, x, &K))) return rc;
+    const int Ke = std::max(K, 3);
+    if ((rc = ensure_work(ctx, 1, (size_t)4 * np1,
+                          (in_dev && out_dev) ? 0 : (size_t)std::max<int64_t>(2 * n, 8 * np1))))
+        return rc;
+    if ((rc = ensure_ac(ctx))) return rc;
+    cudaStream_t s = ctx->stream;
+    int64_t launches = 0;
+    if (ctx->fermi_K == 0 || beta != ctx->fermi_beta || mu != ctx->fermi_mu) {
+        ctx->fermi_K = 0;
+        CU(launch_fermi_coeffs(beta, mu, ctx->rescale, 1e-12, kFermiCap, ctx->d_fnodes, ctx->d_fc, ctx->d_gc,
+                               ctx->d_kmax, s));
+        int kf = 0;
+        CU(cudaMemcpyAsync(&kf, ctx->d_kmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        launches += 2;
+        if (kf >= kFermiCap) {
+            ctx->last_error = "tbpm_ac_corr: the Fermi series needs more than TBPM_FERMI_MAX_TERMS terms";
+            return TBPM_ERR_ARG;
+        }
+        kf = std::max(kf, 1);
+        // zero tail: the series below runs max(kf + 1, 4) terms with a zero top coefficient
+        CU(cudaMemsetAsync(ctx->d_fc + kf, 0, sizeof(double2) * (kFermiCap - kf), s));
+        CU(cudaMemsetAsync(ctx->d_gc + kf, 0, sizeof(double2) * (kFermiCap - kf), s));
+        ctx->fermi_K = kf;
+        ctx->fermi_beta = beta;
+        ctx->fermi_mu = mu;
+    }
+    const int Kp = std::max(ctx->fermi_K + 1, 4);
+    void *v[3];
+    ac_vectors(ctx, v);
+    const double *src;
+    if ((rc = stage_input(ctx, psi0, in_dev, (size_t)2 * n, &src))) return rc;
+    CU(launch_load_states(ctx->precision, src, n, ctx->n_pad, 1, 0, 1, ctx->d_psi0, ctx->d_psi, s));
+    ++launches;
+    // phi2 = f(H~) phi;  phi1_b = [1 - f(H~)] J_b phi
+    if ((rc = enqueue_series(ctx, ctx->d_fc, Kp, false, ctx->d_psi0, v[0], kChunk, s, &launches))) return rc;
+    for (int b = 0; b < 2; ++b) {
+        CU(launch_jmul(ctx->cur, b == 0 ? ctx->cur.jx : ctx->cur.jy, ctx->d_psi0, ctx->d_psi, 2 * ctx->nblk, s));
+        ++launches;
+        if ((rc = enqueue_series(ctx, ctx->d_gc, Kp, false, ctx->d_psi, v[1 + b], kChunk, s, &launches)))
+            return rc;
+    }
+    // C(t_0), then the time steps
+    const int64_t W = (int64_t)ctx->nblk * (kBlockB1 / 32);
+    CU(launch_jdot(ctx->cur, v[0], v[1], v[2], ctx->d_acpart, 0, ctx->nblk, s));
+    CU(launch_reduce_seg(ctx->d_acpart, 1, 4, W, nullptr, 1, nullptr, 0, ctx->d_out, 0, s));
+    CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), s));
+    launches += 2;
+    int done = 0;
+    while (done < n_steps) {
+        const int len = std::min(kChunk, n_steps - done);
+        if ((rc = run_chunk(ctx, 6, Ke, len, &launches))) return rc;
+        done += len;
+    }
+    double2 *dst = out_dev ? reinterpret_cast<double2 *>(corr) : reinterpret_cast<double2 *>(ctx->d_stage);
+    CU(launch_ac_transpose(ctx->d_out, np1, dst, s));
+    ++launches;
+    if (!out_dev) CU(cudaMemcpyAsync(corr, dst, sizeof(double2) * 4 * np1, cudaMemcpyDeviceToHost, s));
+    if (!out_dev || !in_dev) CU(cudaStreamSynchronize(s));
+    CU(cudaGetLastError());
+    ctx->last_K = Ke;
+    ctx->last_passes = (int64_t)3 * n_steps * (Ke - 1) + 3 * (int64_t)(Kp - 1) + 2 + (int64_t)n_steps + 1;
+    ctx->last_launches = launches;
+    return TBPM_OK;
+}
+
+int tbpm_ac_cond(tbpm_ctx *ctx, const double *corr, int n_steps, double dt, double beta, double area,
+                 const double *omegas, int n_w, double *sigma)
+{
+    if (!ctx || !corr || !omegas || !sigma || n_steps < 1 || n_w < 1) return TBPM_ERR_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt) || !(beta > 0.0) || !std::isfinite(beta) || !(area > 0.0) ||
+        !std::isfinite(area) || n_steps > (1 << 28) || n_w > (1 << 24))
+        return TBPM_ERR_ARG;
+    CU(cudaSetDevice(ctx->device));
+    bool c_dev, w_dev, s_dev;
+    int rc;
+    if ((rc = classify(ctx, corr, &c_dev)) || (rc = classify(ctx, omegas, &w_dev)) ||
+        (rc = classify(ctx, sigma, &s_dev)))
+        return rc;
+    const size_t nc = 8 * ((size_t)n_steps + 1);
+    if ((rc = ensure_work(ctx, 1, 0, nc + (size_t)n_w + 4 * (size_t)n_w))) return rc;
+    cudaStream_t s = ctx->stream;
+    const double2 *c = reinterpret_cast<const double2 *>(corr);
+    if (!c_dev) {
+        CU(cudaMemcpyAsync(ctx->d_stage, corr, nc * sizeof(double), cudaMemcpyHostToDevice, s));
+        c = reinterpret_cast<const double2 *>(ctx->d_stage);
+    }
+    const double *w = omegas;
+    if (!w_dev) {
+        CU(cudaMemcpyAsync(ctx->d_stage + nc, omegas, n_w * sizeof(double), cudaMemcpyHostToDevice, s));
+        w = ctx->d_stage + nc;
+    }
+    double *dsg = s_dev ? sigma : ctx->d_stage + nc + n_w;
+    CU(launch_ac_cond(c, n_steps, dt, beta, area, w, n_w, dsg, s));
+    if (!s_dev) CU(cudaMemcpyAsync(sigma, dsg, 4 * (size_t)n_w * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (!c_dev || !w_dev || !s_dev) CU(cudaStreamSynchronize(s));
+    ctx->last_launches = 1;
+    return TBPM_OK;
+}
+
 int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info)
 {
     if (!ctx || !info) return TBPM_ERR_ARG;
@@ -1427,6 +1779,7 @@ int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info)
     info->rescale = ctx->rescale;
     info->grid_blocks = ctx->nblk;
     info->tuned = ctx->tuned ? 1 : 0;
+    info->fermi_terms = ctx->fermi_K;
     return TBPM_OK;
 }
 

@@ -84,6 +84,18 @@ struct SweepParams {
     const int32_t *slice_inst;
 };
 
+// Current operators J_x, J_y on one SELL-32 pattern (complex values, any
+// diagonal entries kept among the entries; padding: own row, value 0).
+struct CurrentOp {
+    int64_t nslices = 0;
+    const int64_t *slice_off = nullptr;
+    const int32_t *cols = nullptr;
+    const double2 *jx = nullptr;
+    const double2 *jy = nullptr;
+};
+
+constexpr int kFermiCap = TBPM_FERMI_MAX_TERMS;   // Fermi series terms; 2x as many quadrature nodes
+
 // KPM sweep: T_{m+1} = 2 H~ T_m - T_{m-1} with <T_m|T_m> and <T_{m+1}|T_m>.
 struct KpmParams {
     int64_t n;
@@ -171,6 +183,16 @@ struct tbpm_ctx {
     size_t qe_cap = 0, qe_e_cap = 0;
     int qe_ne = 0, qe_N = 0;
     double qe_h = 0.0;
+    // AC conductivity: current operators (tbpm_set_current) and their work buffers
+    tbpm::CurrentOp cur;
+    int64_t cur_nnz = 0;
+    void *d_ac = nullptr;                // phi2, phi1_x, phi1_y: [3][n_pad] double2
+    double *d_fnodes = nullptr;          // [2 kFermiCap] f at the quadrature nodes
+    double2 *d_fc = nullptr, *d_gc = nullptr;   // [kFermiCap] series of f and of 1 - f
+    int *d_kmax = nullptr;
+    double2 *d_acpart = nullptr;         // [(kChunk + 1) * 4 * warps] jdot partials
+    double fermi_beta = 0.0, fermi_mu = 0.0;
+    int fermi_K = 0;                     // 0: no coefficients cached
     // autotuner: (blocks per SM, ms per middle sweep) of each candidate grid
     bool tuned = false;
     std::vector<std::pair<int, float>> tune_ms;
@@ -228,6 +250,23 @@ bool cluster_fits(int precision, int64_t n_pad, int *log_rows, int *ncta, size_t
 cudaError_t launch_cluster_dos(int precision, bool real_values, const SweepParams &op, int max_width,
                                const void *psi0, const double2 *coef, int K, int n_steps,
                                double2 *partials, void *psi_out, cudaStream_t s);
+
+// AC conductivity (ac.cu). Fermi series: fc[k] = a_k, gc[k] = delta_k0 - a_k
+// for k < kcap (fj: 2 kcap doubles of scratch), *kmax = 1 + the last k with
+// |a_k| >= tol.
+cudaError_t launch_fermi_coeffs(double beta, double mu, double rescale, double tol, int kcap, double *fj,
+                                double2 *fc, double2 *gc, int *kmax, cudaStream_t s);
+// y = J x (one of j.jx, j.jy as vals), FP64 complex vectors of n_pad rows.
+cudaError_t launch_jmul(const CurrentOp &j, const double2 *vals, const void *x, void *y, int grid, cudaStream_t s);
+// <phi2|J_a|phi1_b> for ab = xx, xy, yx, yy: per-warp partials
+// partials[(slot * 4 + q) * W + w], W = grid * kBlockB1 / 32.
+cudaError_t launch_jdot(const CurrentOp &j, const void *phi2, const void *p1x, const void *p1y,
+                        double2 *partials, int slot, int grid, cudaStream_t s);
+// [n+1][4] -> [4][n+1]
+cudaError_t launch_ac_transpose(const double2 *src, int64_t np1, double2 *dst, cudaStream_t s);
+// Re sigma_q(w_j) for the 4 correlation rows of corr [4][n_steps+1]: sigma [4][n_w].
+cudaError_t launch_ac_cond(const double2 *corr, int n_steps, double dt, double beta, double area,
+                           const double *omegas, int n_w, double *sigma, cudaStream_t s);
 
 // dst (FP64 complex [n]) = scale[col] * column col of an interleaved [n_pad][B]
 // buffer (scale may be null) (aux.cu).

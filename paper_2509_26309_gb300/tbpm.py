@@ -55,7 +55,7 @@ class tbpm_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("path", C.c_int), ("precision", C.c_int),
                 ("real_values", C.c_int), ("num_terms", C.c_int), ("passes", C.c_int64),
                 ("kernel_launches", C.c_int64), ("gershgorin", C.c_double), ("rescale", C.c_double),
-                ("grid_blocks", C.c_int), ("tuned", C.c_int)]
+                ("grid_blocks", C.c_int), ("tuned", C.c_int), ("fermi_terms", C.c_int)]
 
 
 class TbpmError(RuntimeError):
@@ -91,9 +91,15 @@ SIGNATURES = {
     "tbpm_batch_dos_corr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "tbpm_dos_corr_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                         C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p]),
+    "tbpm_set_current": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tbpm_ac_corr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_int,
+                               C.c_void_p]),
+    "tbpm_ac_cond": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double,
+                               C.c_void_p, C.c_int, C.c_void_p]),
 }
 
 TBPM_NOALLOC_MAX_N = 65536
+TBPM_FERMI_MAX_TERMS = 8192
 
 
 class tbpm_instance(C.Structure):
@@ -378,6 +384,50 @@ def kpm_dos_jackson(ctx: Ctx, mu, n_e: int):
     _check(lib().kpm_dos_jackson(ctx.handle, _ptr(mu), int(mu.shape[-1]), int(n_e), _ptr(e), _ptr(r)),
            "kpm_dos_jackson")
     return e, r
+
+
+def tbpm_set_current(ctx: Ctx, row_ptr, col, jx, jy) -> None:
+    """Current operators J_x, J_y on one CSR pattern (host arrays: int64, int32,
+    complex128, complex128)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    jx = np.ascontiguousarray(jx, dtype=np.complex128)
+    jy = np.ascontiguousarray(jy, dtype=np.complex128)
+    if row_ptr.shape != (ctx.n + 1,):
+        raise ValueError("row_ptr must have n + 1 entries")
+    nnz = int(row_ptr[-1])
+    if col.shape != (nnz,) or jx.shape != (nnz,) or jy.shape != (nnz,):
+        raise ValueError("col, jx and jy must have row_ptr[n] entries")
+    _check(lib().tbpm_set_current(ctx.handle, _ptr(row_ptr), _ptr(col), _ptr(jx), _ptr(jy)), "tbpm_set_current")
+
+
+def tbpm_ac_corr(ctx: Ctx, psi0, beta: float, mu: float, dt: float, n_steps: int, out=None):
+    """C_ab(t_n) for ab = xx, xy, yx, yy: complex128 (4, n_steps + 1)."""
+    a, ns, cuda = _complex_in(psi0, ctx.n)
+    if ns != 1:
+        raise ValueError("tbpm_ac_corr takes one state")
+    if out is None:
+        out = _alloc((4, n_steps + 1), np.complex128, cuda, a.device if cuda else None)
+    _check(lib().tbpm_ac_corr(ctx.handle, _ptr(a), float(beta), float(mu), float(dt), int(n_steps), _ptr(out)),
+           "tbpm_ac_corr")
+    return out
+
+
+def tbpm_ac_cond(ctx: Ctx, corr, dt: float, beta: float, area: float, omegas):
+    """Re sigma_ab(w) for the four rows of corr (4, n_steps + 1): float64 (4, n_w)."""
+    cuda = _is_torch(corr) and corr.is_cuda
+    if not _is_torch(corr):
+        corr = np.ascontiguousarray(corr, dtype=np.complex128)
+    if not _is_torch(omegas):
+        omegas = np.ascontiguousarray(omegas, dtype=np.float64)
+    if tuple(corr.shape[:1]) != (4,):
+        raise ValueError("corr must have 4 rows")
+    n_steps = int(corr.shape[-1]) - 1
+    n_w = int(omegas.shape[0])
+    out = _alloc((4, n_w), np.float64, cuda, corr.device if cuda else None)
+    _check(lib().tbpm_ac_cond(ctx.handle, _ptr(corr), n_steps, float(dt), float(beta), float(area), _ptr(omegas),
+                              n_w, _ptr(out)), "tbpm_ac_cond")
+    return out
 
 
 def tbpm_get_info(ctx: Ctx) -> dict:
