@@ -348,7 +348,8 @@ def run_variants(args, dev, stream):
       - FP32 block of 16 states vs FP64 single state on graphene 4096x4096,
         W = 1 (N = 33,554,432, the paper's benchmark lattice), stencil and
         stored-matrix paths, 32 steps each (the speedup is a throughput ratio,
-        so the step count only sets the sample length); DOS L1 of state 0.
+        so the step count only sets the sample length); DOS L1 of state 0;
+      - the AC current correlation on graphene 1024x1024 (W = 1) at 300 K.
     The FP64 runs the errors are taken against are the path the parity tests
     hold to 1e-10 of the oracle."""
     import numpy as np
@@ -467,6 +468,27 @@ def run_variants(args, dev, stream):
         res[f"fp32_batched_speedup_vs_fp64_{path}"] = v32 / v64
         tb.tbpm_destroy(ctx64)
     res["fp32_batched_speedup_vs_fp64"] = res["fp32_batched_speedup_vs_fp64_stencil"]
+    del blk, one
+    # AC conductivity correlation on the config-2 lattice: room temperature,
+    # mu = 0, 64 steps; units count the Hamiltonian sweeps (three Fermi series
+    # and three states per time step)
+    n2 = 2 * L1 * L2
+    h2 = build_inputs()
+    cur = ti.graphene_current(L1, L2)
+    cac = tb.tbpm_create(n2, h2.row_ptr, h2.col, h2.val, RESCALE, tb.make_opts(stream=so))
+    tb.tbpm_set_current(cac, *cur.as_tuple())
+    del h2, cur
+    pac = torch.from_numpy(ti.random_phase_state(n2, 0)).to(dev)
+    oac = torch.empty((4, 65), dtype=torch.complex128, device=dev)
+    beta = 1.0 / 0.025852
+    msac = timed_calls(lambda: tb.tbpm_ac_corr(cac, pac, beta, 0.0, DT, 64, out=oac), 1, stream)
+    info = tb.tbpm_get_info(cac)
+    kp = max(info["fermi_terms"] + 1, 4)
+    sweeps = 3 * (kp - 1) + 3 * 64 * (info["num_terms"] - 1)
+    res["fp64_ac_corr_1024x1024"] = {"value": n2 * sweeps / (msac / 1e3), "unit": UNIT, "ms_per_call": msac,
+                                     "n_steps": 64, "fermi_terms": info["fermi_terms"], "beta": beta,
+                                     "sweeps": sweeps}
+    tb.tbpm_destroy(cac)
     return res
 
 
