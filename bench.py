@@ -349,6 +349,8 @@ def run_variants(args, dev, stream):
         W = 1 (N = 33,554,432, the paper's benchmark lattice), stencil and
         stored-matrix paths, 32 steps each (the speedup is a throughput ratio,
         so the step count only sets the sample length); DOS L1 of state 0;
+      - FP32 single state on that stencil, temporally blocked vs one launch per
+        sweep;
       - the AC current correlation on graphene 1024x1024 (W = 1) at 300 K.
     The FP64 runs the errors are taken against are the path the parity tests
     hold to 1e-10 of the oracle."""
@@ -468,6 +470,21 @@ def run_variants(args, dev, stream):
         res[f"fp32_batched_speedup_vs_fp64_{path}"] = v32 / v64
         tb.tbpm_destroy(ctx64)
     res["fp32_batched_speedup_vs_fp64"] = res["fp32_batched_speedup_vs_fp64_stencil"]
+    # FP32 single state on the same stencil: temporally blocked sweeps (kTbS = 6
+    # terms per pass over a tile in shared memory) against one launch per sweep
+    for name, flags in (("fp32_x1_stencil_tblock_4096x4096", 0),
+                        ("fp32_x1_stencil_per_sweep_4096x4096", tb.TBPM_F_NO_TBLOCK)):
+        c1s = tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l4, l4, ti.T_GRAPHENE, 0.0, eps, RESCALE,
+                                     tb.make_opts(precision=tb.TBPM_FP32, path=tb.TBPM_PATH_STENCIL, flags=flags,
+                                                  stream=so))
+        ms1s = timed_calls(lambda: tb.tbpm_dos_corr(c1s, one, DT, steps, out=o1), 2, stream)
+        K = tb.tbpm_get_info(c1s)["num_terms"]
+        res[name] = {"value": n4 * steps * (K - 1) / (ms1s / 1e3), "unit": UNIT, "ms_per_call": ms1s, "states": 1,
+                     "n_steps": steps, "kernel_launches": tb.tbpm_get_info(c1s)["kernel_launches"],
+                     "max_abs_dC_vs_fp64": float(np.max(np.abs(o1[0].cpu().numpy() - ref4)))}
+        tb.tbpm_destroy(c1s)
+    res["fp32_tblock_speedup_vs_per_sweep"] = (res["fp32_x1_stencil_tblock_4096x4096"]["value"] /
+                                               res["fp32_x1_stencil_per_sweep_4096x4096"]["value"])
     del blk, one
     # AC conductivity correlation on the config-2 lattice: room temperature,
     # mu = 0, 64 steps; units count the Hamiltonian sweeps (three Fermi series

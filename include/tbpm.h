@@ -71,6 +71,11 @@ extern "C" {
                                           operator for grids of 1 .. occupancy
                                           blocks per SM (and twice occupancy) and
                                           keep the fastest for the context's life */
+#define TBPM_F_NO_TBLOCK          0x20u /* FP32 monolayer stencil contexts run each
+                                          time step's sweeps in temporally blocked
+                                          launches (several sweeps per pass over a
+                                          lattice tile in shared memory); this flag
+                                          keeps one launch per sweep instead       */
 
 typedef struct tbpm_opts {
     int precision;       /* TBPM_FP64 | TBPM_FP32                                  */

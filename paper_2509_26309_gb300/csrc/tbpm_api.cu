@@ -345,7 +345,8 @@ int ensure_work(tbpm_ctx *ctx, int states, size_t out_elems, size_t stage_double
         // single-state partials: one per slice; 16-state partials: one per block and state
         const size_t nsl = (size_t)(ctx->n_pad / kSlice);
         const size_t W = (size_t)ctx->nblk * (kBlockB1 / 32);
-        const size_t per_slot = std::max<size_t>(std::max(2 * nsl, 2 * W), (size_t)ctx->nblk16 * kMaxBlockStates);
+        const size_t per_slot = std::max<size_t>(std::max(std::max(2 * nsl, 2 * W), (size_t)ctx->num_sms * 32),
+                                                 (size_t)ctx->nblk16 * kMaxBlockStates);
         ctx->partials_cap = (size_t)(kChunk + 1) * per_slot;
         CU(cudaMalloc(&ctx->d_partials, ctx->partials_cap * sizeof(double2)));
         if (ctx->flags & TBPM_F_RENORM) {
@@ -642,13 +643,85 @@ int ensure_ac(tbpm_ctx *ctx)
     return TBPM_OK;
 }
 
+// Whether single-state time steps take the temporally blocked kernel: FP32
+// monolayer stencil without renormalisation, unless TBPM_F_NO_TBLOCK.
+bool use_tblock(const tbpm_ctx *ctx)
+{
+    return ctx->op == OP_STENCIL_MONO && ctx->precision == TBPM_FP32 && ctx->ninst == 0 &&
+           !(ctx->flags & (TBPM_F_RENORM | TBPM_F_NO_TBLOCK));
+}
+
+// The temporally blocked path's extra vectors (two b buffers, a second state).
+int ensure_tb(tbpm_ctx *ctx)
+{
+    if (ctx->d_tb) return TBPM_OK;
+    CU(tb_prepare());
+    const size_t vb = 3 * sizeof(float2) * (size_t)ctx->n_pad;
+    CU(cudaMalloc(&ctx->d_tb, vb));
+    CU(cudaMemsetAsync(ctx->d_tb, 0, vb, ctx->stream));
+    int t1, t2;
+    ctx->tb_grid = std::min(ctx->num_sms, tb_tiles(ctx->sten.l1, ctx->sten.l2, &t1, &t2));
+    return TBPM_OK;
+}
+
+// `len` single-state time steps by temporally blocked launches: each step runs
+// its K - 1 sweeps as ceil((K-1)/kTbS) launches; blocks alternate between the
+// b-buffer pairs (b0, b1) and (tb0, tb1), and each step writes psi(t_{n+1})
+// to the other state buffer (a chunk of odd length copies it back, so every
+// chunk ends with the state in d_psi). The final launch of step d writes the
+// <psi0|psi> partials of slot d, one per warp of the grid.
+int enqueue_tb_chunk(tbpm_ctx *ctx, int K, int len, cudaStream_t s, int64_t *launches)
+{
+    const size_t vb = sizeof(float2) * (size_t)ctx->n_pad;
+    char *tb = static_cast<char *>(ctx->d_tb);
+    float2 *P[4] = {static_cast<float2 *>(ctx->d_b0), static_cast<float2 *>(ctx->d_b1),
+                    reinterpret_cast<float2 *>(tb), reinterpret_cast<float2 *>(tb + vb)};
+    float2 *S[2] = {static_cast<float2 *>(ctx->d_psi), reinterpret_cast<float2 *>(tb + 2 * vb)};
+    TbParams p;
+    memset(&p, 0, sizeof(p));
+    p.L1 = (int)ctx->sten.l1;
+    p.L2 = (int)ctx->sten.l2;
+    tb_tiles(ctx->sten.l1, ctx->sten.l2, &p.tiles1, &p.tiles2);
+    p.t = (float)ctx->sten.t;
+    p.onsite = static_cast<const float *>(ctx->sten.onsite);
+    p.psi0 = static_cast<const float2 *>(ctx->d_psi0);
+    p.partials = ctx->d_partials;
+    p.coef = ctx->d_coef;
+    p.K = K;
+    const int grid = ctx->tb_grid;
+    for (int d = 0; d < len; ++d) {
+        p.psi = S[d & 1];
+        p.psi_out = S[(d + 1) & 1];
+        p.delta = d;
+        int pair = 0;
+        for (int j0 = 0; j0 < K - 1; j0 += kTbS) {
+            p.j0 = j0;
+            p.S = std::min(kTbS, K - 1 - j0);
+            p.bx = P[2 * (pair ^ 1)];
+            p.bz = P[2 * (pair ^ 1) + 1];
+            p.ox = P[2 * pair];
+            p.oz = P[2 * pair + 1];
+            CU(launch_tb_block(p, grid, s));
+            ++*launches;
+            pair ^= 1;
+        }
+    }
+    if (len & 1) CU(cudaMemcpyAsync(S[0], S[1], vb, cudaMemcpyDeviceToDevice, s));
+    CU(launch_reduce_seg(ctx->d_partials, len, 1, (int64_t)grid * (kTbThreads / 32), nullptr, 1, ctx->d_counter,
+                         1, ctx->d_out, 0, s));
+    CU(launch_advance(ctx->d_counter, len, s));
+    *launches += 2;
+    return TBPM_OK;
+}
+
 // Runs (and on first use captures) the graph of one chunk.
 int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_t ld = 0)
 {
     // kind 0: DOS, one state; 1: KPM, one state; 2: DOS, 16 states; 3: DOS, batch of
     // instances (ld = n_steps + 1 for kinds 2 and 3); 4: Haydock (ld = M); 5: DOS with
     // quasi-eigenstate accumulation (one state; dropped at the end of the call);
-    // 6: AC correlation (three states and the current-operator dots)
+    // 6: AC correlation (three states and the current-operator dots); 7: DOS, one
+    // state, temporally blocked stencil sweeps
     const auto key = std::make_tuple(kind, len, K, (int)ld);
     auto it = ctx->graphs.find(key);
     int64_t nl = 0;
@@ -658,6 +731,7 @@ int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_
         int rc = kind == 1   ? enqueue_kpm_chunk(ctx, len, ctx->cap_stream, &nl)
                  : kind == 4 ? enqueue_hay_chunk(ctx, len, (int)ld, ctx->cap_stream, &nl)
                  : kind == 6 ? enqueue_ac_chunk(ctx, K, len, ctx->cap_stream, &nl)
+                 : kind == 7 ? enqueue_tb_chunk(ctx, K, len, ctx->cap_stream, &nl)
                              : enqueue_dos_chunk(ctx, K, len, kind == 2 ? 16 : 1, ld, ctx->cap_stream, &nl,
                                                  kind == 5);
         cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
@@ -672,6 +746,7 @@ int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_
         nl = kind == 1   ? (int64_t)len + 2
              : kind == 4 ? 4 * (int64_t)len
              : kind == 6 ? (int64_t)len * (3 * (K - 1) + 1) + 2
+             : kind == 7 ? (int64_t)len * ((K - 2) / kTbS + 1) + 2
                          : (int64_t)len * (K - 1) + 2;
         if (kind != 1 && kind != 4 && (ctx->flags & TBPM_F_RENORM)) nl += len;
         if (kind == 5) nl += len;
@@ -743,7 +818,7 @@ static int check_opts(const tbpm_opts *in, tbpm_opts *o)
     if (o->precision != TBPM_FP64 && o->precision != TBPM_FP32) return TBPM_ERR_ARG;
     if (o->path < TBPM_PATH_AUTO || o->path > TBPM_PATH_STENCIL) return TBPM_ERR_ARG;
     if (o->flags & ~(unsigned)(TBPM_F_NO_HERMITIAN_CHECK | TBPM_F_FORCE_RESCALE | TBPM_F_RENORM |
-                               TBPM_F_NO_CLUSTER | TBPM_F_AUTOTUNE))
+                               TBPM_F_NO_CLUSTER | TBPM_F_AUTOTUNE | TBPM_F_NO_TBLOCK))
         return TBPM_ERR_ARG;
     if (o->bessel_tol == 0.0) o->bessel_tol = 1e-12;
     if (!(o->bessel_tol > 0.0 && o->bessel_tol < 1e-2)) return TBPM_ERR_ARG;
@@ -940,6 +1015,7 @@ void tbpm_destroy(tbpm_ctx *ctx)
     cudaFree(ctx->d_qe); cudaFree(ctx->d_qe_e);
     free_ac(ctx);
     free_current(ctx);
+    cudaFree(ctx->d_tb);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     cudaGetLastError();
@@ -1078,10 +1154,12 @@ static int run_dos(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, in
                                  ctx->stream));
             launches += 2;
         } else {
+            const bool tbk = use_tblock(ctx);
+            if (tbk && (rc = ensure_tb(ctx))) return rc;
             int done = 0;
             while (done < n_steps) {
                 const int len = std::min(kChunk, n_steps - done);
-                if ((rc = run_chunk(ctx, 0, Ke, len, &launches))) return rc;
+                if ((rc = run_chunk(ctx, tbk ? 7 : 0, Ke, len, &launches))) return rc;
                 done += len;
             }
         }

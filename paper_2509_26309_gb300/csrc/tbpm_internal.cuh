@@ -96,6 +96,32 @@ struct CurrentOp {
 
 constexpr int kFermiCap = TBPM_FERMI_MAX_TERMS;   // Fermi series terms; 2x as many quadrature nodes
 
+// Temporally blocked sweeps on the monolayer stencil, FP32, one state
+// (cheb_tblock.cu): one launch runs sweeps [j0, j0 + S) of a time step's
+// K - 1 Clenshaw sweeps (j = 0 first, j = K - 2 final) over lattice tiles.
+constexpr int kTbS = 6;            // sweeps per block
+constexpr int kTbThreads = 1024;
+struct TbParams {
+    int L1, L2;
+    int tiles1, tiles2;
+    float t;                       // pre-scaled hopping 2 t / rescale
+    const float *onsite;           // pre-scaled on-site energies, or nullptr
+    const float2 *psi;             // psi(t_n)
+    const float2 *bx, *bz;         // b_{k+1}, b_{k+2} at the block start (unused for j0 = 0)
+    float2 *ox, *oz;               // the block's newest b and the one before (non-final blocks)
+    float2 *psi_out;               // psi(t_{n+1}) (the block holding the final sweep)
+    const float2 *psi0;
+    double2 *partials;             // final block: <psi0|psi> partials, slot delta, one per warp
+    int delta;
+    const double2 *coef;
+    int K, j0, S;
+};
+size_t tb_smem_bytes();
+int tb_tiles(int64_t l1, int64_t l2, int *tiles1, int *tiles2);
+// Opts the kernel in to its shared memory on the current device (before any capture).
+cudaError_t tb_prepare();
+cudaError_t launch_tb_block(const TbParams &p, int grid, cudaStream_t s);
+
 // KPM sweep: T_{m+1} = 2 H~ T_m - T_{m-1} with <T_m|T_m> and <T_{m+1}|T_m>.
 struct KpmParams {
     int64_t n;
@@ -192,6 +218,9 @@ struct tbpm_ctx {
     int *d_kmax = nullptr;
     double2 *d_acpart = nullptr;         // [(kChunk + 1) * 4 * warps] jdot partials
     double fermi_beta = 0.0, fermi_mu = 0.0;
+    // temporally blocked stencil path: b buffers P2, P3 and the second state buffer
+    void *d_tb = nullptr;                // [3][n_pad] float2
+    int tb_grid = 0;
     int fermi_K = 0;                     // 0: no coefficients cached
     // autotuner: (blocks per SM, ms per middle sweep) of each candidate grid
     bool tuned = false;

@@ -37,6 +37,7 @@ TBPM_F_FORCE_RESCALE = 0x2
 TBPM_F_RENORM = 0x4
 TBPM_F_NO_CLUSTER = 0x8
 TBPM_F_AUTOTUNE = 0x10
+TBPM_F_NO_TBLOCK = 0x20
 TBPM_LATTICE_GRAPHENE = 0
 TBPM_LATTICE_AB_BILAYER = 1
 

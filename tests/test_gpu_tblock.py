@@ -1,0 +1,91 @@
+"""Temporally blocked sweeps on the FP32 monolayer stencil (several Chebyshev
+terms per pass over a lattice tile held in shared memory) against the FP64
+oracle and against the one-launch-per-sweep FP32 path.
+
+The FP32 bars are those of test_gpu_fp32.py: |dC| <= 3e-5 over up to 1024
+steps (a random walk of 2^-24 roundings over 17 sweeps per step) and a DOS L1
+relative error <= 1e-4; blocked and per-sweep FP32 results differ only by the
+rounding order, well inside that."""
+import math
+
+import numpy as np
+import pytest
+
+import tbpm_inputs as ti
+import paper_2509_26309_gb300 as tb
+
+pytestmark = pytest.mark.gpu
+DT = math.pi / 9
+C_TOL = 3e-5
+
+
+def lattice(l1, l2, w=1.0, seed=1, flags=0):
+    n = 2 * l1 * l2
+    eps = ti.anderson_onsite(n, w, seed)
+    ctx = tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l1, l2, ti.T_GRAPHENE, 0.0, eps, 9.0,
+                                 tb.make_opts(precision=tb.TBPM_FP32, path=tb.TBPM_PATH_STENCIL, flags=flags))
+    return ctx, eps
+
+
+@pytest.mark.parametrize("l1,l2,dt,steps", [
+    (9, 12, DT, 37),            # one tile smaller than the region: the halo wraps the torus
+    (61, 70, DT, 64),           # ragged 2 x 2 tiles
+    (150, 131, DT, 33),         # 3 x 3 tiles, odd step count (chunk copy-back)
+    (64, 64, 0.05, 20),         # K = 4..5: a single block holds every sweep
+    (40, 58, 1e-4, 9),          # K = 3
+    (100, 116, 3.0, 16),        # x = 27: K ~ 45, eight blocks per step
+])
+def test_tblock_matches_oracle(orc, l1, l2, dt, steps):
+    ctx, eps = lattice(l1, l2)
+    h = ti.graphene_csr(l1, l2, onsite=eps)
+    psi0 = ti.random_phase_state(h.n, 5)
+    c = tb.tbpm_dos_corr(ctx, psi0, dt, steps)
+    ref = orc.dos_corr(h, 9.0, psi0, dt, steps)
+    assert np.max(np.abs(c - ref)) <= C_TOL, np.max(np.abs(c - ref))
+    # blocked launches: ceil((K-1)/6) per step instead of K-1
+    info = tb.tbpm_get_info(ctx)
+    K = info["num_terms"]
+    assert info["kernel_launches"] <= 3 + steps * ((K - 2) // 6 + 1) + 2 * ((steps + 15) // 16)
+    # the per-sweep path on the same FP32 inputs differs only by rounding order
+    ctx2, _ = lattice(l1, l2, flags=tb.TBPM_F_NO_TBLOCK)
+    c2 = tb.tbpm_dos_corr(ctx2, psi0, dt, steps)
+    assert np.max(np.abs(c - c2)) <= 2e-6
+
+
+def test_tblock_long_run_dos(orc):
+    l1, l2 = 48, 47
+    ctx, eps = lattice(l1, l2, w=1.0, seed=2)
+    h = ti.graphene_csr(l1, l2, onsite=eps)
+    psi0 = ti.random_phase_state(h.n, 0)
+    c = tb.tbpm_dos_corr(ctx, psi0, DT, 1024)
+    ref = orc.dos_corr(h, 9.0, psi0, DT, 1024)
+    assert np.max(np.abs(c - ref)) <= C_TOL
+    _, d, _ = orc.dos_hann(c, DT)
+    _, dr, _ = orc.dos_hann(ref, DT)
+    assert np.sum(np.abs(d - dr)) / np.sum(np.abs(dr)) <= 1e-4
+    c2 = tb.tbpm_dos_corr(ctx, psi0, DT, 1024)
+    assert np.array_equal(c, c2)                       # fixed tiles and reduction order
+
+
+def test_tblock_final_state(orc):
+    l1, l2 = 70, 61
+    ctx, eps = lattice(l1, l2, seed=3)
+    h = ti.graphene_csr(l1, l2, onsite=eps)
+    psi0 = ti.random_phase_state(h.n, 9)
+    for steps in (7, 16):
+        psi = tb.tbpm_propagate(ctx, psi0, DT, steps)
+        _, _, ref = orc.propagate(h, 9.0, psi0, DT, steps, want_corr=False, want_psi=True)
+        assert np.max(np.abs(np.asarray(psi).reshape(-1) - ref)) <= 1e-5
+
+
+def test_tblock_device_buffers_and_pristine(orc):
+    torch = pytest.importorskip("torch")
+    l1, l2 = 64, 64
+    ctx = tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l1, l2, ti.T_GRAPHENE, 0.0, None, 9.0,
+                                 tb.make_opts(precision=tb.TBPM_FP32, path=tb.TBPM_PATH_STENCIL))
+    h = ti.graphene_csr(l1, l2)
+    psi0 = ti.random_phase_state(h.n, 0)
+    out = torch.empty((1, 129), dtype=torch.complex128, device="cuda")
+    tb.tbpm_dos_corr(ctx, torch.from_numpy(psi0).cuda().reshape(1, -1), DT, 128, out=out)
+    ref = orc.dos_corr(h, 9.0, psi0, DT, 128)
+    assert np.max(np.abs(out[0].cpu().numpy() - ref)) <= C_TOL
