@@ -10,6 +10,7 @@
 // per thread. The sweep kinds and the Clenshaw update are those of
 // cheb_sweep.cu (y = a psi + beta A x - z, with A = 2 H / rescale stored).
 #include "tbpm_internal.cuh"
+#include "sweep_ops.cuh"
 
 namespace tbpm {
 namespace {
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(kBlock) sweep_b16(SweepParams p)
     const float beta0 = (float)(BM == B_ONE ? braw : sc0 * braw);
     const float beta1 = (float)(BM == B_ONE ? braw : sc1 * braw);
     double d0r = 0.0, d0i = 0.0, d1r = 0.0, d1i = 0.0, n0 = 0.0, n1 = 0.0;
+    F2Sum f0r, f0i, f1r, f1i, g0, g1;   // the dots, summed on the FP32 pipe
 
     for (int64_t s = blockIdx.x; s < p.nslices; s += gridDim.x) {
         const int64_t row = s * 32 + r_in;
@@ -200,17 +202,19 @@ __global__ void __launch_bounds__(kBlock) sweep_b16(SweepParams p)
         st4(y, row, pair, out);
         if (FINAL) {
             const C2 q = ld4_plain(psi0, row, pair);
-            d0r = fma((double)q.r0, (double)out.r0, fma((double)q.i0, (double)out.i0, d0r));
-            d0i = fma((double)q.r0, (double)out.i0, fma(-(double)q.i0, (double)out.r0, d0i));
-            d1r = fma((double)q.r1, (double)out.r1, fma((double)q.i1, (double)out.i1, d1r));
-            d1i = fma((double)q.r1, (double)out.i1, fma(-(double)q.i1, (double)out.r1, d1i));
+            f0r.add_prod(q.r0, out.r0); f0r.add_prod(q.i0, out.i0);
+            f0i.add_prod(q.r0, out.i0); f0i.add_prod(-q.i0, out.r0);
+            f1r.add_prod(q.r1, out.r1); f1r.add_prod(q.i1, out.i1);
+            f1i.add_prod(q.r1, out.i1); f1i.add_prod(-q.i1, out.r1);
             if (p.norm_partials) {
-                n0 = fma((double)out.r0, (double)out.r0, fma((double)out.i0, (double)out.i0, n0));
-                n1 = fma((double)out.r1, (double)out.r1, fma((double)out.i1, (double)out.i1, n1));
+                g0.add_prod(out.r0, out.r0); g0.add_prod(out.i0, out.i0);
+                g1.add_prod(out.r1, out.r1); g1.add_prod(out.i1, out.i1);
             }
         }
     }
     if (FINAL) {
+        d0r = f0r.value(); d0i = f0i.value(); d1r = f1r.value(); d1i = f1i.value();
+        n0 = g0.value(); n1 = g1.value();
         block_pairs(d0r, d0i, d1r, d1i, red, p.partials + ((int64_t)p.delta * p.nblk + blockIdx.x) * kB);
         if (p.norm_partials)
             block_pairs(n0, 0.0, n1, 0.0, red,

@@ -76,6 +76,8 @@ __global__ void __launch_bounds__(kBlockB1) sweep_b1(SweepParams p)
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double dr = 0.0, di = 0.0, nn = 0.0;
+    F2Sum fr, fi, fn;                   // FP32 data: the same sums on the FP32 pipe
+    constexpr bool kF32 = sizeof(R) == 4;
 
     for (int64_t s = warp; s < p.nslices; s += nwarps) {
         if (MULTI) sweep_coeffs<R, BM, AIMAG>(p, __ldg(p.slice_inst + s), a, beta);
@@ -102,7 +104,17 @@ __global__ void __launch_bounds__(kBlockB1) sweep_b1(SweepParams p)
         else if (BM == B_REAL) { out.x = fma(beta, ar, tr); out.y = fma(beta, ai, ti); }
         else { out.x = fma(-beta, ai, tr); out.y = fma(beta, ar, ti); }
         y[row] = out;
-        if (FINAL) {
+        if (FINAL && kF32 && !MULTI) {
+            const V q = psi0[row];
+            fr.add_prod((float)q.x, (float)out.x);
+            fr.add_prod((float)q.y, (float)out.y);
+            fi.add_prod((float)q.x, (float)out.y);
+            fi.add_prod(-(float)q.y, (float)out.x);
+            if (p.norm_partials) {
+                fn.add_prod((float)out.x, (float)out.x);
+                fn.add_prod((float)out.y, (float)out.y);
+            }
+        } else if (FINAL) {
             const V q = psi0[row];
             const double qr = (double)q.x, qi = (double)q.y;
             const double orr = (double)out.x, oi = (double)out.y;
@@ -122,6 +134,11 @@ __global__ void __launch_bounds__(kBlockB1) sweep_b1(SweepParams p)
         }
     }
     if (FINAL && !MULTI) {
+        if (kF32) {
+            dr = fr.value();
+            di = fi.value();
+            nn = fn.value();
+        }
         dr = warp_sum(dr);
         di = warp_sum(di);
         if (lane == 0) p.partials[(int64_t)p.delta * nwarps + warp] = make_double2(dr, di);
@@ -150,6 +167,7 @@ __global__ void __launch_bounds__(kBlockB1) kpm_b1(KpmParams p)
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double nn = 0.0, cr = 0.0, ci = 0.0;
+    F2Sum fn, fr, fi;                   // FP32 data: the same sums on the FP32 pipe
     for (int64_t s = warp; s < p.nslices; s += nwarps) {
         const int64_t row = (s << 5) + lane;
         const V xi = __ldg(x + row);
@@ -169,12 +187,26 @@ __global__ void __launch_bounds__(kBlockB1) kpm_b1(KpmParams p)
             out.x = ar; out.y = ai;
         }
         y[row] = out;
-        const double xr = (double)xi.x, xim = (double)xi.y;
-        const double orr = (double)out.x, oi = (double)out.y;
-        nn = fma(xr, xr, fma(xim, xim, nn));
-        // <y|x> = sum conj(y) x
-        cr = fma(orr, xr, fma(oi, xim, cr));
-        ci = fma(orr, xim, fma(-oi, xr, ci));
+        if (sizeof(R) == 4) {
+            fn.add_prod((float)xi.x, (float)xi.x);
+            fn.add_prod((float)xi.y, (float)xi.y);
+            fr.add_prod((float)out.x, (float)xi.x);
+            fr.add_prod((float)out.y, (float)xi.y);
+            fi.add_prod((float)out.x, (float)xi.y);
+            fi.add_prod(-(float)out.y, (float)xi.x);
+        } else {
+            const double xr = (double)xi.x, xim = (double)xi.y;
+            const double orr = (double)out.x, oi = (double)out.y;
+            nn = fma(xr, xr, fma(xim, xim, nn));
+            // <y|x> = sum conj(y) x
+            cr = fma(orr, xr, fma(oi, xim, cr));
+            ci = fma(orr, xim, fma(-oi, xr, ci));
+        }
+    }
+    if (sizeof(R) == 4) {
+        nn = fn.value();
+        cr = fr.value();
+        ci = fi.value();
     }
     nn = warp_sum(nn);
     cr = warp_sum(cr);

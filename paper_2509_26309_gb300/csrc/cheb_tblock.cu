@@ -70,25 +70,6 @@ __device__ __forceinline__ void cp_async(void *dst, const void *src, int bytes)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// (hi, lo) += v, Knuth's two-sum: hi + lo carries the running sum to about
-// twice FP32's precision using only FP32 additions.
-__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v)
-{
-    const float s = __fadd_rn(hi, v);
-    const float bb = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
-    hi = s;
-    lo = __fadd_rn(lo, err);
-}
-// (hi, lo) += a b, with the product split exactly as p + e (e = fma(a, b, -p)).
-__device__ __forceinline__ void two_prod_add(float &hi, float &lo, float a, float b)
-{
-    const float pr = __fmul_rn(a, b);
-    const float e = fmaf(a, b, -pr);
-    two_sum_add(hi, lo, pr);
-    lo = __fadd_rn(lo, e);
-}
-
 // Staging slots of item r for this thread: psi, b_{k+1}, b_{k+2} (float2) and on-site (float).
 struct Stage {
     float2 *ps, *bx, *bz;
@@ -179,8 +160,8 @@ __global__ void __launch_bounds__(kTbThreads, 1) tb_block_kernel(TbParams p)
         cf[threadIdx.x][3] = bi;
         cf[threadIdx.x][4] = (!is_first && !is_second && !(is_final && K == 3)) ? 1.0f : 0.0f;
     }
-    // <psi0|psi> of this thread's interior cells, all tiles, as two-sum pairs
-    float shr = 0.0f, slr = 0.0f, shi = 0.0f, sli = 0.0f;
+    // <psi0|psi> of this thread's interior cells, all tiles, on the FP32 pipe
+    F2Sum sr, si;
 
     float2 ps[kTbItems], xo[kTbItems], zo[kTbItems];
     float on[kTbItems];
@@ -244,10 +225,10 @@ __global__ void __launch_bounds__(kTbThreads, 1) tb_block_kernel(TbParams p)
                 __stcs(p.psi_out + row, xo[r]);
                 const float2 q0 = __ldcs(p.psi0 + row);
                 // conj(q0) y = (q0.x y.x + q0.y y.y) + i (q0.x y.y - q0.y y.x), products exact
-                two_prod_add(shr, slr, q0.x, xo[r].x);
-                two_prod_add(shr, slr, q0.y, xo[r].y);
-                two_prod_add(shi, sli, q0.x, xo[r].y);
-                two_prod_add(shi, sli, -q0.y, xo[r].x);
+                sr.add_prod(q0.x, xo[r].x);
+                sr.add_prod(q0.y, xo[r].y);
+                si.add_prod(q0.x, xo[r].y);
+                si.add_prod(-q0.y, xo[r].x);
             } else {
                 __stcs(p.ox + row, xo[r]);
                 __stcs(p.oz + row, zo[r]);
@@ -255,8 +236,8 @@ __global__ void __launch_bounds__(kTbThreads, 1) tb_block_kernel(TbParams p)
         }
     }
     if (final) {
-        const double dr = warp_sum((double)shr + (double)slr);
-        const double di = warp_sum((double)shi + (double)sli);
+        const double dr = warp_sum(sr.value());
+        const double di = warp_sum(si.value());
         if (lane == 0)
             p.partials[(int64_t)p.delta * gridDim.x * kTbWarps + blockIdx.x * kTbWarps + warp] =
                 make_double2(dr, di);

@@ -124,6 +124,33 @@ __device__ __forceinline__ void stencil_apply(const SweepParams &p, int64_t row,
     }
 }
 
+// Sums of FP32 products at about twice FP32's precision on the FP32 pipe:
+// GB300 issues FP64 at a small fraction of its FP32 rate, so the FP32 kernels
+// do not convert every element to FP64 for their dots. Each product a b is
+// split exactly into p + e (p = a b rounded, e = fma(a, b, -p)), p is added to
+// the running (hi, lo) pair by Knuth's two-sum and e to lo; the pair is
+// converted to FP64 once, when the partial leaves the thread. The _rn
+// intrinsics keep the compiler from contracting or reordering the steps.
+struct F2Sum {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float s = __fadd_rn(hi, v);
+        const float bb = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+        hi = s;
+        lo = __fadd_rn(lo, err);
+    }
+    __device__ __forceinline__ void add_prod(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);
+        add(p);
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Warp-wide sum in a fixed butterfly order; every lane gets the result.
 __device__ __forceinline__ double warp_sum(double v)
 {
