@@ -89,29 +89,19 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // kind: 0 FIRST (x = psi, y = b_{K-2}), 1 SECOND, 2 MID, 3 FINAL
 template <typename R, bool REALV, bool SMAT>
-__device__ void cluster_sweep(const ClusterParams &p, const MatView &mv, cg::cluster_group &cl, int kind, int k,
-                              typename V2<R>::T *xs, typename V2<R>::T *psi, typename V2<R>::T *y,
+__device__ void cluster_sweep(const ClusterParams &p, const MatView &mv, cg::cluster_group &cl, const R *tab,
+                              int kind, int k, typename V2<R>::T *xs, typename V2<R>::T *psi, typename V2<R>::T *y,
                               const typename V2<R>::T *z, int step)
 {
     typedef typename V2<R>::T V;
     const int K = p.K;
-    // a on psi and beta on A x, as in cheb_sweep.cu (c_k real for even k)
-    double2 ca, cb = make_double2(0.0, 0.0);
-    double bs = 1.0;
-    bool bimag = false, breal = false;
-    if (kind == 0) { ca = p.coef[K - 2]; breal = true; }
-    else if (kind == 1) { ca = p.coef[K - 3]; cb = p.coef[K - 1]; }
-    else if (kind == 2) { ca = p.coef[k]; }
-    else { ca = p.coef[0]; if (K == 3) cb = p.coef[2]; bs = 0.5; }
+    // a on psi and beta on A x, as in cheb_sweep.cu (c_k real for even k), from
+    // the table the kernel formed once (no FP64 arithmetic per sweep)
     const int ka = kind == 0 ? K - 2 : kind == 1 ? K - 3 : kind == 2 ? k : 0;
     const bool aimag = (ka & 1) != 0;
-    const R a = (R)(aimag ? (ca.y - cb.y) : (ca.x - cb.x));
-    R beta = (R)bs;
-    if (kind == 0) {
-        const double2 cc = p.coef[K - 1];
-        bimag = ((K - 1) & 1) != 0;
-        beta = (R)(bimag ? cc.y : cc.x);
-    }
+    const R a = tab[ka];
+    const bool bimag = kind == 0 && ((K - 1) & 1) != 0;
+    const R beta = kind == 0 ? tab[K - 1] : kind == 3 ? (R)0.5 : (R)1;
     const bool fold = (kind == 1 || kind == 2);          // beta = 1: acc starts at t
     const unsigned rank = cl.block_rank();
     const int rows = 1 << p.log_rows;
@@ -208,22 +198,39 @@ __global__ void __launch_bounds__(1024) cluster_dos_kernel(ClusterParams p)
         b0[i] = v;                      // defined values for rows never written
         b1[i] = v;
     }
+    // per-term coefficient table: tab[k] = a of the sweep producing term k (the
+    // part of c_k that is nonzero, minus c_{K-1} for the second sweep and c_2 for
+    // the final one at K = 3), tab[K-1] = beta of the first sweep
+    __shared__ R tab[kMaxTerms];
+    {
+        const int K = p.K;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            double v;
+            if (k == K - 1) v = ((K - 1) & 1) ? p.coef[K - 1].y : p.coef[K - 1].x;
+            else {
+                v = (k & 1) ? p.coef[k].y : p.coef[k].x;
+                if (k == K - 3 && K >= 4) v -= (k & 1) ? p.coef[K - 1].y : p.coef[K - 1].x;
+                if (k == 0 && K == 3) v -= p.coef[2].x;
+            }
+            tab[k] = (R)v;
+        }
+    }
     cl.sync();
     const int K = p.K;
     V *B[2] = {b0, b1};
     for (int step = 0; step < p.n_steps; ++step) {
-        cluster_sweep<R, REALV, SMAT>(p, mv, cl, 0, K - 2, psi, psi, B[0], nullptr, step);
+        cluster_sweep<R, REALV, SMAT>(p, mv, cl, tab, 0, K - 2, psi, psi, B[0], nullptr, step);
         cl.sync();
         if (K >= 4) {
-            cluster_sweep<R, REALV, SMAT>(p, mv, cl, 1, K - 3, B[0], psi, B[1], nullptr, step);
+            cluster_sweep<R, REALV, SMAT>(p, mv, cl, tab, 1, K - 3, B[0], psi, B[1], nullptr, step);
             cl.sync();
         }
         for (int k = K - 4; k >= 1; --k) {
             V *yk = B[(K - 2 - k) & 1];
-            cluster_sweep<R, REALV, SMAT>(p, mv, cl, 2, k, B[(K - 3 - k) & 1], psi, yk, yk, step);
+            cluster_sweep<R, REALV, SMAT>(p, mv, cl, tab, 2, k, B[(K - 3 - k) & 1], psi, yk, yk, step);
             cl.sync();
         }
-        cluster_sweep<R, REALV, SMAT>(p, mv, cl, 3, 0, B[(K - 3) & 1], psi, psi, K >= 4 ? B[(K - 4) & 1] : nullptr,
+        cluster_sweep<R, REALV, SMAT>(p, mv, cl, tab, 3, 0, B[(K - 3) & 1], psi, psi, K >= 4 ? B[(K - 4) & 1] : nullptr,
                                       step);
         cl.sync();
     }

@@ -34,19 +34,27 @@ enum BMode { B_ONE = 0, B_REAL = 1, B_IMAG = 2 };
 // Coefficients of one sweep: a on psi (real, or imaginary if AIMAG), beta on A x.
 // For a batch of instances, coefficients and the renormalisation scale are
 // those of the slice's instance.
+// Only the FP64 operations a sweep needs are issued (each one costs every
+// thread of the grid a slot of GB300's narrow FP64 pipe): the difference for
+// the second sweep, the scale only when renormalising, bscale only when not 1.
 template <typename R, int BM, bool AIMAG>
 __device__ __forceinline__ void sweep_coeffs(const SweepParams &p, int inst, R &a, R &beta)
 {
     const double2 *c = p.coef + (int64_t)inst * kMaxTerms;
     const double2 ca = c[p.ia];
-    const double2 cb = p.ib >= 0 ? c[p.ib] : make_double2(0.0, 0.0);
+    double av = AIMAG ? ca.y : ca.x;
+    if (p.ib >= 0) av -= AIMAG ? c[p.ib].y : c[p.ib].x;
     // renormalisation folds 1/||psi|| into the coefficients that multiply psi
     // (in the first sweep also into beta, whose operand is psi itself)
-    const double sc = p.scale ? p.scale[inst] : 1.0;
-    a = (R)(sc * (AIMAG ? (ca.y - cb.y) : (ca.x - cb.x)));
+    if (p.scale) av *= p.scale[inst];
+    a = (R)av;
     beta = (R)p.bscale;
-    if (BM == B_REAL && p.ic >= 0) beta = (R)(sc * p.bscale * c[p.ic].x);
-    if (BM == B_IMAG && p.ic >= 0) beta = (R)(sc * p.bscale * c[p.ic].y);
+    if (BM != B_ONE && p.ic >= 0) {
+        double bv = BM == B_REAL ? c[p.ic].x : c[p.ic].y;
+        if (p.bscale != 1.0) bv *= p.bscale;
+        if (p.scale) bv *= p.scale[inst];
+        beta = (R)bv;
+    }
 }
 
 // One Clenshaw sweep for a single state per row (B = 1). A warp owns one
@@ -79,8 +87,15 @@ __global__ void __launch_bounds__(kBlockB1) sweep_b1(SweepParams p)
     F2Sum fr, fi, fn;                   // FP32 data: the same sums on the FP32 pipe
     constexpr bool kF32 = sizeof(R) == 4;
 
+    int cur_inst = 0;                   // instance whose coefficients a, beta hold
     for (int64_t s = warp; s < p.nslices; s += nwarps) {
-        if (MULTI) sweep_coeffs<R, BM, AIMAG>(p, __ldg(p.slice_inst + s), a, beta);
+        if (MULTI) {                    // instances span many slices: recompute on a change only
+            const int g = __ldg(p.slice_inst + s);
+            if (g != cur_inst) {
+                sweep_coeffs<R, BM, AIMAG>(p, g, a, beta);
+                cur_inst = g;
+            }
+        }
         const int64_t row = (s << 5) + lane;
         const V ps = psi[row];
         // t = a psi - z  (a real: a*psi; a imaginary: i*a*psi), one FMA per part

@@ -98,6 +98,44 @@ __device__ __forceinline__ void prefetch_tile(const TbParams &p, const Stage &st
     cp_async_commit();
 }
 
+// One sweep over this thread's kTbItems cells. x holds each cell's b_{k+1}
+// (own value; the neighbours' come from shared memory xb), z its b_{k+2} on
+// entry and the new b_k on exit (written to yb as well). FORM 0: a middle
+// sweep with c_k real (out = a psi - z + A x); FORM 1: c_k imaginary
+// (i a psi); FORM 2: the general form
+//   out = alpha psi - hz z + beta (d x + t sum of the neighbours).
+template <int FORM>
+__device__ __forceinline__ void tb_items(const float2 *xb, float2 *yb, int own0, int oth0, int d1, int d2,
+                                         const float2 (&ps)[kTbItems], const float (&on)[kTbItems],
+                                         const float2 (&x)[kTbItems], float2 (&z)[kTbItems], float t,
+                                         const float *c)
+{
+#pragma unroll
+    for (int r = 0; r < kTbItems; ++r) {
+        const int oth = oth0 + 16 * kTbWarps * r;
+        const float2 x0 = xb[oth], x1 = xb[oth + d1], x2 = xb[oth + d2];
+        const float2 xi = x[r], pv = ps[r], zz = z[r];
+        const float sr = x0.x + x1.x + x2.x, si = x0.y + x1.y + x2.y;
+        float2 out;
+        if (FORM == 0) {
+            out.x = fmaf(t, sr, fmaf(on[r], xi.x, fmaf(c[0], pv.x, -zz.x)));
+            out.y = fmaf(t, si, fmaf(on[r], xi.y, fmaf(c[0], pv.y, -zz.y)));
+        } else if (FORM == 1) {
+            out.x = fmaf(t, sr, fmaf(on[r], xi.x, fmaf(-c[1], pv.y, -zz.x)));
+            out.y = fmaf(t, si, fmaf(on[r], xi.y, fmaf(c[1], pv.x, -zz.y)));
+        } else {
+            const float tr = fmaf(-c[4], zz.x, fmaf(c[0], pv.x, -c[1] * pv.y));
+            const float ti = fmaf(-c[4], zz.y, fmaf(c[0], pv.y, c[1] * pv.x));
+            const float hr = fmaf(t, sr, on[r] * xi.x);
+            const float hi = fmaf(t, si, on[r] * xi.y);
+            out.x = fmaf(c[2], hr, fmaf(-c[3], hi, tr));
+            out.y = fmaf(c[2], hi, fmaf(c[3], hr, ti));
+        }
+        yb[own0 + 16 * kTbWarps * r] = out;
+        z[r] = out;
+    }
+}
+
 __global__ void __launch_bounds__(kTbThreads, 1) tb_block_kernel(TbParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -105,6 +143,7 @@ __global__ void __launch_bounds__(kTbThreads, 1) tb_block_kernel(TbParams p)
     // Formed once per block from the FP64 series: on GB300 an FP64 operation costs
     // as much issue time as a few dozen FP32 ones, so no thread repeats this per tile.
     __shared__ float cf[kTbS][5];
+    __shared__ int cform[kTbS];
     float2 *X[2] = {reinterpret_cast<float2 *>(smem), reinterpret_cast<float2 *>(smem) + 2 * kTbPlane};
     Stage st;
     {
@@ -159,6 +198,7 @@ __global__ void __launch_bounds__(kTbThreads, 1) tb_block_kernel(TbParams p)
         cf[threadIdx.x][2] = br;
         cf[threadIdx.x][3] = bi;
         cf[threadIdx.x][4] = (!is_first && !is_second && !(is_final && K == 3)) ? 1.0f : 0.0f;
+        cform[threadIdx.x] = (is_first || is_second || is_final) ? 2 : (k & 1);
     }
     // <psi0|psi> of this thread's interior cells, all tiles, on the FP32 pipe
     F2Sum sr, si;
@@ -188,30 +228,26 @@ __global__ void __launch_bounds__(kTbThreads, 1) tb_block_kernel(TbParams p)
         // the staging slots are free again: fetch the next tile during the sweeps
         if (tile + (int)gridDim.x < ntiles) prefetch_tile(p, st, tile + gridDim.x, warp, sl, cl, first);
         __syncthreads();
-        int cur = 0;
+        // the register arrays trade roles each sweep: even sweeps read b_{k+1} from
+        // xo and overwrite zo with b_k, odd sweeps the reverse
         for (int q = 0; q < p.S; ++q) {
-            const float ar_ = cf[q][0], ai_ = cf[q][1], br_ = cf[q][2], bi_ = cf[q][3], hz = cf[q][4];
-            const float2 *xb = X[cur];
-            float2 *yb = X[cur ^ 1];
-#pragma unroll
-            for (int r = 0; r < kTbItems; ++r) {
-                const int oth = oth0 + 16 * kTbWarps * r;
-                const float2 x0 = xb[oth], x1 = xb[oth + d1], x2 = xb[oth + d2];
-                const float2 xi = xo[r], pv = ps[r];
-                const float tr = fmaf(-hz, zo[r].x, fmaf(ar_, pv.x, -ai_ * pv.y));
-                const float ti = fmaf(-hz, zo[r].y, fmaf(ar_, pv.y, ai_ * pv.x));
-                const float hr = fmaf(t, x0.x + x1.x + x2.x, on[r] * xi.x);
-                const float hi = fmaf(t, x0.y + x1.y + x2.y, on[r] * xi.y);
-                float2 out;
-                out.x = fmaf(br_, hr, fmaf(-bi_, hi, tr));
-                out.y = fmaf(br_, hi, fmaf(bi_, hr, ti));
-                yb[own0 + 16 * kTbWarps * r] = out;
-                zo[r] = xi;
-                xo[r] = out;
+            const float *c = cf[q];
+            const int form = cform[q];
+            const float2 *xb = X[q & 1];
+            float2 *yb = X[(q & 1) ^ 1];
+            if ((q & 1) == 0) {
+                if (form == 0) tb_items<0>(xb, yb, own0, oth0, d1, d2, ps, on, xo, zo, t, c);
+                else if (form == 1) tb_items<1>(xb, yb, own0, oth0, d1, d2, ps, on, xo, zo, t, c);
+                else tb_items<2>(xb, yb, own0, oth0, d1, d2, ps, on, xo, zo, t, c);
+            } else {
+                if (form == 0) tb_items<0>(xb, yb, own0, oth0, d1, d2, ps, on, zo, xo, t, c);
+                else if (form == 1) tb_items<1>(xb, yb, own0, oth0, d1, d2, ps, on, zo, xo, t, c);
+                else tb_items<2>(xb, yb, own0, oth0, d1, d2, ps, on, zo, xo, t, c);
             }
             __syncthreads();
-            cur ^= 1;
         }
+        // newest b (or psi(t_{n+1})) in zo after an odd number of sweeps, else in xo
+        const bool odd = (p.S & 1) != 0;
         // interior: cells [kTbH, kTbH + T) of the region that lie on the lattice
 #pragma unroll
         for (int r = 0; r < kTbItems; ++r) {
@@ -221,17 +257,18 @@ __global__ void __launch_bounds__(kTbThreads, 1) tb_block_kernel(TbParams p)
             const int m1 = o1 + c1, m2 = o2 + c2;
             if (m1 >= p.L1 || m2 >= p.L2) continue;
             const int row = 2 * (m1 * p.L2 + m2) + sl;
+            const float2 yn = odd ? zo[r] : xo[r], yp = odd ? xo[r] : zo[r];
             if (final) {
-                __stcs(p.psi_out + row, xo[r]);
+                __stcs(p.psi_out + row, yn);
                 const float2 q0 = __ldcs(p.psi0 + row);
                 // conj(q0) y = (q0.x y.x + q0.y y.y) + i (q0.x y.y - q0.y y.x), products exact
-                sr.add_prod(q0.x, xo[r].x);
-                sr.add_prod(q0.y, xo[r].y);
-                si.add_prod(q0.x, xo[r].y);
-                si.add_prod(-q0.y, xo[r].x);
+                sr.add_prod(q0.x, yn.x);
+                sr.add_prod(q0.y, yn.y);
+                si.add_prod(q0.x, yn.y);
+                si.add_prod(-q0.y, yn.x);
             } else {
-                __stcs(p.ox + row, xo[r]);
-                __stcs(p.oz + row, zo[r]);
+                __stcs(p.ox + row, yn);
+                __stcs(p.oz + row, yp);
             }
         }
     }
