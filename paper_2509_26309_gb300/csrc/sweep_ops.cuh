@@ -22,60 +22,83 @@ __device__ __forceinline__ T ldm(const T *p)
     return __ldg(p);
 }
 
+// One stored entry: acc += v x[c] (real v) or v x[c] (complex v).
+template <typename R, bool REALV>
+struct SellEntry;
+template <typename R>
+struct SellEntry<R, true> {
+    typedef typename V2<R>::T V;
+    int c;
+    R v;
+    __device__ __forceinline__ void load(const int32_t *cp, const void *vp, int64_t e)
+    {
+        c = ldm<R>(cp + e);
+        v = ldm<R>(reinterpret_cast<const R *>(vp) + e);
+    }
+    __device__ __forceinline__ void apply(const V &xv, R &ar, R &ai) const
+    {
+        ar = fma(v, xv.x, ar);
+        ai = fma(v, xv.y, ai);
+    }
+};
+template <typename R>
+struct SellEntry<R, false> {
+    typedef typename V2<R>::T V;
+    int c;
+    V v;
+    __device__ __forceinline__ void load(const int32_t *cp, const void *vp, int64_t e)
+    {
+        c = ldm<R>(cp + e);
+        v = ldm<R>(reinterpret_cast<const V *>(vp) + e);
+    }
+    __device__ __forceinline__ void apply(const V &xv, R &ar, R &ai) const
+    {
+        ar = fma(v.x, xv.x, fma(-v.y, xv.y, ar));
+        ai = fma(v.x, xv.y, fma(v.y, xv.x, ai));
+    }
+};
+
+// N entries j0 .. j0+N-1 of the lane's row: all loads first, then the FMAs.
+template <typename R, bool REALV, int N>
+__device__ __forceinline__ void sell_entries(const int32_t *cp, const void *vp, int j0,
+                                             const typename V2<R>::T *__restrict__ x, R &ar, R &ai)
+{
+    typedef typename V2<R>::T V;
+    SellEntry<R, REALV> e[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) e[q].load(cp, vp, 32 * (int64_t)(j0 + q));
+    V xv[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) xv[q] = __ldg(x + e[q].c);
+#pragma unroll
+    for (int q = 0; q < N; ++q) e[q].apply(xv[q], ar, ai);
+}
+
 // acc = A x for row `row` of a SELL slice, accumulated onto (ar, ai).
+// The slice width w is uniform across the warp. Widths 3 and 4 (monolayer and
+// AB-bilayer rows with the diagonal stored apart) run as straight-line code;
+// other widths as groups of 4 and a plain remainder loop. No code path issues
+// instructions for entries past w: a predicated-off FP64 instruction still
+// takes its slot in GB300's narrow FP64 pipe.
 template <typename R, bool REALV>
 __device__ __forceinline__ void sell_apply(const SweepParams &p, int64_t s, int lane,
                                            const typename V2<R>::T *__restrict__ x,
                                            R &ar, R &ai)
 {
-    typedef typename V2<R>::T V;
     const int64_t off = ldm<R>(p.slice_off + s);
     const int w = (int)((ldm<R>(p.slice_off + s + 1) - off) >> 5);
     const int32_t *cp = p.cols + off + lane;
-    if (REALV) {
-        const R *vp = reinterpret_cast<const R *>(p.vals) + off + lane;
-        int j = 0;
-        for (; j + 4 <= w; j += 4) {
-            int c0 = ldm<R>(cp + 32 * j), c1 = ldm<R>(cp + 32 * (j + 1));
-            int c2 = ldm<R>(cp + 32 * (j + 2)), c3 = ldm<R>(cp + 32 * (j + 3));
-            R v0 = ldm<R>(vp + 32 * j), v1 = ldm<R>(vp + 32 * (j + 1));
-            R v2 = ldm<R>(vp + 32 * (j + 2)), v3 = ldm<R>(vp + 32 * (j + 3));
-            V x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
-            ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
-            ar = fma(v1, x1.x, ar); ai = fma(v1, x1.y, ai);
-            ar = fma(v2, x2.x, ar); ai = fma(v2, x2.y, ai);
-            ar = fma(v3, x3.x, ar); ai = fma(v3, x3.y, ai);
-        }
-        if (j + 2 <= w) {
-            int c0 = ldm<R>(cp + 32 * j), c1 = ldm<R>(cp + 32 * (j + 1));
-            R v0 = ldm<R>(vp + 32 * j), v1 = ldm<R>(vp + 32 * (j + 1));
-            V x0 = __ldg(x + c0), x1 = __ldg(x + c1);
-            ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
-            ar = fma(v1, x1.x, ar); ai = fma(v1, x1.y, ai);
-            j += 2;
-        }
-        if (j < w) {
-            int c0 = ldm<R>(cp + 32 * j);
-            R v0 = ldm<R>(vp + 32 * j);
-            V x0 = __ldg(x + c0);
-            ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
-        }
+    const void *vp = REALV ? (const void *)(reinterpret_cast<const R *>(p.vals) + off + lane)
+                           : (const void *)(reinterpret_cast<const typename V2<R>::T *>(p.vals) + off + lane);
+    if (w == 3) {
+        sell_entries<R, REALV, 3>(cp, vp, 0, x, ar, ai);
+    } else if (w == 4) {
+        sell_entries<R, REALV, 4>(cp, vp, 0, x, ar, ai);
     } else {
-        const V *vp = reinterpret_cast<const V *>(p.vals) + off + lane;
         int j = 0;
-        for (; j + 2 <= w; j += 2) {
-            int c0 = ldm<R>(cp + 32 * j), c1 = ldm<R>(cp + 32 * (j + 1));
-            V v0 = ldm<R>(vp + 32 * j), v1 = ldm<R>(vp + 32 * (j + 1));
-            V x0 = __ldg(x + c0), x1 = __ldg(x + c1);
-            ar = fma(v0.x, x0.x, fma(-v0.y, x0.y, ar)); ai = fma(v0.x, x0.y, fma(v0.y, x0.x, ai));
-            ar = fma(v1.x, x1.x, fma(-v1.y, x1.y, ar)); ai = fma(v1.x, x1.y, fma(v1.y, x1.x, ai));
-        }
-        if (j < w) {
-            int c0 = ldm<R>(cp + 32 * j);
-            V v0 = ldm<R>(vp + 32 * j);
-            V x0 = __ldg(x + c0);
-            ar = fma(v0.x, x0.x, fma(-v0.y, x0.y, ar)); ai = fma(v0.x, x0.y, fma(v0.y, x0.x, ai));
-        }
+        for (; j + 4 <= w; j += 4) sell_entries<R, REALV, 4>(cp, vp, j, x, ar, ai);
+#pragma unroll 1
+        for (; j < w; ++j) sell_entries<R, REALV, 1>(cp, vp, j, x, ar, ai);
     }
 }
 
