@@ -439,10 +439,14 @@ def run_variants(args, dev, stream):
     o16 = torch.empty((16, steps + 1), dtype=torch.complex128, device=dev)
     o1 = torch.empty((1, steps + 1), dtype=torch.complex128, device=dev)
     ref4 = None
-    for path in ("stencil", "sell"):
-        if path == "stencil":
-            mk = lambda prec: tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l4, l4, ti.T_GRAPHENE, 0.0, eps,
-                                                     RESCALE, tb.make_opts(precision=prec, stream=so))
+    for path in ("stencil", "stencil_spmm", "sell"):
+        if path.startswith("stencil"):
+            # "stencil": the default path (FP32 monolayer: one temporally blocked run
+            # per state); "stencil_spmm": 16 states per sweep (TBPM_F_NO_TBLOCK)
+            fl = tb.TBPM_F_NO_TBLOCK if path == "stencil_spmm" else 0
+            mk = lambda prec, fl=fl: tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l4, l4, ti.T_GRAPHENE, 0.0,
+                                                            eps, RESCALE,
+                                                            tb.make_opts(precision=prec, flags=fl, stream=so))
         else:
             h4 = ti.graphene_csr(l4, l4, onsite=eps)
             mk = lambda prec: tb.tbpm_create(n4, h4.row_ptr, h4.col, h4.val, RESCALE,

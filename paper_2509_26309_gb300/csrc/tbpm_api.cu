@@ -1056,7 +1056,10 @@ static int run_dos(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, in
     const int Ke = std::max(K, 3);
     const int64_t n = ctx->n;
     int64_t launches = 0;
-    if (ctx->precision == TBPM_FP32 && nstates > 1) {
+    // FP32 with several states: blocks of 16 states per sweep, except on the
+    // monolayer stencil, where there is no stored matrix to share and the
+    // temporally blocked single-state kernel runs the states one after another
+    if (ctx->precision == TBPM_FP32 && nstates > 1 && !use_tblock(ctx)) {
         // blocks of 16 states advance together; missing states of the last
         // block are zero vectors, which stay zero
         const int B = kMaxBlockStates;

@@ -65,8 +65,12 @@ def test_fp32_batched_complex_ragged(orc):
         assert np.max(np.abs(c[j] - ref)) <= C_TOL
 
 
-@pytest.mark.parametrize("kind", [tb.TBPM_LATTICE_GRAPHENE, tb.TBPM_LATTICE_AB_BILAYER])
-def test_fp32_batched_stencil(orc, kind):
+@pytest.mark.parametrize("kind,flags", [(tb.TBPM_LATTICE_GRAPHENE, 0),
+                                        (tb.TBPM_LATTICE_GRAPHENE, tb.TBPM_F_NO_TBLOCK),
+                                        (tb.TBPM_LATTICE_AB_BILAYER, 0)])
+def test_fp32_batched_stencil(orc, kind, flags):
+    """16 states on the stencil: the 16-state sweeps (bilayer, or with
+    TBPM_F_NO_TBLOCK) or one temporally blocked run per state (monolayer)."""
     l1, l2 = 21, 19
     per = 2 if kind == 0 else 4
     n = per * l1 * l2
@@ -74,21 +78,22 @@ def test_fp32_batched_stencil(orc, kind):
     h = ti.graphene_csr(l1, l2, onsite=eps) if kind == 0 else ti.bilayer_csr(l1, l2, onsite=eps)
     rescale = max(9.0, 1.02 * ti.gershgorin_bound(h))
     psi = ti.random_phase_block(n, 16, seed0=0).T.copy()
-    ctx = tb.tbpm_create_lattice(kind, l1, l2, -2.7, 0.39, eps, rescale, tb.make_opts(precision=tb.TBPM_FP32))
+    ctx = tb.tbpm_create_lattice(kind, l1, l2, -2.7, 0.39, eps, rescale,
+                                 tb.make_opts(precision=tb.TBPM_FP32, flags=flags))
     c = tb.tbpm_dos_corr(ctx, psi, math.pi / rescale, 200)
     for j in (0, 9):
         ref = orc.dos_corr(h, rescale, psi[j], math.pi / rescale, 200)
         assert np.max(np.abs(c[j] - ref)) <= C_TOL
 
 
-@pytest.mark.parametrize("stencil", [False, True])
-def test_fp32_batched_large(orc, stencil):
+@pytest.mark.parametrize("stencil,flags", [(False, 0), (True, 0), (True, tb.TBPM_F_NO_TBLOCK)])
+def test_fp32_batched_large(orc, stencil, flags):
     """16 states on 512x512 graphene (N = 524,288; 268 MB of state vectors, beyond L2)."""
     l = 512
     n = 2 * l * l
     eps = ti.anderson_onsite(n, 1.0, 1)
     h = ti.graphene_csr(l, l, onsite=eps)
-    opts = tb.make_opts(precision=tb.TBPM_FP32)
+    opts = tb.make_opts(precision=tb.TBPM_FP32, flags=flags)
     ctx = (tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l, l, -2.7, 0.0, eps, 9.0, opts) if stencil
            else tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, 9.0, opts))
     psi = np.stack([ti.random_phase_state(n, j) for j in range(16)])
