@@ -89,3 +89,15 @@ def test_tblock_device_buffers_and_pristine(orc):
     tb.tbpm_dos_corr(ctx, torch.from_numpy(psi0).cuda().reshape(1, -1), DT, 128, out=out)
     ref = orc.dos_corr(h, 9.0, psi0, DT, 128)
     assert np.max(np.abs(out[0].cpu().numpy() - ref)) <= C_TOL
+
+
+def test_tblock_large(orc):
+    """2048 x 2048 cells (N = 8,388,608; the state vectors exceed L2): six steps
+    against the oracle."""
+    l = 2048
+    ctx, eps = lattice(l, l, seed=4)
+    h = ti.graphene_csr(l, l, onsite=eps)
+    psi0 = ti.random_phase_state(h.n, 0)
+    c = tb.tbpm_dos_corr(ctx, psi0, DT, 6)
+    ref = orc.dos_corr(h, 9.0, psi0, DT, 6)
+    assert np.max(np.abs(c - ref)) <= C_TOL
