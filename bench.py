@@ -349,8 +349,8 @@ def run_variants(args, dev, stream):
         W = 1 (N = 33,554,432, the paper's benchmark lattice), stencil and
         stored-matrix paths, 32 steps each (the speedup is a throughput ratio,
         so the step count only sets the sample length); DOS L1 of state 0;
-      - FP32 single state on that stencil, temporally blocked vs one launch per
-        sweep;
+      - FP32 single state on that stencil and on an AB-bilayer stencil of as many
+        orbitals, temporally blocked vs one launch per sweep;
       - the AC current correlation on graphene 1024x1024 (W = 1) at 300 K.
     The FP64 runs the errors are taken against are the path the parity tests
     hold to 1e-10 of the oracle."""
@@ -489,6 +489,22 @@ def run_variants(args, dev, stream):
         tb.tbpm_destroy(c1s)
     res["fp32_tblock_speedup_vs_per_sweep"] = (res["fp32_x1_stencil_tblock_4096x4096"]["value"] /
                                                res["fp32_x1_stencil_per_sweep_4096x4096"]["value"])
+    # the same on the AB-bilayer stencil with as many orbitals (2896 x 2896 cells, 4 per cell)
+    lb = 2896
+    nb = 4 * lb * lb
+    epsb = ti.anderson_onsite(nb, W_DISORDER, 1)
+    pb = torch.from_numpy(ti.random_phase_state(nb, 0)).to(dev).reshape(1, nb)
+    for name, flags in (("fp32_x1_bilayer_tblock_2896x2896", 0),
+                        ("fp32_x1_bilayer_per_sweep_2896x2896", tb.TBPM_F_NO_TBLOCK)):
+        cbs = tb.tbpm_create_lattice(tb.TBPM_LATTICE_AB_BILAYER, lb, lb, ti.T_GRAPHENE, ti.T_PERP_AB, epsb, RESCALE,
+                                     tb.make_opts(precision=tb.TBPM_FP32, path=tb.TBPM_PATH_STENCIL, flags=flags,
+                                                  stream=so))
+        msb = timed_calls(lambda: tb.tbpm_dos_corr(cbs, pb, DT, steps, out=o1), 2, stream)
+        K = tb.tbpm_get_info(cbs)["num_terms"]
+        res[name] = {"value": nb * steps * (K - 1) / (msb / 1e3), "unit": UNIT, "ms_per_call": msb, "states": 1,
+                     "n_steps": steps}
+        tb.tbpm_destroy(cbs)
+    del pb
     del blk, one
     # AC conductivity correlation on the config-2 lattice: room temperature,
     # mu = 0, 64 steps; units count the Hamiltonian sweeps (three Fermi series

@@ -644,23 +644,25 @@ int ensure_ac(tbpm_ctx *ctx)
 }
 
 // Whether single-state time steps take the temporally blocked kernel: FP32
-// monolayer stencil without renormalisation, unless TBPM_F_NO_TBLOCK.
+// lattice stencil without renormalisation, unless TBPM_F_NO_TBLOCK.
 bool use_tblock(const tbpm_ctx *ctx)
 {
-    return ctx->op == OP_STENCIL_MONO && ctx->precision == TBPM_FP32 && ctx->ninst == 0 &&
-           !(ctx->flags & (TBPM_F_RENORM | TBPM_F_NO_TBLOCK));
+    return (ctx->op == OP_STENCIL_MONO || ctx->op == OP_STENCIL_BI) && ctx->precision == TBPM_FP32 &&
+           ctx->ninst == 0 && !(ctx->flags & (TBPM_F_RENORM | TBPM_F_NO_TBLOCK));
 }
+
+int tb_per(const tbpm_ctx *ctx) { return ctx->op == OP_STENCIL_MONO ? 2 : 4; }
 
 // The temporally blocked path's extra vectors (two b buffers, a second state).
 int ensure_tb(tbpm_ctx *ctx)
 {
     if (ctx->d_tb) return TBPM_OK;
-    CU(tb_prepare());
+    CU(tb_prepare(tb_per(ctx)));
     const size_t vb = 3 * sizeof(float2) * (size_t)ctx->n_pad;
     CU(cudaMalloc(&ctx->d_tb, vb));
     CU(cudaMemsetAsync(ctx->d_tb, 0, vb, ctx->stream));
     int t1, t2;
-    ctx->tb_grid = std::min(ctx->num_sms, tb_tiles(ctx->sten.l1, ctx->sten.l2, &t1, &t2));
+    ctx->tb_grid = std::min(ctx->num_sms, tb_tiles(tb_per(ctx), ctx->sten.l1, ctx->sten.l2, &t1, &t2));
     return TBPM_OK;
 }
 
@@ -681,8 +683,10 @@ int enqueue_tb_chunk(tbpm_ctx *ctx, int K, int len, cudaStream_t s, int64_t *lau
     memset(&p, 0, sizeof(p));
     p.L1 = (int)ctx->sten.l1;
     p.L2 = (int)ctx->sten.l2;
-    tb_tiles(ctx->sten.l1, ctx->sten.l2, &p.tiles1, &p.tiles2);
+    const int per = tb_per(ctx);
+    tb_tiles(per, ctx->sten.l1, ctx->sten.l2, &p.tiles1, &p.tiles2);
     p.t = (float)ctx->sten.t;
+    p.t_perp = (float)ctx->sten.t_perp;
     p.onsite = static_cast<const float *>(ctx->sten.onsite);
     p.psi0 = static_cast<const float2 *>(ctx->d_psi0);
     p.partials = ctx->d_partials;
@@ -701,13 +705,13 @@ int enqueue_tb_chunk(tbpm_ctx *ctx, int K, int len, cudaStream_t s, int64_t *lau
             p.bz = P[2 * (pair ^ 1) + 1];
             p.ox = P[2 * pair];
             p.oz = P[2 * pair + 1];
-            CU(launch_tb_block(p, grid, s));
+            CU(launch_tb_block(per, p, grid, s));
             ++*launches;
             pair ^= 1;
         }
     }
     if (len & 1) CU(cudaMemcpyAsync(S[0], S[1], vb, cudaMemcpyDeviceToDevice, s));
-    CU(launch_reduce_seg(ctx->d_partials, len, 1, (int64_t)grid * (kTbThreads / 32), nullptr, 1, ctx->d_counter,
+    CU(launch_reduce_seg(ctx->d_partials, len, 1, (int64_t)grid * tb_warps(per), nullptr, 1, ctx->d_counter,
                          1, ctx->d_out, 0, s));
     CU(launch_advance(ctx->d_counter, len, s));
     *launches += 2;

@@ -96,15 +96,15 @@ struct CurrentOp {
 
 constexpr int kFermiCap = TBPM_FERMI_MAX_TERMS;   // Fermi series terms; 2x as many quadrature nodes
 
-// Temporally blocked sweeps on the monolayer stencil, FP32, one state
+// Temporally blocked sweeps on the lattice stencils, FP32, one state
 // (cheb_tblock.cu): one launch runs sweeps [j0, j0 + S) of a time step's
 // K - 1 Clenshaw sweeps (j = 0 first, j = K - 2 final) over lattice tiles.
+// per = orbitals per cell: 2 (monolayer) or 4 (AB bilayer).
 constexpr int kTbS = 6;            // sweeps per block
-constexpr int kTbThreads = 1024;
 struct TbParams {
     int L1, L2;
     int tiles1, tiles2;
-    float t;                       // pre-scaled hopping 2 t / rescale
+    float t, t_perp;               // pre-scaled hoppings 2 t / rescale, 2 t_perp / rescale
     const float *onsite;           // pre-scaled on-site energies, or nullptr
     const float2 *psi;             // psi(t_n)
     const float2 *bx, *bz;         // b_{k+1}, b_{k+2} at the block start (unused for j0 = 0)
@@ -116,11 +116,11 @@ struct TbParams {
     const double2 *coef;
     int K, j0, S;
 };
-size_t tb_smem_bytes();
-int tb_tiles(int64_t l1, int64_t l2, int *tiles1, int *tiles2);
+int tb_warps(int per);             // warps per block (partials per block)
+int tb_tiles(int per, int64_t l1, int64_t l2, int *tiles1, int *tiles2);
 // Opts the kernel in to its shared memory on the current device (before any capture).
-cudaError_t tb_prepare();
-cudaError_t launch_tb_block(const TbParams &p, int grid, cudaStream_t s);
+cudaError_t tb_prepare(int per);
+cudaError_t launch_tb_block(int per, const TbParams &p, int grid, cudaStream_t s);
 
 // KPM sweep: T_{m+1} = 2 H~ T_m - T_{m-1} with <T_m|T_m> and <T_{m+1}|T_m>.
 struct KpmParams {

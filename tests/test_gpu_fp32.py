@@ -67,10 +67,11 @@ def test_fp32_batched_complex_ragged(orc):
 
 @pytest.mark.parametrize("kind,flags", [(tb.TBPM_LATTICE_GRAPHENE, 0),
                                         (tb.TBPM_LATTICE_GRAPHENE, tb.TBPM_F_NO_TBLOCK),
-                                        (tb.TBPM_LATTICE_AB_BILAYER, 0)])
+                                        (tb.TBPM_LATTICE_AB_BILAYER, 0),
+                                        (tb.TBPM_LATTICE_AB_BILAYER, tb.TBPM_F_NO_TBLOCK)])
 def test_fp32_batched_stencil(orc, kind, flags):
-    """16 states on the stencil: the 16-state sweeps (bilayer, or with
-    TBPM_F_NO_TBLOCK) or one temporally blocked run per state (monolayer)."""
+    """16 states on the stencil: one temporally blocked run per state, or the
+    16-state sweeps with TBPM_F_NO_TBLOCK."""
     l1, l2 = 21, 19
     per = 2 if kind == 0 else 4
     n = per * l1 * l2

@@ -19,25 +19,35 @@ DT = math.pi / 9
 C_TOL = 3e-5
 
 
-def lattice(l1, l2, w=1.0, seed=1, flags=0):
-    n = 2 * l1 * l2
+MONO, BI = tb.TBPM_LATTICE_GRAPHENE, tb.TBPM_LATTICE_AB_BILAYER
+
+
+def lattice(l1, l2, w=1.0, seed=1, flags=0, kind=MONO):
+    n = (2 if kind == MONO else 4) * l1 * l2
     eps = ti.anderson_onsite(n, w, seed)
-    ctx = tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l1, l2, ti.T_GRAPHENE, 0.0, eps, 9.0,
+    ctx = tb.tbpm_create_lattice(kind, l1, l2, ti.T_GRAPHENE, ti.T_PERP_AB if kind == BI else 0.0, eps, 9.0,
                                  tb.make_opts(precision=tb.TBPM_FP32, path=tb.TBPM_PATH_STENCIL, flags=flags))
     return ctx, eps
 
 
-@pytest.mark.parametrize("l1,l2,dt,steps", [
-    (9, 12, DT, 37),            # one tile smaller than the region: the halo wraps the torus
-    (61, 70, DT, 64),           # ragged 2 x 2 tiles
-    (150, 131, DT, 33),         # 3 x 3 tiles, odd step count (chunk copy-back)
-    (64, 64, 0.05, 20),         # K = 4..5: a single block holds every sweep
-    (40, 58, 1e-4, 9),          # K = 3
-    (100, 116, 3.0, 16),        # x = 27: K ~ 45, eight blocks per step
+def csr(l1, l2, eps, kind):
+    return ti.graphene_csr(l1, l2, onsite=eps) if kind == MONO else ti.bilayer_csr(l1, l2, onsite=eps)
+
+
+@pytest.mark.parametrize("kind,l1,l2,dt,steps", [
+    (MONO, 9, 12, DT, 37),      # one tile smaller than the region: the halo wraps the torus
+    (MONO, 61, 70, DT, 64),     # ragged tiles
+    (MONO, 150, 131, DT, 33),   # several tiles, odd step count (chunk copy-back)
+    (MONO, 64, 64, 0.05, 20),   # K = 4..5: a single block holds every sweep
+    (MONO, 40, 58, 1e-4, 9),    # K = 3
+    (MONO, 100, 116, 3.0, 16),  # x = 27: K ~ 45, eight blocks per step
+    (BI, 7, 9, DT, 21),         # AB bilayer: wrapped single tile
+    (BI, 90, 61, DT, 33),       # ragged tiles, odd steps
+    (BI, 45, 50, 3.0, 8),       # many blocks per step
 ])
-def test_tblock_matches_oracle(orc, l1, l2, dt, steps):
-    ctx, eps = lattice(l1, l2)
-    h = ti.graphene_csr(l1, l2, onsite=eps)
+def test_tblock_matches_oracle(orc, kind, l1, l2, dt, steps):
+    ctx, eps = lattice(l1, l2, kind=kind)
+    h = csr(l1, l2, eps, kind)
     psi0 = ti.random_phase_state(h.n, 5)
     c = tb.tbpm_dos_corr(ctx, psi0, dt, steps)
     ref = orc.dos_corr(h, 9.0, psi0, dt, steps)
@@ -47,7 +57,7 @@ def test_tblock_matches_oracle(orc, l1, l2, dt, steps):
     K = info["num_terms"]
     assert info["kernel_launches"] <= 3 + steps * ((K - 2) // 6 + 1) + 2 * ((steps + 15) // 16)
     # the per-sweep path on the same FP32 inputs differs only by rounding order
-    ctx2, _ = lattice(l1, l2, flags=tb.TBPM_F_NO_TBLOCK)
+    ctx2, _ = lattice(l1, l2, flags=tb.TBPM_F_NO_TBLOCK, kind=kind)
     c2 = tb.tbpm_dos_corr(ctx2, psi0, dt, steps)
     assert np.max(np.abs(c - c2)) <= 2e-6
 
@@ -91,12 +101,11 @@ def test_tblock_device_buffers_and_pristine(orc):
     assert np.max(np.abs(out[0].cpu().numpy() - ref)) <= C_TOL
 
 
-def test_tblock_large(orc):
-    """2048 x 2048 cells (N = 8,388,608; the state vectors exceed L2): six steps
-    against the oracle."""
-    l = 2048
-    ctx, eps = lattice(l, l, seed=4)
-    h = ti.graphene_csr(l, l, onsite=eps)
+@pytest.mark.parametrize("kind,l", [(MONO, 2048), (BI, 1448)])
+def test_tblock_large(orc, kind, l):
+    """About 8.4 M orbitals (the state vectors exceed L2): six steps against the oracle."""
+    ctx, eps = lattice(l, l, seed=4, kind=kind)
+    h = csr(l, l, eps, kind)
     psi0 = ti.random_phase_state(h.n, 0)
     c = tb.tbpm_dos_corr(ctx, psi0, DT, 6)
     ref = orc.dos_corr(h, 9.0, psi0, DT, 6)
