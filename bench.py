@@ -147,9 +147,29 @@ def cpu_sample(h, seconds_target=(10.0, 30.0)):
     return units / el, f"N={h.n}, {s} DOS steps (K={K}) + {8 * s} KPM moments, {el:.1f} s"
 
 
+def cpu_sample_1core(h, all_core_rate):
+    """The oracle on one thread, on a sample sized for about 10 s at the rate
+    one core should reach (a sixteenth of the all-core rate, at least one step)."""
+    import oracle
+    import tbpm_inputs as ti
+    psi0 = ti.random_phase_state(h.n, 0)
+    K = oracle.cheb_num_terms(DT * RESCALE)
+    s = max(1, int(10.0 * all_core_rate / 16 / workload_units(h.n, K, 1, 8)))
+    n0 = oracle.get_threads()
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.dos_corr(h, RESCALE, psi0, DT, s)
+        oracle.kpm_moments(h, RESCALE, psi0, 8 * s)
+        el = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(n0)
+    return workload_units(h.n, K, s, 8 * s) / el, f"N={h.n}, {s} DOS steps + {8 * s} KPM moments, {el:.1f} s"
+
+
 def threads_used() -> int:
-    v = os.environ.get("OMP_NUM_THREADS")
-    return int(v) if v and v.isdigit() else os.cpu_count()
+    import oracle
+    return oracle.get_threads()
 
 
 # --------------------------------------------------------------- our arm
@@ -304,9 +324,11 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_variants:
         out["variants"] = run_variants(args, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sample = cpu_sample(build_inputs())
+        hc = build_inputs()
+        v, sample = cpu_sample(hc)
+        v1, sample1 = cpu_sample_1core(hc, v)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
-                               "sample": sample}
+                               "sample": sample, "value_1core": v1, "sample_1core": sample1}
     return out
 
 

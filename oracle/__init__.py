@@ -63,6 +63,10 @@ def _bind(path: str):
     l.oracle_fermi_coeffs.argtypes = [d, d, d, d, i32, p]
     l.oracle_ac_corr.restype = i32
     l.oracle_ac_corr.argtypes = [i64, p, p, p, p, p, p, p, d, p, d, d, d, i32, d, d, i32, p]
+    l.oracle_set_threads.restype = None
+    l.oracle_set_threads.argtypes = [i32]
+    l.oracle_get_threads.restype = i32
+    l.oracle_get_threads.argtypes = []
     l.oracle_ac_cond.restype = i32
     l.oracle_ac_cond.argtypes = [p, i32, d, d, d, i32, p, p]
     return l
@@ -90,6 +94,13 @@ class Oracle:
     def __init__(self, path: str):
         self.path = path
         self._l = _bind(path)
+
+    def set_threads(self, n: int) -> None:
+        """OpenMP threads of the row loops (timing only; results do not depend on it)."""
+        self._l.oracle_set_threads(int(n))
+
+    def get_threads(self) -> int:
+        return self._l.oracle_get_threads()
 
     def bessel_j(self, k: int, x: float) -> float:
         return self._l.oracle_bessel_j(int(k), float(x))
@@ -257,6 +268,6 @@ def __getattr__(name):
     # module-level access to the default instance: oracle.propagate(...), etc.
     if name in ("bessel_j", "cheb_num_terms", "cheb_coeffs", "spmv", "propagate", "dos_corr",
                 "kpm_moments", "dos_hann", "jackson", "kpm_dos", "haydock", "haydock_ldos",
-                "quasi_eigenstates", "fermi_coeffs", "ac_corr", "ac_cond"):
+                "quasi_eigenstates", "fermi_coeffs", "ac_corr", "ac_cond", "set_threads", "get_threads"):
         return getattr(default(), name)
     raise AttributeError(name)

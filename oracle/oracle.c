@@ -33,6 +33,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double _Complex cplx;
 
@@ -92,6 +95,25 @@ void oracle_cheb_coeffs(double x, int K, cplx *c)
         }
         c[k] = (k == 0 ? 1.0 : 2.0) * mi_k * j;
     }
+}
+
+/* OpenMP threads for the row loops (timing on one core and on all of them). */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int oracle_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------ sparse ops */
