@@ -356,6 +356,27 @@ def dos_l1(ctx, corr, ref, dt):
     return float(np.sum(np.abs(d - r)) / np.sum(np.abs(r)))
 
 
+def hbm_roof(units_per_s, bytes_per_unit, basis):
+    """HBM roofline of a variant: algorithmic bytes per unit (orbital-term or
+    orbital-term-state) x units/s against the measured copy bandwidth."""
+    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    gbs = units_per_s * bytes_per_unit / 1e9
+    return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+            "bytes_per_unit": bytes_per_unit, "basis": basis}
+
+
+# algorithmic bytes per orbital-term of a middle sweep (FP32, real hoppings):
+# three stored hoppings (int32 column + FP32 value), FP32 diagonal, slice
+# offset; four vector streams (gathered operand, psi, b_{k+2}, output) of 8 B
+B_SELL32 = 3 * (4 + 4) + 4 + 0.25
+B_VEC32 = 4 * 8
+# the blocked stencil over one time step of 17 sweeps, without halo re-reads:
+# first block psi + on-site in (12 B), two b out (16 B); middle block psi,
+# b_{k+1}, b_{k+2}, on-site in (28 B), two b out; final block the same in plus
+# psi0 (8 B), psi out (8 B)
+B_TBLOCK_STEP = (12 + 16) + (28 + 16) + (28 + 8 + 8)
+
+
 def run_variants(args, dev, stream):
     """The precision and batching patterns, each timed with CUDA events on
     device-resident inputs (not part of the headline value):
@@ -382,7 +403,7 @@ def run_variants(args, dev, stream):
     import paper_2509_26309_gb300 as tb
     res = {}
     so = stream.cuda_stream
-    # config 1: 64x64 pristine graphene (N = 8192), FP64, 1024 steps: the
+    # 64x64 pristine graphene (N = 8192), FP64, 1024 steps: the
     # single-launch cluster path against one graph-launched kernel per sweep
     h1 = ti.graphene_csr(64, 64)
     p1 = torch.from_numpy(ti.random_phase_state(h1.n, 0).reshape(1, h1.n)).to(dev)
@@ -394,7 +415,7 @@ def run_variants(args, dev, stream):
         res[name] = {"value": h1.n * 1024 * (K1 - 1) / (ms1 / 1e3), "unit": UNIT, "ms_per_call": ms1,
                      "states": 1, "n_steps": 1024}
         tb.tbpm_destroy(c1)
-    # config 5: uneven batch of 40 lattices (monolayer / AB bilayer, N log-uniform
+    # uneven batch of 40 lattices (monolayer / AB bilayer, N log-uniform
     # 1e4..4e6, per-instance W and rescale), FP64, one block-diagonal operator
     # with an autotuned grid, against the same 40 instances one context at a time
     insts = ti.batch_instances()
@@ -428,7 +449,7 @@ def run_variants(args, dev, stream):
     res["fp64_batch40_sequential"] = {"value": units5 / (seq_ms / 1e3), "unit": UNIT, "ms_per_call": seq_ms,
                                       "instances": len(insts), "n_steps": steps5}
     del insts, psi5
-    # config 3: FP32 single state, SELL, against FP64 on the same state
+    # graphene 2048x2048, W = 1: FP32 single state, SELL, against FP64 on the same state
     n3 = 2 * 2048 * 2048
     h3 = ti.graphene_csr(2048, 2048, onsite=ti.anderson_onsite(n3, W_DISORDER, 1))
     psi = torch.from_numpy(ti.random_phase_state(n3, 0).reshape(1, n3)).to(dev)
@@ -442,14 +463,16 @@ def run_variants(args, dev, stream):
                              tb.make_opts(precision=tb.TBPM_FP32, flags=flags, stream=so))
         ms = timed_calls(lambda: tb.tbpm_dos_corr(ctx, psi, DT, 1024, out=out), 1, stream)
         K = tb.tbpm_get_info(ctx)["num_terms"]
-        res[name] = {"value": n3 * 1024 * (K - 1) / (ms / 1e3), "unit": UNIT, "ms_per_call": ms,
+        v3 = n3 * 1024 * (K - 1) / (ms / 1e3)
+        res[name] = {"value": v3, "unit": UNIT, "ms_per_call": ms,
                      "states": 1, "n_steps": 1024,
+                     "roofline": hbm_roof(v3, B_SELL32 + B_VEC32, "middle sweep, stored matrix + 4 vector streams"),
                      "dos_l1_vs_fp64": dos_l1(c64, out[0].cpu().numpy(), ref3h, DT),
                      "max_abs_dC_vs_fp64": float(np.max(np.abs(out[0].cpu().numpy() - ref3h)))}
         tb.tbpm_destroy(ctx)
     tb.tbpm_destroy(c64)
     del psi, h3
-    # config 4 lattice: FP32 x16 states vs FP64 x1, stencil and stored matrix
+    # graphene 4096x4096, W = 1: FP32 x16 states vs FP64 x1, stencil and stored matrix
     l4 = 4096
     n4 = 2 * l4 * l4
     eps = ti.anderson_onsite(n4, W_DISORDER, 1)
@@ -487,9 +510,15 @@ def run_variants(args, dev, stream):
         v32 = n4 * 16 * steps * (K - 1) / (ms32 / 1e3)
         v64 = n4 * steps * (K - 1) / (ms64 / 1e3)
         s0 = o16[0].cpu().numpy()
+        if path == "stencil":
+            roof = hbm_roof(v32, B_TBLOCK_STEP / (K - 1), "blocked time step, no halo re-reads, per sweep")
+        elif path == "stencil_spmm":
+            roof = hbm_roof(v32, 4 / 16 + B_VEC32, "middle sweep, on-site / 16 + 4 vector streams")
+        else:
+            roof = hbm_roof(v32, B_SELL32 / 16 + B_VEC32, "middle sweep, stored matrix / 16 + 4 vector streams")
         res[f"fp32_x16_{path}_4096x4096"] = {"value": v32, "unit": "orbital-term-states/s", "ms_per_call": ms32,
                                              "states": 16, "n_steps": steps,
-                                             "dos_l1_vs_fp64_state0": dos_l1(ctx64, s0, r, DT)}
+                                             "dos_l1_vs_fp64_state0": dos_l1(ctx64, s0, r, DT), "roofline": roof}
         res[f"fp64_x1_{path}_4096x4096"] = {"value": v64, "unit": UNIT, "ms_per_call": ms64, "states": 1,
                                             "n_steps": steps,
                                             "max_abs_dC_vs_stencil": float(np.max(np.abs(r - ref4)))}
@@ -505,9 +534,12 @@ def run_variants(args, dev, stream):
                                                   stream=so))
         ms1s = timed_calls(lambda: tb.tbpm_dos_corr(c1s, one, DT, steps, out=o1), 2, stream)
         K = tb.tbpm_get_info(c1s)["num_terms"]
-        res[name] = {"value": n4 * steps * (K - 1) / (ms1s / 1e3), "unit": UNIT, "ms_per_call": ms1s, "states": 1,
+        v1s = n4 * steps * (K - 1) / (ms1s / 1e3)
+        roof = (hbm_roof(v1s, B_TBLOCK_STEP / (K - 1), "blocked time step, no halo re-reads, per sweep") if flags == 0
+                else hbm_roof(v1s, 4 + B_VEC32, "middle sweep, on-site + 4 vector streams"))
+        res[name] = {"value": v1s, "unit": UNIT, "ms_per_call": ms1s, "states": 1,
                      "n_steps": steps, "kernel_launches": tb.tbpm_get_info(c1s)["kernel_launches"],
-                     "max_abs_dC_vs_fp64": float(np.max(np.abs(o1[0].cpu().numpy() - ref4)))}
+                     "max_abs_dC_vs_fp64": float(np.max(np.abs(o1[0].cpu().numpy() - ref4))), "roofline": roof}
         tb.tbpm_destroy(c1s)
     res["fp32_tblock_speedup_vs_per_sweep"] = (res["fp32_x1_stencil_tblock_4096x4096"]["value"] /
                                                res["fp32_x1_stencil_per_sweep_4096x4096"]["value"])
@@ -528,7 +560,7 @@ def run_variants(args, dev, stream):
         tb.tbpm_destroy(cbs)
     del pb
     del blk, one
-    # AC conductivity correlation on the config-2 lattice: room temperature,
+    # AC conductivity correlation on the 1024x1024 headline lattice: room temperature,
     # mu = 0, 64 steps; units count the Hamiltonian sweeps (three Fermi series
     # and three states per time step)
     n2 = 2 * L1 * L2

@@ -18,7 +18,7 @@ def test_haydock_coefficients(orc, prec, tol):
         assert np.max(np.abs(a - ra)) <= tol * 10 and np.max(np.abs(b - rb)) <= tol * 10
 
 
-def test_haydock_config2_size_and_ldos(orc):
+def test_haydock_1024x1024_and_ldos(orc):
     """Full 1024x1024 disordered graphene (the bench lattice), LDOS at one site."""
     n = 2 * 1024 * 1024
     h = ti.graphene_csr(1024, 1024, onsite=ti.anderson_onsite(n, 1.0, 1))

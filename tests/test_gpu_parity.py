@@ -23,7 +23,7 @@ def create(h, rescale=9.0, **kw):
     return tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, rescale, tb.make_opts(**kw))
 
 
-def test_config1_pristine_64x64_full(orc):
+def test_pristine_64x64_1024_steps(orc):
     """64x64 pristine graphene, psi0 seed 0, 1024 steps of pi/9, K = 18."""
     h = ti.graphene_csr(64, 64)
     psi0 = ti.random_phase_state(h.n, 0)
@@ -116,7 +116,7 @@ def test_zero_steps_and_multistate(orc):
         assert np.max(np.abs(c[j] - orc.dos_corr(h, 9.0, psi[j], DT, 33))) <= TOL
 
 
-def test_config2_full_size_first_steps(orc):
+def test_disordered_1024x1024_first_steps(orc):
     """1024x1024 graphene (N = 2,097,152), W = 1 eV seed 1, psi0 seed 0: the bench's
     matrix and launch configuration, checked over the first steps and moments."""
     n = 2 * 1024 * 1024
@@ -140,7 +140,7 @@ def test_kpm_moments(orc, M):
     assert np.max(np.abs(mu - ref)) <= TOL
 
 
-def test_kpm_config1_site_state(orc):
+def test_kpm_pristine_64x64_site_state(orc):
     h = ti.graphene_csr(64, 64)
     ctx = create(h)
     psi0 = ti.site_state(h.n, 0)
