@@ -137,3 +137,14 @@ def test_ac_errors():
     # the earlier current operators survive a rejected replacement
     c = tb.tbpm_ac_corr(ctx, psi0, 5.0, 0.0, 0.3, 4)
     assert np.all(np.isfinite(c))
+
+
+def test_ac_zero_steps(orc):
+    """n_steps = 0 gives C_ab(0) only: <phi|f J_a [1 - f] J_b|phi>."""
+    h, cur = make("graphene_8x8")
+    psi0 = ti.random_phase_state(h.n, 5)
+    ctx = ctx_for(h, cur, 9.0)
+    c = tb.tbpm_ac_corr(ctx, psi0, 7.0, -0.2, 0.3, 0)
+    _, ref = orc.ac_corr(h, cur.as_tuple(), 9.0, psi0, 7.0, -0.2, 0.3, 0, kcap=KCAP)
+    assert c.shape == (4, 1)
+    assert np.max(np.abs(c - ref)) <= TOL
