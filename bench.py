@@ -393,7 +393,8 @@ def run_variants(args, dev, stream):
         stored-matrix paths, 32 steps each (the speedup is a throughput ratio,
         so the step count only sets the sample length); DOS L1 of state 0;
       - FP32 single state on that stencil and on an AB-bilayer stencil of as many
-        orbitals, temporally blocked vs one launch per sweep;
+        orbitals, temporally blocked vs one launch per sweep, and 512 KPM moments
+        blocked vs one launch per pass;
       - the AC current correlation on graphene 1024x1024 (W = 1) at 300 K.
     The FP64 runs the errors are taken against are the path the parity tests
     hold to 1e-10 of the oracle."""
@@ -543,6 +544,18 @@ def run_variants(args, dev, stream):
         tb.tbpm_destroy(c1s)
     res["fp32_tblock_speedup_vs_per_sweep"] = (res["fp32_x1_stencil_tblock_4096x4096"]["value"] /
                                                res["fp32_x1_stencil_per_sweep_4096x4096"]["value"])
+    # KPM moments (512) on the same stencil: blocked passes vs one launch per pass
+    mk = torch.empty((1, 512), dtype=torch.complex128, device=dev)
+    for name, flags in (("fp32_kpm_stencil_tblock_4096x4096", 0),
+                        ("fp32_kpm_stencil_per_pass_4096x4096", tb.TBPM_F_NO_TBLOCK)):
+        ck = tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l4, l4, ti.T_GRAPHENE, 0.0, eps, RESCALE,
+                                    tb.make_opts(precision=tb.TBPM_FP32, path=tb.TBPM_PATH_STENCIL, flags=flags,
+                                                 stream=so))
+        msk = timed_calls(lambda: tb.kpm_moments(ck, one, 512, out=mk), 2, stream)
+        res[name] = {"value": n4 * 256 / (msk / 1e3), "unit": UNIT, "ms_per_call": msk, "moments": 512}
+        tb.tbpm_destroy(ck)
+    res["fp32_kpm_tblock_speedup_vs_per_pass"] = (res["fp32_kpm_stencil_tblock_4096x4096"]["value"] /
+                                                  res["fp32_kpm_stencil_per_pass_4096x4096"]["value"])
     # the same on the AB-bilayer stencil with as many orbitals (2896 x 2896 cells, 4 per cell)
     lb = 2896
     nb = 4 * lb * lb

@@ -43,10 +43,12 @@ constexpr int kTbW2 = 32;                       // region cells along m2 (one pe
 constexpr int kTbT2 = kTbW2 - 2 * kTbH;         // interior cells along m2
 
 // PER orbitals per cell: the monolayer runs 1024 threads (64 registers each),
-// the bilayer, with twice the state per cell, 512 (128 registers each).
-template <int PER>
+// the bilayer, with twice the state per cell, 512 (128 registers each); the
+// KPM kernel (KPM = true), which also keeps per-pass dot sums in registers,
+// runs 512 threads for both.
+template <int PER, bool KPM = false>
 struct TbCfg {
-    static constexpr int threads = PER == 2 ? 1024 : 512;
+    static constexpr int threads = (PER == 2 && !KPM) ? 1024 : 512;
     static constexpr int warps = threads / 32;
     static constexpr int W1 = warps * kTbR;     // region rows (m1)
     static constexpr int T1 = W1 - 2 * kTbH;    // interior rows
@@ -93,11 +95,11 @@ struct Stage {
     float2 *on;
 };
 
-template <int PER>
+template <int PER, bool KPM>
 __device__ __forceinline__ void prefetch_tile(const TbParams &p, const Stage &st, int tile, int r0, int lane,
                                               bool first)
 {
-    typedef TbCfg<PER> C;
+    typedef TbCfg<PER, KPM> C;
     const int t1 = tile / p.tiles2, t2 = tile - t1 * p.tiles2;
     const int o1 = t1 * C::T1 - kTbH, o2 = t2 * kTbT2 - kTbH;
     const int m2 = wrap(o2 + lane, p.L2);
@@ -112,7 +114,7 @@ __device__ __forceinline__ void prefetch_tile(const TbParams &p, const Stage &st
         for (int v = 0; v < C::V4; ++v) {
             const int g = cell * C::V4 + v;             // float4 index: orbitals 2v, 2v+1 of the cell
             const int slot = (r * C::V4 + v) * C::threads;
-            cp_async16(st.ps + slot, psi + g);
+            if (!KPM) cp_async16(st.ps + slot, psi + g);
             if (p.onsite) cp_async8(st.on + slot, on + g);
             else st.on[slot] = make_float2(0.0f, 0.0f);
             if (!first) {
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
     // sweeps run so far by this block: the exchange buffer alternates with it
     // (across tiles too), so a buffer is rewritten only two barriers after its reads
     int nsweep = 0;
-    if ((int)blockIdx.x < ntiles) prefetch_tile<PER>(p, st, blockIdx.x, r0, lane, first);
+    if ((int)blockIdx.x < ntiles) prefetch_tile<PER, false>(p, st, blockIdx.x, r0, lane, first);
     __syncthreads();                               // the coefficient table
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int t1 = tile / p.tiles2, t2 = tile - t1 * p.tiles2;
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
             }
         }
         // the staging slots are free again: fetch the next tile during the sweeps
-        if (tile + (int)gridDim.x < ntiles) prefetch_tile<PER>(p, st, tile + gridDim.x, r0, lane, first);
+        if (tile + (int)gridDim.x < ntiles) prefetch_tile<PER, false>(p, st, tile + gridDim.x, r0, lane, first);
         // the register arrays trade roles each sweep: even sweeps read b_{k+1} from
         // xo and overwrite zo with b_k, odd sweeps the reverse
         for (int q = 0; q < p.S; ++q) {
@@ -353,6 +355,146 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
     }
 }
 
+
+// Temporally blocked KPM passes: from T_{m-1} (bz) and T_m (bx), p.S passes
+// T_{m+q+1} = A T_{m+q} - T_{m+q-1}, each with <T_{m+q}|T_{m+q}> and
+// <T_{m+q+1}|T_{m+q}> over the interior cells, written as the partials of
+// slot delta + q in the layout of the one-pass KPM kernel:
+// partials[(2 slot) W + w] = (<T|T>, 0), partials[(2 slot + 1) W + w] = <T'|T>.
+// The interior of the last two T's goes to ox (newest) and oz. A thread's
+// contributions within one tile (at most 3 PER terms) are summed in FP32, then
+// added to per-pass FP32 two-sum pairs that run over all tiles; the pairs are
+// converted to FP64 once and reduced over the warp in FP64.
+template <int PER>
+__global__ void __launch_bounds__(TbCfg<PER, true>::threads, 1) tb_kpm_kernel(TbParams p)
+{
+    typedef TbCfg<PER, true> C;
+    constexpr int N = PER * kTbR;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Stage st;
+    {
+        float4 *base = reinterpret_cast<float4 *>(smem) + threadIdx.x;
+        const int span = kTbR * C::V4 * C::threads;
+        st.ps = base;
+        st.bx = base + span;
+        st.bz = base + 2 * span;
+        st.on = reinterpret_cast<float2 *>(reinterpret_cast<float4 *>(smem) + 3 * span) + threadIdx.x;
+    }
+    float2 *exch = reinterpret_cast<float2 *>(smem + C::stage);
+    const int r0 = warp * kTbR;
+    const int ntiles = p.tiles1 * p.tiles2;
+    const float t = p.t, tp = p.t_perp;
+    // T_{m+1} = A T_m - T_{m-1}: the middle-sweep form with no psi term
+    const float cm[5] = {0.0f, 0.0f, 1.0f, 0.0f, 1.0f};
+    float2 zero[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) zero[i] = make_float2(0.0f, 0.0f);
+    F2Sum acc[kTbS][3];
+
+    float2 xo[N], zo[N];
+    float on[N];
+    int nsweep = 0;
+    if ((int)blockIdx.x < ntiles) prefetch_tile<PER, true>(p, st, blockIdx.x, r0, lane, false);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int t1 = tile / p.tiles2, t2 = tile - t1 * p.tiles2;
+        const int o1 = t1 * C::T1 - kTbH, o2 = t2 * kTbT2 - kTbH;
+        cp_async_wait_all();
+#pragma unroll
+        for (int r = 0; r < kTbR; ++r) {
+#pragma unroll
+            for (int v = 0; v < C::V4; ++v) {
+                const int slot = (r * C::V4 + v) * C::threads;
+                const int i = PER * r + 2 * v;
+                const float2 o = st.on[slot];
+                on[i] = o.x;
+                on[i + 1] = o.y;
+                const float4 bx = st.bx[slot], bz = st.bz[slot];
+                xo[i] = make_float2(bx.x, bx.y);
+                xo[i + 1] = make_float2(bx.z, bx.w);
+                zo[i] = make_float2(bz.x, bz.y);
+                zo[i + 1] = make_float2(bz.z, bz.w);
+            }
+        }
+        if (tile + (int)gridDim.x < ntiles) prefetch_tile<PER, true>(p, st, tile + gridDim.x, r0, lane, false);
+        const int m2 = o2 + lane;
+        const bool col_in = lane >= kTbH && lane < kTbH + kTbT2 && m2 < p.L2;
+        bool row_in[kTbR];
+#pragma unroll
+        for (int r = 0; r < kTbR; ++r) {
+            const int c1 = r0 + r;
+            row_in[r] = col_in && c1 >= kTbH && c1 < kTbH + C::T1 && o1 + c1 < p.L1;
+        }
+#pragma unroll
+        for (int q = 0; q < kTbS; ++q) {
+            if (q < p.S) {
+                float2 *ex = exch + (nsweep++ & 1) * 2 * C::V4 * C::warps * 32;
+                float2 *x = (q & 1) ? zo : xo;
+                float2 *y = (q & 1) ? xo : zo;
+                float2 up[C::V4], dn[C::V4];
+#pragma unroll
+                for (int v = 0; v < C::V4; ++v) {
+                    ex[(v * C::warps + warp) * 32 + lane] = x[2 * v];
+                    ex[((C::V4 + v) * C::warps + warp) * 32 + lane] = x[PER * (kTbR - 1) + 2 * v + 1];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int v = 0; v < C::V4; ++v) {
+                    up[v] = warp > 0 ? ex[((C::V4 + v) * C::warps + warp - 1) * 32 + lane] : x[2 * v + 1];
+                    dn[v] = warp < C::warps - 1 ? ex[(v * C::warps + warp + 1) * 32 + lane]
+                                                : x[PER * (kTbR - 1) + 2 * v];
+                }
+                if ((q & 1) == 0) tb_rows<PER, 0>(zero, on, xo, zo, up, dn, t, tp, cm);
+                else tb_rows<PER, 0>(zero, on, zo, xo, up, dn, t, tp, cm);
+                // the dots of this pass: x = T_{m+q}, y = T_{m+q+1}
+                float nn = 0.0f, cr = 0.0f, ci = 0.0f;
+#pragma unroll
+                for (int r = 0; r < kTbR; ++r) {
+                    if (!row_in[r]) continue;
+#pragma unroll
+                    for (int o = 0; o < PER; ++o) {
+                        const float2 a = x[PER * r + o], b = y[PER * r + o];
+                        nn = fmaf(a.x, a.x, fmaf(a.y, a.y, nn));
+                        cr = fmaf(b.x, a.x, fmaf(b.y, a.y, cr));
+                        ci = fmaf(b.x, a.y, fmaf(-b.y, a.x, ci));
+                    }
+                }
+                acc[q][0].add(nn);
+                acc[q][1].add(cr);
+                acc[q][2].add(ci);
+            }
+        }
+        const bool odd = (p.S & 1) != 0;
+#pragma unroll
+        for (int r = 0; r < kTbR; ++r) {
+            if (!row_in[r]) continue;
+            const int cell = (o1 + r0 + r) * p.L2 + m2;
+#pragma unroll
+            for (int v = 0; v < C::V4; ++v) {
+                const int i = PER * r + 2 * v;
+                const float2 na = odd ? zo[i] : xo[i], nb = odd ? zo[i + 1] : xo[i + 1];
+                const float2 pa = odd ? xo[i] : zo[i], pb = odd ? xo[i + 1] : zo[i + 1];
+                __stcs(reinterpret_cast<float4 *>(p.ox) + cell * C::V4 + v, make_float4(na.x, na.y, nb.x, nb.y));
+                __stcs(reinterpret_cast<float4 *>(p.oz) + cell * C::V4 + v, make_float4(pa.x, pa.y, pb.x, pb.y));
+            }
+        }
+    }
+    const int64_t W = (int64_t)gridDim.x * C::warps;
+    const int64_t gw = (int64_t)blockIdx.x * C::warps + warp;
+#pragma unroll
+    for (int q = 0; q < kTbS; ++q) {
+        if (q < p.S) {
+            const double nn = warp_sum(acc[q][0].value());
+            const double cr = warp_sum(acc[q][1].value());
+            const double ci = warp_sum(acc[q][2].value());
+            if (lane == 0) {
+                p.partials[(2 * (int64_t)(p.delta + q)) * W + gw] = make_double2(nn, 0.0);
+                p.partials[(2 * (int64_t)(p.delta + q) + 1) * W + gw] = make_double2(cr, ci);
+            }
+        }
+    }
+}
+
 }  // namespace
 
 int tb_warps(int per) { return per == 2 ? TbCfg<2>::warps : TbCfg<4>::warps; }
@@ -372,6 +514,32 @@ cudaError_t tb_prepare(int per)
                                     (int)TbCfg<2>::smem);
     return cudaFuncSetAttribute(tb_block_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)TbCfg<4>::smem);
+}
+
+int tb_kpm_warps() { return TbCfg<2, true>::warps; }
+
+int tb_kpm_tiles(int per, int64_t l1, int64_t l2, int *tiles1, int *tiles2)
+{
+    const int t1 = per == 2 ? TbCfg<2, true>::T1 : TbCfg<4, true>::T1;
+    *tiles1 = (int)((l1 + t1 - 1) / t1);
+    *tiles2 = (int)((l2 + kTbT2 - 1) / kTbT2);
+    return *tiles1 * *tiles2;
+}
+
+cudaError_t tb_kpm_prepare(int per)
+{
+    if (per == 2)
+        return cudaFuncSetAttribute(tb_kpm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)TbCfg<2, true>::smem);
+    return cudaFuncSetAttribute(tb_kpm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TbCfg<4, true>::smem);
+}
+
+cudaError_t launch_tb_kpm(int per, const TbParams &p, int grid, cudaStream_t s)
+{
+    if (per == 2) tb_kpm_kernel<2><<<grid, TbCfg<2, true>::threads, TbCfg<2, true>::smem, s>>>(p);
+    else tb_kpm_kernel<4><<<grid, TbCfg<4, true>::threads, TbCfg<4, true>::smem, s>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tb_block(int per, const TbParams &p, int grid, cudaStream_t s)

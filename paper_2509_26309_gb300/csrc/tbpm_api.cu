@@ -653,16 +653,25 @@ bool use_tblock(const tbpm_ctx *ctx)
 
 int tb_per(const tbpm_ctx *ctx) { return ctx->op == OP_STENCIL_MONO ? 2 : 4; }
 
+// KPM moments on an FP32 lattice stencil run their passes blocked too.
+bool use_tblock_kpm(const tbpm_ctx *ctx)
+{
+    return (ctx->op == OP_STENCIL_MONO || ctx->op == OP_STENCIL_BI) && ctx->precision == TBPM_FP32 &&
+           !(ctx->flags & TBPM_F_NO_TBLOCK);
+}
+
 // The temporally blocked path's extra vectors (two b buffers, a second state).
 int ensure_tb(tbpm_ctx *ctx)
 {
     if (ctx->d_tb) return TBPM_OK;
     CU(tb_prepare(tb_per(ctx)));
+    CU(tb_kpm_prepare(tb_per(ctx)));
     const size_t vb = 3 * sizeof(float2) * (size_t)ctx->n_pad;
     CU(cudaMalloc(&ctx->d_tb, vb));
     CU(cudaMemsetAsync(ctx->d_tb, 0, vb, ctx->stream));
     int t1, t2;
     ctx->tb_grid = std::min(ctx->num_sms, tb_tiles(tb_per(ctx), ctx->sten.l1, ctx->sten.l2, &t1, &t2));
+    ctx->tb_kpm_grid = std::min(ctx->num_sms, tb_kpm_tiles(tb_per(ctx), ctx->sten.l1, ctx->sten.l2, &t1, &t2));
     return TBPM_OK;
 }
 
@@ -718,6 +727,52 @@ int enqueue_tb_chunk(tbpm_ctx *ctx, int K, int len, cudaStream_t s, int64_t *lau
     return TBPM_OK;
 }
 
+// `len` KPM passes (after the first) by blocked launches of up to kTbS passes:
+// T_{m-1} in d_psi and T_m in d_b0 at the start; launches alternate between
+// that pair and (tb0, tb1), and a chunk that ends on the other pair copies it
+// back. The dots of pass d go to partial slot d as in enqueue_kpm_chunk.
+constexpr int kTbKpmChunk = 2 * kTbS;   // two launches per full chunk
+
+int enqueue_tbkpm_chunk(tbpm_ctx *ctx, int len, cudaStream_t s, int64_t *launches)
+{
+    const size_t vb = sizeof(float2) * (size_t)ctx->n_pad;
+    char *tb = static_cast<char *>(ctx->d_tb);
+    float2 *x0 = static_cast<float2 *>(ctx->d_b0), *z0 = static_cast<float2 *>(ctx->d_psi);
+    float2 *x1 = reinterpret_cast<float2 *>(tb), *z1 = reinterpret_cast<float2 *>(tb + vb);
+    TbParams p;
+    memset(&p, 0, sizeof(p));
+    const int per = tb_per(ctx);
+    p.L1 = (int)ctx->sten.l1;
+    p.L2 = (int)ctx->sten.l2;
+    tb_kpm_tiles(per, ctx->sten.l1, ctx->sten.l2, &p.tiles1, &p.tiles2);
+    p.t = (float)ctx->sten.t;
+    p.t_perp = (float)ctx->sten.t_perp;
+    p.onsite = static_cast<const float *>(ctx->sten.onsite);
+    p.partials = ctx->d_partials;
+    const int grid = ctx->tb_kpm_grid;
+    int pr = 0;
+    for (int d0 = 0; d0 < len; d0 += kTbS) {
+        p.S = std::min(kTbS, len - d0);
+        p.delta = d0;
+        p.bx = pr ? x1 : x0;
+        p.bz = pr ? z1 : z0;
+        p.ox = pr ? x0 : x1;
+        p.oz = pr ? z0 : z1;
+        CU(launch_tb_kpm(per, p, grid, s));
+        ++*launches;
+        pr ^= 1;
+    }
+    if (pr) {
+        CU(cudaMemcpyAsync(x0, x1, vb, cudaMemcpyDeviceToDevice, s));
+        CU(cudaMemcpyAsync(z0, z1, vb, cudaMemcpyDeviceToDevice, s));
+    }
+    CU(launch_reduce_seg(ctx->d_partials, len, 2, (int64_t)grid * tb_kpm_warps(), nullptr, 1, ctx->d_counter, 1,
+                         ctx->d_out, 0, s));
+    CU(launch_advance(ctx->d_counter, len, s));
+    *launches += 2;
+    return TBPM_OK;
+}
+
 // Runs (and on first use captures) the graph of one chunk.
 int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_t ld = 0)
 {
@@ -725,7 +780,7 @@ int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_
     // instances (ld = n_steps + 1 for kinds 2 and 3); 4: Haydock (ld = M); 5: DOS with
     // quasi-eigenstate accumulation (one state; dropped at the end of the call);
     // 6: AC correlation (three states and the current-operator dots); 7: DOS, one
-    // state, temporally blocked stencil sweeps
+    // state, temporally blocked stencil sweeps; 8: KPM, temporally blocked passes
     const auto key = std::make_tuple(kind, len, K, (int)ld);
     auto it = ctx->graphs.find(key);
     int64_t nl = 0;
@@ -736,6 +791,7 @@ int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_
                  : kind == 4 ? enqueue_hay_chunk(ctx, len, (int)ld, ctx->cap_stream, &nl)
                  : kind == 6 ? enqueue_ac_chunk(ctx, K, len, ctx->cap_stream, &nl)
                  : kind == 7 ? enqueue_tb_chunk(ctx, K, len, ctx->cap_stream, &nl)
+                 : kind == 8 ? enqueue_tbkpm_chunk(ctx, len, ctx->cap_stream, &nl)
                              : enqueue_dos_chunk(ctx, K, len, kind == 2 ? 16 : 1, ld, ctx->cap_stream, &nl,
                                                  kind == 5);
         cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
@@ -751,6 +807,7 @@ int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_
              : kind == 4 ? 4 * (int64_t)len
              : kind == 6 ? (int64_t)len * (3 * (K - 1) + 1) + 2
              : kind == 7 ? (int64_t)len * ((K - 2) / kTbS + 1) + 2
+             : kind == 8 ? (int64_t)(len + kTbS - 1) / kTbS + 2
                          : (int64_t)len * (K - 1) + 2;
         if (kind != 1 && kind != 4 && (ctx->flags & TBPM_F_RENORM)) nl += len;
         if (kind == 5) nl += len;
@@ -1234,10 +1291,12 @@ int kpm_moments(tbpm_ctx *ctx, const double *psi0, int nstates, int M, double *m
                              ctx->d_out, 0, ctx->stream));
         CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
         launches += 3;
+        const bool tbk = use_tblock_kpm(ctx);
+        if (tbk && (rc = ensure_tb(ctx))) return rc;
         int done = 0;
         while (done < P) {
-            const int len = std::min(kChunk, P - done);
-            if ((rc = run_chunk(ctx, 1, 0, len, &launches))) return rc;
+            const int len = std::min(tbk ? kTbKpmChunk : kChunk, P - done);
+            if ((rc = run_chunk(ctx, tbk ? 8 : 1, 0, len, &launches))) return rc;
             done += len;
         }
         double2 *dmu = ctx->d_out + ndots;

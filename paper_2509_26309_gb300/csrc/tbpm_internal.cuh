@@ -121,6 +121,13 @@ int tb_tiles(int per, int64_t l1, int64_t l2, int *tiles1, int *tiles2);
 // Opts the kernel in to its shared memory on the current device (before any capture).
 cudaError_t tb_prepare(int per);
 cudaError_t launch_tb_block(int per, const TbParams &p, int grid, cudaStream_t s);
+// The blocked KPM passes (512 threads per block for both lattices): p.S passes
+// from T_{m-1} (bz), T_m (bx), dot partials of slots delta .. delta + S - 1,
+// the last two T's to ox (newest) and oz.
+int tb_kpm_warps();
+int tb_kpm_tiles(int per, int64_t l1, int64_t l2, int *tiles1, int *tiles2);
+cudaError_t tb_kpm_prepare(int per);
+cudaError_t launch_tb_kpm(int per, const TbParams &p, int grid, cudaStream_t s);
 
 // KPM sweep: T_{m+1} = 2 H~ T_m - T_{m-1} with <T_m|T_m> and <T_{m+1}|T_m>.
 struct KpmParams {
@@ -221,6 +228,7 @@ struct tbpm_ctx {
     // temporally blocked stencil path: b buffers P2, P3 and the second state buffer
     void *d_tb = nullptr;                // [3][n_pad] float2
     int tb_grid = 0;
+    int tb_kpm_grid = 0;
     int fermi_K = 0;                     // 0: no coefficients cached
     // autotuner: (blocks per SM, ms per middle sweep) of each candidate grid
     bool tuned = false;

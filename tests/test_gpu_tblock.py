@@ -110,3 +110,36 @@ def test_tblock_large(orc, kind, l):
     c = tb.tbpm_dos_corr(ctx, psi0, DT, 6)
     ref = orc.dos_corr(h, 9.0, psi0, DT, 6)
     assert np.max(np.abs(c - ref)) <= C_TOL
+
+
+@pytest.mark.parametrize("kind,l1,l2,M", [
+    (MONO, 30, 30, 1024),       # one wrapped tile
+    (MONO, 130, 61, 301),       # ragged tiles, odd M, a short last chunk
+    (MONO, 47, 50, 2),          # only the first pass
+    (BI, 33, 29, 512),
+])
+def test_tblock_kpm_matches_oracle(orc, kind, l1, l2, M):
+    """KPM moments with blocked passes on the FP32 stencils: the FP32 bar of the
+    one-pass kernel (|dmu| <= 1e-4 over 1024 moments), and close to the
+    one-pass FP32 result."""
+    ctx, eps = lattice(l1, l2, seed=6, kind=kind)
+    h = csr(l1, l2, eps, kind)
+    psi0 = ti.random_phase_state(h.n, 1)
+    mu = tb.kpm_moments(ctx, psi0, M)
+    ref = orc.kpm_moments(h, 9.0, psi0, M)
+    assert np.max(np.abs(mu - ref)) <= 1e-4
+    ctx2, _ = lattice(l1, l2, seed=6, kind=kind, flags=tb.TBPM_F_NO_TBLOCK)
+    mu2 = tb.kpm_moments(ctx2, psi0, M)
+    assert np.max(np.abs(mu - mu2)) <= 2e-5
+    assert np.array_equal(mu, tb.kpm_moments(ctx, psi0, M))      # fixed reduction order
+
+
+def test_tblock_kpm_large(orc):
+    """Blocked KPM passes on 2048 x 2048 cells (state vectors beyond L2)."""
+    l = 2048
+    ctx, eps = lattice(l, l, seed=7)
+    h = csr(l, l, eps, MONO)
+    psi0 = ti.random_phase_state(h.n, 2)
+    mu = tb.kpm_moments(ctx, psi0, 40)
+    ref = orc.kpm_moments(h, 9.0, psi0, 40)
+    assert np.max(np.abs(mu - ref)) <= 1e-5
