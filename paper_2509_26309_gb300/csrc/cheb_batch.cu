@@ -202,13 +202,13 @@ __global__ void __launch_bounds__(kBlock) sweep_b16(SweepParams p)
         st4(y, row, pair, out);
         if (FINAL) {
             const C2 q = ld4_plain(psi0, row, pair);
-            f0r.add_prod(q.r0, out.r0); f0r.add_prod(q.i0, out.i0);
-            f0i.add_prod(q.r0, out.i0); f0i.add_prod(-q.i0, out.r0);
-            f1r.add_prod(q.r1, out.r1); f1r.add_prod(q.i1, out.i1);
-            f1i.add_prod(q.r1, out.i1); f1i.add_prod(-q.i1, out.r1);
+            f0r.add_dot(q.r0, out.r0, q.i0, out.i0);
+            f0i.add_dot(q.r0, out.i0, -q.i0, out.r0);
+            f1r.add_dot(q.r1, out.r1, q.i1, out.i1);
+            f1i.add_dot(q.r1, out.i1, -q.i1, out.r1);
             if (p.norm_partials) {
-                g0.add_prod(out.r0, out.r0); g0.add_prod(out.i0, out.i0);
-                g1.add_prod(out.r1, out.r1); g1.add_prod(out.i1, out.i1);
+                g0.add_dot(out.r0, out.r0, out.i0, out.i0);
+                g1.add_dot(out.r1, out.r1, out.i1, out.i1);
             }
         }
     }

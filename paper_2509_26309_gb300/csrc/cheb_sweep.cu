@@ -121,14 +121,9 @@ __global__ void __launch_bounds__(kBlockB1) sweep_b1(SweepParams p)
         y[row] = out;
         if (FINAL && kF32 && !MULTI) {
             const V q = psi0[row];
-            fr.add_prod((float)q.x, (float)out.x);
-            fr.add_prod((float)q.y, (float)out.y);
-            fi.add_prod((float)q.x, (float)out.y);
-            fi.add_prod(-(float)q.y, (float)out.x);
-            if (p.norm_partials) {
-                fn.add_prod((float)out.x, (float)out.x);
-                fn.add_prod((float)out.y, (float)out.y);
-            }
+            fr.add_dot((float)q.x, (float)out.x, (float)q.y, (float)out.y);
+            fi.add_dot((float)q.x, (float)out.y, -(float)q.y, (float)out.x);
+            if (p.norm_partials) fn.add_dot((float)out.x, (float)out.x, (float)out.y, (float)out.y);
         } else if (FINAL) {
             const V q = psi0[row];
             const double qr = (double)q.x, qi = (double)q.y;
@@ -203,12 +198,9 @@ __global__ void __launch_bounds__(kBlockB1) kpm_b1(KpmParams p)
         }
         y[row] = out;
         if (sizeof(R) == 4) {
-            fn.add_prod((float)xi.x, (float)xi.x);
-            fn.add_prod((float)xi.y, (float)xi.y);
-            fr.add_prod((float)out.x, (float)xi.x);
-            fr.add_prod((float)out.y, (float)xi.y);
-            fi.add_prod((float)out.x, (float)xi.y);
-            fi.add_prod(-(float)out.y, (float)xi.x);
+            fn.add_dot((float)xi.x, (float)xi.x, (float)xi.y, (float)xi.y);
+            fr.add_dot((float)out.x, (float)xi.x, (float)out.y, (float)xi.y);
+            fi.add_dot((float)out.x, (float)xi.y, -(float)out.y, (float)xi.x);
         } else {
             const double xr = (double)xi.x, xim = (double)xi.y;
             const double orr = (double)out.x, oi = (double)out.y;

@@ -333,11 +333,11 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
                 if (final) {
                     __stcs(reinterpret_cast<float4 *>(p.psi_out) + g, yn);
                     const float4 q0 = __ldcs(reinterpret_cast<const float4 *>(p.psi0) + g);
-                    // conj(q0) y = (q0.x y.x + q0.y y.y) + i (q0.x y.y - q0.y y.x), products exact
-                    sr.add_prod(q0.x, yn.x); sr.add_prod(q0.y, yn.y);
-                    si.add_prod(q0.x, yn.y); si.add_prod(-q0.y, yn.x);
-                    sr.add_prod(q0.z, yn.z); sr.add_prod(q0.w, yn.w);
-                    si.add_prod(q0.z, yn.w); si.add_prod(-q0.w, yn.z);
+                    // conj(q0) y = (q0.x y.x + q0.y y.y) + i (q0.x y.y - q0.y y.x), two orbitals
+                    sr.add_dot(q0.x, yn.x, q0.y, yn.y);
+                    si.add_dot(q0.x, yn.y, -q0.y, yn.x);
+                    sr.add_dot(q0.z, yn.z, q0.w, yn.w);
+                    si.add_dot(q0.z, yn.w, -q0.w, yn.z);
                 } else {
                     const float2 pa = odd ? xo[i] : zo[i], pb = odd ? xo[i + 1] : zo[i + 1];
                     __stcs(reinterpret_cast<float4 *>(p.ox) + g, yn);

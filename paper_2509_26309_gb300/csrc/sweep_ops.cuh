@@ -147,13 +147,14 @@ __device__ __forceinline__ void stencil_apply(const SweepParams &p, int64_t row,
     }
 }
 
-// Sums of FP32 products at about twice FP32's precision on the FP32 pipe:
+// Long sums of FP32 terms at about twice FP32's precision, on the FP32 pipe:
 // GB300 issues FP64 at a small fraction of its FP32 rate, so the FP32 kernels
-// do not convert every element to FP64 for their dots. Each product a b is
-// split exactly into p + e (p = a b rounded, e = fma(a, b, -p)), p is added to
-// the running (hi, lo) pair by Knuth's two-sum and e to lo; the pair is
-// converted to FP64 once, when the partial leaves the thread. The _rn
-// intrinsics keep the compiler from contracting or reordering the steps.
+// do not convert every element to FP64 for their dots. Each term (one
+// component of a complex product, a1 b1 + a2 b2, formed by one FMA in FP32 as
+// the FP32 data it comes from) is added to the running (hi, lo) pair by Knuth's
+// two-sum, so the summation itself loses nothing; the pair is converted to
+// FP64 once, when the partial leaves the thread. The _rn intrinsics keep the
+// compiler from contracting or reordering the two-sum.
 struct F2Sum {
     float hi = 0.0f, lo = 0.0f;
     __device__ __forceinline__ void add(float v)
@@ -164,13 +165,8 @@ struct F2Sum {
         hi = s;
         lo = __fadd_rn(lo, err);
     }
-    __device__ __forceinline__ void add_prod(float a, float b)
-    {
-        const float p = __fmul_rn(a, b);
-        const float e = fmaf(a, b, -p);
-        add(p);
-        lo = __fadd_rn(lo, e);
-    }
+    // += a1 b1 + a2 b2
+    __device__ __forceinline__ void add_dot(float a1, float b1, float a2, float b2) { add(fmaf(a1, b1, a2 * b2)); }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
