@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kBlockB1) sweep_b1(SweepParams p)
 // <x|x> and <y|x> over the warp's slices, reduced once per warp into
 // partials[(2 delta + 0/1) * W + warp].
 template <typename R, int OP, bool REALV, bool FIRST>
-__global__ void __launch_bounds__(kBlockB1) kpm_b1(KpmParams p)
+__global__ void __launch_bounds__(kBlockB1, sizeof(R) == 4 ? 3 : 1) kpm_b1(KpmParams p)
 {
     typedef typename V2<R>::T V;
     SweepParams sp;                     // operator fields for the shared helpers
@@ -304,6 +304,20 @@ cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cuda
                              : kpm_dispatch<float, OP_SELL, false>(p, grid, s);
     if (v.op == OP_STENCIL_MONO) return kpm_dispatch<float, OP_STENCIL_MONO, true>(p, grid, s);
     return kpm_dispatch<float, OP_STENCIL_BI, true>(p, grid, s);
+}
+
+// Grid of the KPM kernel: its own occupancy (it holds the dot sums in more
+// registers than the Clenshaw sweeps), whole waves of resident blocks.
+int kpm_grid(const SweepVariant &v, int num_sms)
+{
+    int per_sm = 0;
+    cudaError_t e;
+    if (v.precision == TBPM_FP64)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpm_b1<double, OP_SELL, true, false>, kBlockB1, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpm_b1<float, OP_SELL, true, false>, kBlockB1, 0);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 2;
+    return per_sm * num_sms;
 }
 
 int sweep_grid(const SweepVariant &v, int num_sms)

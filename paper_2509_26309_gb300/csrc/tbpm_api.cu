@@ -344,7 +344,7 @@ int ensure_work(tbpm_ctx *ctx, int states, size_t out_elems, size_t stage_double
         CU(cudaMemsetAsync(ctx->d_b1, 0, vb, ctx->stream));
         // single-state partials: one per slice; 16-state partials: one per block and state
         const size_t nsl = (size_t)(ctx->n_pad / kSlice);
-        const size_t W = (size_t)ctx->nblk * (kBlockB1 / 32);
+        const size_t W = (size_t)std::max(ctx->nblk, ctx->nblk_kpm) * (kBlockB1 / 32);
         const size_t per_slot = std::max<size_t>(std::max(std::max(2 * nsl, 2 * W), (size_t)ctx->num_sms * 32),
                                                  (size_t)ctx->nblk16 * kMaxBlockStates);
         ctx->partials_cap = (size_t)(kChunk + 1) * per_slot;
@@ -482,7 +482,7 @@ int enqueue_kpm_chunk(tbpm_ctx *ctx, int len, cudaStream_t s, int64_t *launches)
     p.n = op.n; p.nslices = op.nslices; p.slice_off = op.slice_off; p.cols = op.cols;
     p.vals = op.vals; p.diag = op.diag; p.l1 = op.l1; p.l2 = op.l2; p.t = op.t; p.t_perp = op.t_perp;
     p.partials = ctx->d_partials;
-    p.nblk = ctx->nblk;
+    p.nblk = ctx->nblk_kpm;
     p.scale = 1.0;
     p.first = false;
     for (int d = 0; d < len; ++d) {
@@ -490,10 +490,10 @@ int enqueue_kpm_chunk(tbpm_ctx *ctx, int len, cudaStream_t s, int64_t *launches)
         p.x = (d & 1) == 0 ? ctx->d_b0 : ctx->d_psi;
         p.y = (d & 1) == 0 ? ctx->d_psi : ctx->d_b0;
         p.delta = d;
-        CU(launch_kpm(v, p, ctx->nblk, s));
+        CU(launch_kpm(v, p, ctx->nblk_kpm, s));
         ++*launches;
     }
-    CU(launch_reduce_seg(ctx->d_partials, len, 2, (int64_t)ctx->nblk * (kBlockB1 / 32), nullptr, 1,
+    CU(launch_reduce_seg(ctx->d_partials, len, 2, (int64_t)ctx->nblk_kpm * (kBlockB1 / 32), nullptr, 1,
                          ctx->d_counter, 1, ctx->d_out, 0, s));
     CU(launch_advance(ctx->d_counter, len, s));
     *launches += 2;
@@ -891,6 +891,7 @@ static int finish_create(tbpm_ctx *ctx, const tbpm_opts &o)
     int rc = init_device(ctx, o);
     if (rc) return rc;
     ctx->nblk = sweep_grid(variant(ctx, 1), ctx->num_sms);
+    ctx->nblk_kpm = kpm_grid(variant(ctx, 1), ctx->num_sms);
     ctx->nblk16 = sweep_grid_b16(ctx->num_sms);
     return TBPM_OK;
 }
@@ -1285,9 +1286,9 @@ int kpm_moments(tbpm_ctx *ctx, const double *psi0, int nstates, int M, double *m
         p.n = op.n; p.nslices = op.nslices; p.slice_off = op.slice_off; p.cols = op.cols;
         p.vals = op.vals; p.diag = op.diag; p.l1 = op.l1; p.l2 = op.l2; p.t = op.t; p.t_perp = op.t_perp;
         p.x = ctx->d_psi; p.y = ctx->d_b0; p.scale = 0.5; p.first = true;
-        p.partials = ctx->d_partials; p.delta = 0; p.nblk = ctx->nblk;
-        CU(launch_kpm(v, p, ctx->nblk, ctx->stream));
-        CU(launch_reduce_seg(ctx->d_partials, 1, 2, (int64_t)ctx->nblk * (kBlockB1 / 32), nullptr, 1, nullptr, 0,
+        p.partials = ctx->d_partials; p.delta = 0; p.nblk = ctx->nblk_kpm;
+        CU(launch_kpm(v, p, ctx->nblk_kpm, ctx->stream));
+        CU(launch_reduce_seg(ctx->d_partials, 1, 2, (int64_t)ctx->nblk_kpm * (kBlockB1 / 32), nullptr, 1, nullptr, 0,
                              ctx->d_out, 0, ctx->stream));
         CU(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), ctx->stream));
         launches += 3;

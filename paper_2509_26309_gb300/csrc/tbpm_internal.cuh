@@ -180,6 +180,7 @@ struct tbpm_ctx {
     int64_t nnz = 0;
     // sweep grids (fixed per context so the dot partials are deterministic)
     int nblk = 0;                    // single-state kernels
+    int nblk_kpm = 0;                // the single-state KPM kernel
     int nblk16 = 0;                  // 16-state kernels
     // coefficients
     double2 *d_coef = nullptr;       // [kMaxTerms]
@@ -362,6 +363,7 @@ cudaError_t launch_kpm_dos(const double2 *mu, int M, int n_e, double rescale, do
 
 // Block count of the sweep kernels at full occupancy (cheb_sweep.cu).
 int sweep_grid(const SweepVariant &v, int num_sms);
+int kpm_grid(const SweepVariant &v, int num_sms);
 
 // Batched FP32 sweeps over 16 interleaved states (cheb_batch.cu).
 cudaError_t launch_sweep_b16(const SweepVariant &v, SweepKind kind, bool a_imag, bool has_z,
