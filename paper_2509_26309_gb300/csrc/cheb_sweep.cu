@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kBlockB1) sweep_b1(SweepParams p)
 // <x|x> and <y|x> over the warp's slices, reduced once per warp into
 // partials[(2 delta + 0/1) * W + warp].
 template <typename R, int OP, bool REALV, bool FIRST>
-__global__ void __launch_bounds__(kBlockB1, sizeof(R) == 4 ? 3 : 1) kpm_b1(KpmParams p)
+__global__ void __launch_bounds__(kBlockB1, sizeof(R) == 4 ? 3 : 2) kpm_b1(KpmParams p)
 {
     typedef typename V2<R>::T V;
     SweepParams sp;                     // operator fields for the shared helpers
