@@ -89,6 +89,46 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Warp sum of a two-sum pair in FP32 (a butterfly of two-sums); lane 0 holds
+// the warp's result.
+__device__ __forceinline__ void warp_sum_f2(F2Sum &a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h = __shfl_xor_sync(0xffffffffu, a.hi, o);
+        const float l = __shfl_xor_sync(0xffffffffu, a.lo, o);
+        a.add(h);
+        a.lo = __fadd_rn(a.lo, l);
+    }
+}
+
+// Block sums of NV two-sum pairs (every thread calls it; shared memory sm
+// holds NV * WARPS float2): each warp's lane 0 stores its pairs, then thread
+// v < NV adds the warps' pairs in warp order and returns value v in FP64
+// (one conversion per value and block: GB300's FP64 pipe is narrow, so no
+// per-thread FP64 reduction).
+template <int NV, int WARPS>
+__device__ __forceinline__ double block_sum_f2(F2Sum *a, float2 *sm, int warp, int lane)
+{
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        warp_sum_f2(a[v]);
+        if (lane == 0) sm[v * WARPS + warp] = make_float2(a[v].hi, a[v].lo);
+    }
+    __syncthreads();
+    double out = 0.0;
+    if ((int)threadIdx.x < NV) {
+        F2Sum t;
+        for (int w = 0; w < WARPS; ++w) {
+            const float2 e = sm[threadIdx.x * WARPS + w];
+            t.add(e.x);
+            t.lo = __fadd_rn(t.lo, e.y);
+        }
+        out = t.value();
+    }
+    return out;
+}
+
 // This thread's staging slots: slot (r, v) at [(r * V4 + v) * threads].
 struct Stage {
     float4 *ps, *bx, *bz;
@@ -346,12 +386,12 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
             }
         }
     }
-    if (final) {
-        const double dr = warp_sum(sr.value());
-        const double di = warp_sum(si.value());
-        if (lane == 0)
-            p.partials[(int64_t)p.delta * gridDim.x * C::warps + blockIdx.x * C::warps + warp] =
-                make_double2(dr, di);
+    if (final) {                                  // one partial per block, slot delta
+        __syncthreads();                          // staging reused as reduction scratch
+        F2Sum a[2] = {sr, si};
+        const double v = block_sum_f2<2, C::warps>(a, reinterpret_cast<float2 *>(smem), warp, lane);
+        if ((int)threadIdx.x < 2)
+            reinterpret_cast<double *>(p.partials + (int64_t)p.delta * gridDim.x + blockIdx.x)[threadIdx.x] = v;
     }
 }
 
@@ -359,12 +399,12 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
 // Temporally blocked KPM passes: from T_{m-1} (bz) and T_m (bx), p.S passes
 // T_{m+q+1} = A T_{m+q} - T_{m+q-1}, each with <T_{m+q}|T_{m+q}> and
 // <T_{m+q+1}|T_{m+q}> over the interior cells, written as the partials of
-// slot delta + q in the layout of the one-pass KPM kernel:
-// partials[(2 slot) W + w] = (<T|T>, 0), partials[(2 slot + 1) W + w] = <T'|T>.
+// slot delta + q, one per block (W = blocks):
+// partials[(2 slot) W + b] = (<T|T>, 0), partials[(2 slot + 1) W + b] = <T'|T>.
 // The interior of the last two T's goes to ox (newest) and oz. A thread's
 // contributions within one tile (at most 3 PER terms) are summed in FP32, then
 // added to per-pass FP32 two-sum pairs that run over all tiles; the pairs are
-// converted to FP64 once and reduced over the warp in FP64.
+// summed over the block in FP32 and converted to FP64 once per block.
 template <int PER>
 __global__ void __launch_bounds__(TbCfg<PER, true>::threads, 1) tb_kpm_kernel(TbParams p)
 {
@@ -479,25 +519,23 @@ __global__ void __launch_bounds__(TbCfg<PER, true>::threads, 1) tb_kpm_kernel(Tb
             }
         }
     }
-    const int64_t W = (int64_t)gridDim.x * C::warps;
-    const int64_t gw = (int64_t)blockIdx.x * C::warps + warp;
-#pragma unroll
-    for (int q = 0; q < kTbS; ++q) {
-        if (q < p.S) {
-            const double nn = warp_sum(acc[q][0].value());
-            const double cr = warp_sum(acc[q][1].value());
-            const double ci = warp_sum(acc[q][2].value());
-            if (lane == 0) {
-                p.partials[(2 * (int64_t)(p.delta + q)) * W + gw] = make_double2(nn, 0.0);
-                p.partials[(2 * (int64_t)(p.delta + q) + 1) * W + gw] = make_double2(cr, ci);
-            }
+    // one partial per block and pass: value 3 q + c of thread 3 q + c
+    __syncthreads();                              // staging reused as reduction scratch
+    const double v = block_sum_f2<3 * kTbS, C::warps>(&acc[0][0], reinterpret_cast<float2 *>(smem), warp, lane);
+    const int q = threadIdx.x / 3, c = threadIdx.x - 3 * (threadIdx.x / 3);
+    if ((int)threadIdx.x < 3 * p.S) {
+        const int64_t W = gridDim.x;
+        double *e = reinterpret_cast<double *>(p.partials + (2 * (int64_t)(p.delta + q) + (c > 0)) * W + blockIdx.x);
+        if (c == 0) {
+            e[0] = v;
+            e[1] = 0.0;
+        } else {
+            e[c - 1] = v;
         }
     }
 }
 
 }  // namespace
-
-int tb_warps(int per) { return per == 2 ? TbCfg<2>::warps : TbCfg<4>::warps; }
 
 int tb_tiles(int per, int64_t l1, int64_t l2, int *tiles1, int *tiles2)
 {
@@ -515,8 +553,6 @@ cudaError_t tb_prepare(int per)
     return cudaFuncSetAttribute(tb_block_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)TbCfg<4>::smem);
 }
-
-int tb_kpm_warps() { return TbCfg<2, true>::warps; }
 
 int tb_kpm_tiles(int per, int64_t l1, int64_t l2, int *tiles1, int *tiles2)
 {

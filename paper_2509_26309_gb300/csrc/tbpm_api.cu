@@ -680,7 +680,7 @@ int ensure_tb(tbpm_ctx *ctx)
 // b-buffer pairs (b0, b1) and (tb0, tb1), and each step writes psi(t_{n+1})
 // to the other state buffer (a chunk of odd length copies it back, so every
 // chunk ends with the state in d_psi). The final launch of step d writes the
-// <psi0|psi> partials of slot d, one per warp of the grid.
+// <psi0|psi> partials of slot d, one per block of the grid.
 int enqueue_tb_chunk(tbpm_ctx *ctx, int K, int len, cudaStream_t s, int64_t *launches)
 {
     const size_t vb = sizeof(float2) * (size_t)ctx->n_pad;
@@ -720,7 +720,7 @@ int enqueue_tb_chunk(tbpm_ctx *ctx, int K, int len, cudaStream_t s, int64_t *lau
         }
     }
     if (len & 1) CU(cudaMemcpyAsync(S[0], S[1], vb, cudaMemcpyDeviceToDevice, s));
-    CU(launch_reduce_seg(ctx->d_partials, len, 1, (int64_t)grid * tb_warps(per), nullptr, 1, ctx->d_counter,
+    CU(launch_reduce_seg(ctx->d_partials, len, 1, (int64_t)grid, nullptr, 1, ctx->d_counter,
                          1, ctx->d_out, 0, s));
     CU(launch_advance(ctx->d_counter, len, s));
     *launches += 2;
@@ -766,7 +766,7 @@ int enqueue_tbkpm_chunk(tbpm_ctx *ctx, int len, cudaStream_t s, int64_t *launche
         CU(cudaMemcpyAsync(x0, x1, vb, cudaMemcpyDeviceToDevice, s));
         CU(cudaMemcpyAsync(z0, z1, vb, cudaMemcpyDeviceToDevice, s));
     }
-    CU(launch_reduce_seg(ctx->d_partials, len, 2, (int64_t)grid * tb_kpm_warps(), nullptr, 1, ctx->d_counter, 1,
+    CU(launch_reduce_seg(ctx->d_partials, len, 2, (int64_t)grid, nullptr, 1, ctx->d_counter, 1,
                          ctx->d_out, 0, s));
     CU(launch_advance(ctx->d_counter, len, s));
     *launches += 2;

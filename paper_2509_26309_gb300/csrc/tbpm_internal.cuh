@@ -111,20 +111,18 @@ struct TbParams {
     float2 *ox, *oz;               // the block's newest b and the one before (non-final blocks)
     float2 *psi_out;               // psi(t_{n+1}) (the block holding the final sweep)
     const float2 *psi0;
-    double2 *partials;             // final block: <psi0|psi> partials, slot delta, one per warp
+    double2 *partials;             // final block: <psi0|psi> partials, slot delta, one per block
     int delta;
     const double2 *coef;
     int K, j0, S;
 };
-int tb_warps(int per);             // warps per block (partials per block)
 int tb_tiles(int per, int64_t l1, int64_t l2, int *tiles1, int *tiles2);
 // Opts the kernel in to its shared memory on the current device (before any capture).
 cudaError_t tb_prepare(int per);
 cudaError_t launch_tb_block(int per, const TbParams &p, int grid, cudaStream_t s);
 // The blocked KPM passes (512 threads per block for both lattices): p.S passes
-// from T_{m-1} (bz), T_m (bx), dot partials of slots delta .. delta + S - 1,
-// the last two T's to ox (newest) and oz.
-int tb_kpm_warps();
+// from T_{m-1} (bz), T_m (bx), dot partials of slots delta .. delta + S - 1
+// (one per block), the last two T's to ox (newest) and oz.
 int tb_kpm_tiles(int per, int64_t l1, int64_t l2, int *tiles1, int *tiles2);
 cudaError_t tb_kpm_prepare(int per);
 cudaError_t launch_tb_kpm(int per, const TbParams &p, int grid, cudaStream_t s);
