@@ -308,29 +308,52 @@ cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cuda
 
 // Grid of the KPM kernel: its own occupancy (it holds the dot sums in more
 // registers than the Clenshaw sweeps), whole waves of resident blocks.
+template <typename R>
+static int kpm_occupancy(int op, int *per_sm)
+{
+    cudaError_t e;
+    if (op == OP_STENCIL_MONO)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kpm_b1<R, OP_STENCIL_MONO, true, false>, kBlockB1, 0);
+    else if (op == OP_STENCIL_BI)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kpm_b1<R, OP_STENCIL_BI, true, false>, kBlockB1, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kpm_b1<R, OP_SELL, true, false>, kBlockB1, 0);
+    return e == cudaSuccess ? 0 : 1;
+}
+
 int kpm_grid(const SweepVariant &v, int num_sms)
 {
     int per_sm = 0;
-    cudaError_t e;
-    if (v.precision == TBPM_FP64)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpm_b1<double, OP_SELL, true, false>, kBlockB1, 0);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpm_b1<float, OP_SELL, true, false>, kBlockB1, 0);
-    if (e != cudaSuccess || per_sm < 1) per_sm = 2;
+    const int bad = v.precision == TBPM_FP64 ? kpm_occupancy<double>(v.op, &per_sm)
+                                             : kpm_occupancy<float>(v.op, &per_sm);
+    if (bad || per_sm < 1) per_sm = 2;
     return per_sm * num_sms;
+}
+
+// Grid of the single-state sweeps: whole waves of the middle sweep of this
+// operator (the stencil kernels hold more registers than the SELL ones).
+template <typename R>
+static int middle_sweep_occupancy(int op, int *per_sm)
+{
+    cudaError_t e;
+    if (op == OP_STENCIL_MONO)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            per_sm, sweep_b1<R, OP_STENCIL_MONO, true, B_ONE, false, true, false, false>, kBlockB1, 0);
+    else if (op == OP_STENCIL_BI)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            per_sm, sweep_b1<R, OP_STENCIL_BI, true, B_ONE, false, true, false, false>, kBlockB1, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            per_sm, sweep_b1<R, OP_SELL, true, B_ONE, false, true, false, false>, kBlockB1, 0);
+    return e == cudaSuccess ? 0 : 1;
 }
 
 int sweep_grid(const SweepVariant &v, int num_sms)
 {
     int per_sm = 0;
-    cudaError_t e;
-    if (v.precision == TBPM_FP64)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, sweep_b1<double, OP_SELL, true, B_ONE, false, true, false, false>, kBlockB1, 0);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, sweep_b1<float, OP_SELL, true, B_ONE, false, true, false, false>, kBlockB1, 0);
-    if (e != cudaSuccess || per_sm < 1) per_sm = 4;
+    const int bad = v.precision == TBPM_FP64 ? middle_sweep_occupancy<double>(v.op, &per_sm)
+                                             : middle_sweep_occupancy<float>(v.op, &per_sm);
+    if (bad || per_sm < 1) per_sm = 4;
     return per_sm * num_sms;
 }
 

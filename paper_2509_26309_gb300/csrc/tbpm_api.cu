@@ -1034,6 +1034,9 @@ int tbpm_create_lattice(tbpm_ctx **out, const tbpm_lattice *lat, double rescale,
         } else {
             ctx->path = TBPM_PATH_STENCIL;
             ctx->op = per == 2 ? OP_STENCIL_MONO : OP_STENCIL_BI;
+            // grids in whole waves of this operator's kernels
+            ctx->nblk = sweep_grid(variant(ctx, 1), ctx->num_sms);
+            ctx->nblk_kpm = kpm_grid(variant(ctx, 1), ctx->num_sms);
             ctx->sten.kind = lat->kind;
             ctx->sten.l1 = lat->l1;
             ctx->sten.l2 = lat->l2;
