@@ -143,12 +143,19 @@ __global__ void __launch_bounds__(kBlockB1) sweep_b1(SweepParams p)
             }
         }
     }
-    if (FINAL && !MULTI) {
-        if (kF32) {
-            dr = fr.value();
-            di = fi.value();
-            nn = fn.value();
+    if (FINAL && !MULTI && kF32) {
+        // FP32 data: the block's sums in FP32 pairs, one conversion per value; the
+        // block's first warp slot holds them, its other warp slots zero
+        F2Sum a[3] = {fr, fi, fn};
+        double v[3];
+        block_sum_f2<3>(a, v);
+        if (lane == 0) {
+            const bool lead = (threadIdx.x >> 5) == 0;
+            p.partials[(int64_t)p.delta * nwarps + warp] = lead ? make_double2(v[0], v[1]) : make_double2(0.0, 0.0);
+            if (p.norm_partials)
+                p.norm_partials[(int64_t)p.delta * nwarps + warp] = make_double2(lead ? v[2] : 0.0, 0.0);
         }
+    } else if (FINAL && !MULTI) {
         dr = warp_sum(dr);
         di = warp_sum(di);
         if (lane == 0) p.partials[(int64_t)p.delta * nwarps + warp] = make_double2(dr, di);
@@ -211,9 +218,18 @@ __global__ void __launch_bounds__(kBlockB1, sizeof(R) == 4 ? 3 : 2) kpm_b1(KpmPa
         }
     }
     if (sizeof(R) == 4) {
-        nn = fn.value();
-        cr = fr.value();
-        ci = fi.value();
+        // the block's sums in FP32 pairs, one conversion per value, in the block's
+        // first warp slot (its other warp slots zero)
+        F2Sum a[3] = {fn, fr, fi};
+        double v[3];
+        block_sum_f2<3>(a, v);
+        if (lane == 0) {
+            const bool lead = (threadIdx.x >> 5) == 0;
+            p.partials[((int64_t)p.delta * 2) * nwarps + warp] = make_double2(lead ? v[0] : 0.0, 0.0);
+            p.partials[((int64_t)p.delta * 2 + 1) * nwarps + warp] =
+                lead ? make_double2(v[1], v[2]) : make_double2(0.0, 0.0);
+        }
+        return;
     }
     nn = warp_sum(nn);
     cr = warp_sum(cr);

@@ -89,19 +89,6 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Warp sum of a two-sum pair in FP32 (a butterfly of two-sums); lane 0 holds
-// the warp's result.
-__device__ __forceinline__ void warp_sum_f2(F2Sum &a)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h = __shfl_xor_sync(0xffffffffu, a.hi, o);
-        const float l = __shfl_xor_sync(0xffffffffu, a.lo, o);
-        a.add(h);
-        a.lo = __fadd_rn(a.lo, l);
-    }
-}
-
 // Block sums of NV two-sum pairs (every thread calls it; shared memory sm
 // holds NV * WARPS float2): each warp's lane 0 stores its pairs, then thread
 // v < NV adds the warps' pairs in warp order and returns value v in FP64

@@ -170,6 +170,46 @@ struct F2Sum {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Warp sum of a two-sum pair in FP32 (a butterfly of two-sums); lane 0 holds
+// the warp's result.
+__device__ __forceinline__ void warp_sum_f2(F2Sum &a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h = __shfl_xor_sync(0xffffffffu, a.hi, o);
+        const float l = __shfl_xor_sync(0xffffffffu, a.lo, o);
+        a.add(h);
+        a.lo = __fadd_rn(a.lo, l);
+    }
+}
+
+// Block sum of NV two-sum pairs for blocks of kBlockB1 threads, in FP32 up to
+// one FP64 conversion per value; the results are valid in thread 0. Every
+// thread of the block calls it.
+template <int NV>
+__device__ __forceinline__ void block_sum_f2(F2Sum (&a)[NV], double (&out)[NV])
+{
+    __shared__ float2 sm[NV][kBlockB1 / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        warp_sum_f2(a[v]);
+        if (lane == 0) sm[v][w] = make_float2(a[v].hi, a[v].lo);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            F2Sum t;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+                t.add(sm[v][i].x);
+                t.lo = __fadd_rn(t.lo, sm[v][i].y);
+            }
+            out[v] = t.value();
+        }
+    }
+}
+
 // Warp-wide sum in a fixed butterfly order; every lane gets the result.
 __device__ __forceinline__ double warp_sum(double v)
 {
