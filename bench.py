@@ -262,8 +262,7 @@ def run_ours(args, rank, world, local_rank):
     # FINAL 16 (update 12 + the <psi0|psi> dot 4)
     ops_step_row = 12 + 10 + (K - 4) * 10 + 16
     flops_per_sweep = 2.0 * n * ops_step_row / (K - 1)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    hbm = float(peaks["hbm_gbs"])
+    hbm, hbm_source = measured_hbm()
     fp64_peak = 2 * 152 * 2.07e9 * 2 / 1e12      # 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2
     tflops = flops_per_sweep / sweep_s / 1e12
     gbs = bytes_per_sweep / sweep_s / 1e9
@@ -275,7 +274,7 @@ def run_ours(args, rank, world, local_rank):
                 "flops_per_sweep": round(flops_per_sweep), "sweep_us": round(sweep_s * 1e6, 2),
                 "hbm": {"achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                         "frac": round(gbs / hbm, 4), "bytes_per_sweep": round(bytes_per_sweep),
-                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}}
+                        "peak_source": hbm_source}}
 
     # e2e: the same step through the public API with pinned host buffers,
     # H2D of psi0 and D2H of every result inside the timed region
@@ -356,10 +355,20 @@ def dos_l1(ctx, corr, ref, dt):
     return float(np.sum(np.abs(d - r)) / np.sum(np.abs(r)))
 
 
+def measured_hbm():
+    """(GB/s, source): the measured copy bandwidth of the GB300s, or the
+    earlier single measurement the profiling recipe gives as its fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), \
+            "MEASURED_PEAKS.json hbm_gbs (measured)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
 def hbm_roof(units_per_s, bytes_per_unit, basis):
     """HBM roofline of a variant: algorithmic bytes per unit (orbital-term or
     orbital-term-state) x units/s against the measured copy bandwidth."""
-    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    peak = measured_hbm()[0]
     gbs = units_per_s * bytes_per_unit / 1e9
     return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
             "bytes_per_unit": bytes_per_unit, "basis": basis}
