@@ -92,9 +92,10 @@ def test_bilayer_disorder_and_phases(orc):
     assert np.max(np.abs(c - orc.dos_corr(hp, 9.0, psi0, DT, 256))) <= TOL
 
 
-@pytest.mark.parametrize("dt", [1e-7, 1e-5, 2e-4, 2e-3, 0.05, -DT, 2 * DT, 30.0 / 9.0])
+@pytest.mark.parametrize("dt", [1e-7, 1e-5, 2e-4, 2e-3, 0.05, -DT, 2 * DT, 30.0 / 9.0, 40.0 / 9.0])
 def test_term_counts_and_signs(orc, dt):
-    """Small x gives K = 3 or 4 (the short Clenshaw forms); negative dt runs backwards."""
+    """Small x gives K = 3 or 4 (the short Clenshaw forms); negative dt runs backwards;
+    x = 40 is the largest step the library accepts."""
     h = ti.graphene_csr(9, 7, onsite=ti.anderson_onsite(126, 1.0, 4))
     psi0 = ti.random_phase_state(h.n, 5)
     ctx = create(h)
@@ -103,6 +104,17 @@ def test_term_counts_and_signs(orc, dt):
     K_orc = orc.cheb_num_terms(abs(dt) * 9.0)
     assert tb.tbpm_get_info(ctx)["num_terms"] == max(K_orc, 3)
     assert np.max(np.abs(c - ref)) <= TOL
+
+
+def test_step_beyond_the_coefficient_table_is_rejected():
+    """|dt * rescale| > 40 would need more terms than the device table holds."""
+    h = ti.graphene_csr(9, 7)
+    psi0 = ti.random_phase_state(h.n, 5)
+    ctx = create(h)
+    with pytest.raises(tb.TbpmError) as e:
+        tb.tbpm_dos_corr(ctx, psi0, 41.0 / 9.0, 2)
+    assert e.value.status == tb.TBPM_ERR_ARG
+    assert np.all(np.isfinite(tb.tbpm_dos_corr(ctx, psi0, 40.0 / 9.0, 2)))
 
 
 def test_zero_steps_and_multistate(orc):
