@@ -56,7 +56,23 @@ __device__ __forceinline__ void apply_row(const SweepParams &p, int64_t s, int r
         const int64_t off = __ldg(p.slice_off + s);
         const int w = (int)((__ldg(p.slice_off + s + 1) - off) >> 5);
         const int32_t *cp = p.cols + off + r_in_slice;
-        if (REALV) {
+        if (REALV && (w == 3 || w == 4)) {
+            // monolayer / bilayer rows: every column and value load first, then
+            // the gathers, then the FMAs (one dependent round trip, not one per pair)
+            const float *vp = reinterpret_cast<const float *>(p.vals) + off + r_in_slice;
+            int c[4];
+            float v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < w) { c[j] = __ldg(cp + 32 * j); v[j] = __ldg(vp + 32 * j); }
+            C2 xv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < w) xv[j] = ld4(x, c[j], pair);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < w) fma4(v[j], xv[j], acc);
+        } else if (REALV) {
             const float *vp = reinterpret_cast<const float *>(p.vals) + off + r_in_slice;
             int j = 0;
             for (; j + 2 <= w; j += 2) {
