@@ -64,6 +64,21 @@ __device__ __forceinline__ void gather_row(const ClusterParams &p, const MatView
         w = (int)((__ldg(p.slice_off + s + 1) - off) >> 5);
     }
     const int mask = (1 << p.log_rows) - 1;
+    if (REALV && w == 3) {
+        // monolayer rows: the columns, then the three remote loads, then the FMAs,
+        // so the distributed-shared-memory round trips overlap
+        const int64_t e = off + lane;
+        const int c0 = m.cols[e], c1 = m.cols[e + 32], c2 = m.cols[e + 64];
+        const R *vr = reinterpret_cast<const R *>(m.vals);
+        const R v0 = vr[e], v1 = vr[e + 32], v2 = vr[e + 64];
+        const V x0 = cl.map_shared_rank(xs, (unsigned)(c0 >> p.log_rows))[c0 & mask];
+        const V x1 = cl.map_shared_rank(xs, (unsigned)(c1 >> p.log_rows))[c1 & mask];
+        const V x2 = cl.map_shared_rank(xs, (unsigned)(c2 >> p.log_rows))[c2 & mask];
+        ar = fma(v0, x0.x, ar); ai = fma(v0, x0.y, ai);
+        ar = fma(v1, x1.x, ar); ai = fma(v1, x1.y, ai);
+        ar = fma(v2, x2.x, ar); ai = fma(v2, x2.y, ai);
+        return;
+    }
     for (int j = 0; j < w; ++j) {
         const int c = m.cols[off + 32 * j + lane];
         const V *rx = cl.map_shared_rank(xs, (unsigned)(c >> p.log_rows));
