@@ -43,7 +43,10 @@ extern "C" {
 #define TBPM_ERR_RESCALE       -4  /* rescale below the Gershgorin bound of H     */
 #define TBPM_ERR_OOM           -5  /* device or host allocation failed            */
 #define TBPM_ERR_CUDA          -6  /* a CUDA runtime call failed                  */
-#define TBPM_ERR_TIMEOUT       -7  /* a bounded device wait gave up               */
+#define TBPM_ERR_TIMEOUT       -7  /* a bounded device wait gave up (reserved: no
+                                       kernel of this library waits on a flag; all
+                                       device-side waits are block or cluster
+                                       barriers)                                  */
 #define TBPM_ERR_NO_DEVICE     -8  /* no usable sm_103 GPU                         */
 #define TBPM_ERR_UNSUPPORTED   -9  /* valid request this build does not serve     */
 
