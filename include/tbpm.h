@@ -375,6 +375,13 @@ int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info);
 /* A static, human-readable name for a status code. */
 const char *tbpm_strerror(int status);
 
+/* The detail of the context's most recent failure: the failing CUDA call with
+ * CUDA's message, or for some rejected requests (no current operators, a Fermi
+ * series beyond TBPM_FERMI_MAX_TERMS) what was wrong; "" if nothing was
+ * recorded. Owned by the context, valid until its next failure or
+ * tbpm_destroy. NULL ctx gives "". */
+const char *tbpm_last_error(const tbpm_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

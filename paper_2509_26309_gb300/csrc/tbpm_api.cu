@@ -1912,6 +1912,11 @@ int tbpm_ac_cond(tbpm_ctx *ctx, const double *corr, int n_steps, double dt, doub
     return TBPM_OK;
 }
 
+const char *tbpm_last_error(const tbpm_ctx *ctx)
+{
+    return ctx ? ctx->last_error.c_str() : "";
+}
+
 int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info)
 {
     if (!ctx || !info) return TBPM_ERR_ARG;

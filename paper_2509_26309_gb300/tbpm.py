@@ -81,6 +81,7 @@ SIGNATURES = {
     "kpm_dos_jackson": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "tbpm_get_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tbpm_strerror": (C.c_char_p, [C.c_int]),
+    "tbpm_last_error": (C.c_char_p, [C.c_void_p]),
     "tbpm_propagate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p,
                                  C.c_void_p]),
     "tbpm_haydock": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
@@ -429,6 +430,11 @@ def tbpm_ac_cond(ctx: Ctx, corr, dt: float, beta: float, area: float, omegas):
     _check(lib().tbpm_ac_cond(ctx.handle, _ptr(corr), n_steps, float(dt), float(beta), float(area), _ptr(omegas),
                               n_w, _ptr(out)), "tbpm_ac_cond")
     return out
+
+
+def tbpm_last_error(ctx: Ctx) -> str:
+    """The detail of the context's last failure ("" if none)."""
+    return lib().tbpm_last_error(ctx.handle).decode()
 
 
 def tbpm_get_info(ctx: Ctx) -> dict:

@@ -40,6 +40,7 @@ def test_statuses_have_names():
     for s in range(0, -10, -1):
         assert tb.tbpm_strerror(s) != "unknown status"
     assert tb.tbpm_strerror(-99) == "unknown status"
+    assert B.lib().tbpm_last_error(None) == b""
 
 
 def _h():

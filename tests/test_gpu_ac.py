@@ -121,10 +121,12 @@ def test_ac_errors():
     with pytest.raises(tb.TbpmError) as e:
         tb.tbpm_ac_corr(ctx, psi0, 5.0, 0.0, 0.3, 4)              # no current operators
     assert e.value.status == tb.TBPM_ERR_ARG
+    assert "tbpm_set_current" in tb.tbpm_last_error(ctx)
     tb.tbpm_set_current(ctx, *cur.as_tuple())
     with pytest.raises(tb.TbpmError) as e:
         tb.tbpm_ac_corr(ctx, psi0, 5000.0, 0.0, 0.3, 4)           # Fermi series too long
     assert e.value.status == tb.TBPM_ERR_ARG
+    assert "TBPM_FERMI_MAX_TERMS" in tb.tbpm_last_error(ctx)
     bad = cur.jx.copy()
     bad[0] += 0.5                                                  # breaks J_x = J_x^dagger
     with pytest.raises(tb.TbpmError) as e:
