@@ -263,7 +263,7 @@ def run_ours(args, rank, world, local_rank):
     ops_step_row = 12 + 10 + (K - 4) * 10 + 16
     flops_per_sweep = 2.0 * n * ops_step_row / (K - 1)
     hbm, hbm_source = measured_hbm()
-    fp64_peak = 2 * 152 * 2.07e9 * 2 / 1e12      # 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2
+    fp64_peak = FP64_PEAK_TFLOPS
     tflops = flops_per_sweep / sweep_s / 1e12
     gbs = bytes_per_sweep / sweep_s / 1e9
     roofline = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(fp64_peak, 4),
@@ -374,6 +374,17 @@ def hbm_roof(units_per_s, bytes_per_unit, basis):
             "bytes_per_unit": bytes_per_unit, "basis": basis}
 
 
+FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12   # 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2
+
+
+def alu_roof(units_per_s, fp64_ops_per_unit):
+    """FP64-pipe roofline of a variant: FP64 operations (FMA, MUL or ADD, one
+    issue slot each, 2 flops) per unit x units/s against the pipe's peak."""
+    tf = units_per_s * fp64_ops_per_unit * 2 / 1e12
+    return {"bound": "alu", "achieved": round(tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+            "frac": round(tf / FP64_PEAK_TFLOPS, 4), "fp64_ops_per_unit": fp64_ops_per_unit}
+
+
 # algorithmic bytes per orbital-term of a middle sweep (FP32, real hoppings):
 # three stored hoppings (int32 column + FP32 value), FP32 diagonal, slice
 # offset; four vector streams (gathered operand, psi, b_{k+2}, output) of 8 B
@@ -404,7 +415,9 @@ def run_variants(args, dev, stream):
       - FP32 single state on that stencil and on an AB-bilayer stencil of as many
         orbitals, temporally blocked vs one launch per sweep, and 512 KPM moments
         blocked vs one launch per pass;
-      - the AC current correlation on graphene 1024x1024 (W = 1) at 300 K.
+      - the AC current correlation on graphene 1024x1024 (W = 1) at 300 K;
+      - on that lattice and operator, the time-dependent wave function, the
+        quasi-eigenstates and the Haydock recursion (FP64).
     The FP64 runs the errors are taken against are the path the parity tests
     hold to 1e-10 of the oracle."""
     import numpy as np
@@ -601,6 +614,29 @@ def run_variants(args, dev, stream):
     res["fp64_ac_corr_1024x1024"] = {"value": n2 * sweeps / (msac / 1e3), "unit": UNIT, "ms_per_call": msac,
                                      "n_steps": 64, "fermi_terms": info["fermi_terms"], "beta": beta,
                                      "sweeps": sweeps}
+    # the same lattice and operator for the other propagation products: the
+    # time-dependent wave function (psi(t) returned after 64 steps), the
+    # quasi-eigenstates (64 steps forward and 64 backward, 4 energies, one FP64
+    # accumulation pass per step) and the Haydock recursion (2048 levels)
+    K = info["num_terms"]
+    msw = timed_calls(lambda: tb.tbpm_propagate(cac, pac, DT, 64), 2, stream)
+    res["fp64_wft_1024x1024"] = {"value": n2 * 64 * (K - 1) / (msw / 1e3), "unit": UNIT, "ms_per_call": msw,
+                                 "n_steps": 64}
+    eq = np.array([-2.0, -0.5, 0.5, 2.0])
+    msq = timed_calls(lambda: tb.tbpm_quasi_eigenstates(cac, pac, DT, 64, eq), 2, stream)
+    res["fp64_quasi_eigenstates_1024x1024"] = {"value": n2 * 2 * 64 * (K - 1) / (msq / 1e3), "unit": UNIT,
+                                               "ms_per_call": msq, "n_steps": 64, "energies": int(eq.size)}
+    lv = 2048
+    msh = timed_calls(lambda: tb.tbpm_haydock(cac, pac, lv), 2, stream)
+    rate = n2 * lv / (msh / 1e3)
+    # per orbital and level: the product pass (3 hoppings: int32 column + FP64
+    # value, FP64 diagonal, slice offsets; u_n gathered, u_{n-1} read, w
+    # written) and the update pass (u_n, w read, u_{n+1} written); FP64
+    # operations 14 (product 12, Re <u_n|w> 2) + 4 (update 2, norm 2)
+    res["fp64_haydock_1024x1024"] = {"value": rate, "unit": "orbital-levels/s", "ms_per_call": msh, "levels": lv,
+                                     "roofline": dict(alu_roof(rate, 18),
+                                                      hbm=hbm_roof(rate, 3 * 12 + 8 + 0.5 + 48 + 48,
+                                                                   "product + update pass per level"))}
     tb.tbpm_destroy(cac)
     return res
 

@@ -79,6 +79,13 @@ extern "C" {
                                           launches (several sweeps per pass over a
                                           lattice tile in shared memory); this flag
                                           keeps one launch per sweep instead       */
+#define TBPM_F_NO_PDL             0x40u /* launch the single-state sweeps in plain
+                                          stream order. By default each one is a
+                                          programmatic dependent launch: its blocks
+                                          are scheduled while the previous sweep's
+                                          last blocks run and wait in hardware for
+                                          that sweep to complete before touching
+                                          any vector; results are identical      */
 
 typedef struct tbpm_opts {
     int precision;       /* TBPM_FP64 | TBPM_FP32                                  */
@@ -209,7 +216,9 @@ int tbpm_propagate(tbpm_ctx *ctx, const double *psi0, int nstates, double dt, in
  * polynomial method named in Sec. 1), written as complex numbers to
  * mu[j*M + m]. The GPU uses the product identities
  *   mu_{2m} = 2<T_m|T_m> - mu_0,  mu_{2m+1} = 2<T_{m+1}|T_m> - mu_1
- * (T_m = T_m(H~) psi0), so about M/2 matrix products are made.
+ * (T_m = T_m(H~) psi0), so about M/2 matrix products are made. The moments
+ * of a Hermitian H are real: their imaginary parts are zero, or of rounding
+ * size where a path forms them.
  *   psi0  as tbpm_dos_corr;  M >= 1. */
 int kpm_moments(tbpm_ctx *ctx, const double *psi0, int nstates, int M, double *mu);
 

@@ -31,6 +31,40 @@ namespace {
 
 enum BMode { B_ONE = 0, B_REAL = 1, B_IMAG = 2 };
 
+// Programmatic dependent launch (sm_90 and later). A grid launched with the
+// programmatic-serialisation attribute may be scheduled once every block of the
+// previous kernel in the stream has started and released it; griddepcontrol.wait
+// then blocks until that kernel has completed and its writes are visible. The
+// single-state sweeps wait before their first memory access and release at
+// once, so the next sweep's blocks take each SM as this sweep's blocks leave it
+// and start the moment it completes. For a plain launch both instructions do
+// nothing.
+__device__ __forceinline__ void pdl_wait_release()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename P>
+cudaError_t launch_b1(void (*kern)(P), int grid, bool pdl, cudaStream_t s, const P &p)
+{
+    if (!pdl) {
+        kern<<<grid, kBlockB1, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kBlockB1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
 // Coefficients of one sweep: a on psi (real, or imaginary if AIMAG), beta on A x.
 // For a batch of instances, coefficients and the renormalisation scale are
 // those of the slice's instance.
@@ -70,6 +104,7 @@ template <typename R, int OP, bool REALV, int BM, bool AIMAG, bool HASZ, bool FI
 __global__ void __launch_bounds__(kBlockB1) sweep_b1(SweepParams p)
 {
     typedef typename V2<R>::T V;
+    pdl_wait_release();
     R a, beta;
     sweep_coeffs<R, BM, AIMAG>(p, 0, a, beta);
 
@@ -167,12 +202,16 @@ __global__ void __launch_bounds__(kBlockB1) sweep_b1(SweepParams p)
 }
 
 // KPM sweep for B = 1: y = scale * (A x) - [!first] y. Per lane FP64 sums of
-// <x|x> and <y|x> over the warp's slices, reduced once per warp into
-// partials[(2 delta + 0/1) * W + warp].
+// <x|x> and Re <y|x> over the warp's slices, reduced once per warp into
+// partials[(2 delta + 0/1) * W + warp]. With x = T_m psi0 and y = T_{m+1} psi0,
+// <y|x> = <psi0|T_{m+1}(H~) T_m(H~)|psi0> is real for Hermitian H (a real
+// polynomial of H~ between the same state), so its imaginary part is stored
+// as zero instead of costing two more FP64 operations per row.
 template <typename R, int OP, bool REALV, bool FIRST>
 __global__ void __launch_bounds__(kBlockB1, sizeof(R) == 4 ? 3 : 2) kpm_b1(KpmParams p)
 {
     typedef typename V2<R>::T V;
+    pdl_wait_release();
     SweepParams sp;                     // operator fields for the shared helpers
     sp.n = p.n; sp.nslices = p.nslices; sp.slice_off = p.slice_off; sp.cols = p.cols; sp.vals = p.vals;
     sp.diag = p.diag; sp.l1 = p.l1; sp.l2 = p.l2; sp.t = p.t; sp.t_perp = p.t_perp;
@@ -183,8 +222,8 @@ __global__ void __launch_bounds__(kBlockB1, sizeof(R) == 4 ? 3 : 2) kpm_b1(KpmPa
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double nn = 0.0, cr = 0.0, ci = 0.0;
-    F2Sum fn, fr, fi;                   // FP32 data: the same sums on the FP32 pipe
+    double nn = 0.0, cr = 0.0;
+    F2Sum fn, fr;                       // FP32 data: the same sums on the FP32 pipe
     for (int64_t s = warp; s < p.nslices; s += nwarps) {
         const int64_t row = (s << 5) + lane;
         const V xi = __ldg(x + row);
@@ -207,70 +246,60 @@ __global__ void __launch_bounds__(kBlockB1, sizeof(R) == 4 ? 3 : 2) kpm_b1(KpmPa
         if (sizeof(R) == 4) {
             fn.add_dot((float)xi.x, (float)xi.x, (float)xi.y, (float)xi.y);
             fr.add_dot((float)out.x, (float)xi.x, (float)out.y, (float)xi.y);
-            fi.add_dot((float)out.x, (float)xi.y, -(float)out.y, (float)xi.x);
         } else {
             const double xr = (double)xi.x, xim = (double)xi.y;
             const double orr = (double)out.x, oi = (double)out.y;
             nn = fma(xr, xr, fma(xim, xim, nn));
-            // <y|x> = sum conj(y) x
-            cr = fma(orr, xr, fma(oi, xim, cr));
-            ci = fma(orr, xim, fma(-oi, xr, ci));
+            cr = fma(orr, xr, fma(oi, xim, cr));        // Re sum conj(y) x
         }
     }
     if (sizeof(R) == 4) {
         // the block's sums in FP32 pairs, one conversion per value, in the block's
         // first warp slot (its other warp slots zero)
-        F2Sum a[3] = {fn, fr, fi};
-        double v[3];
-        block_sum_f2<3>(a, v);
+        F2Sum a[2] = {fn, fr};
+        double v[2];
+        block_sum_f2<2>(a, v);
         if (lane == 0) {
             const bool lead = (threadIdx.x >> 5) == 0;
             p.partials[((int64_t)p.delta * 2) * nwarps + warp] = make_double2(lead ? v[0] : 0.0, 0.0);
-            p.partials[((int64_t)p.delta * 2 + 1) * nwarps + warp] =
-                lead ? make_double2(v[1], v[2]) : make_double2(0.0, 0.0);
+            p.partials[((int64_t)p.delta * 2 + 1) * nwarps + warp] = make_double2(lead ? v[1] : 0.0, 0.0);
         }
         return;
     }
     nn = warp_sum(nn);
     cr = warp_sum(cr);
-    ci = warp_sum(ci);
     if (lane == 0) {
         p.partials[((int64_t)p.delta * 2) * nwarps + warp] = make_double2(nn, 0.0);
-        p.partials[((int64_t)p.delta * 2 + 1) * nwarps + warp] = make_double2(cr, ci);
+        p.partials[((int64_t)p.delta * 2 + 1) * nwarps + warp] = make_double2(cr, 0.0);
     }
 }
 
 template <typename R, int OP, bool REALV, bool MULTI>
 cudaError_t sweep_dispatch(SweepKind kind, bool a_imag, bool has_z, const SweepParams &p,
-                           int grid, cudaStream_t s)
+                           int grid, bool pdl, cudaStream_t s)
 {
     switch (kind) {
     case SW_FIRST:
-        if (a_imag) sweep_b1<R, OP, REALV, B_REAL, true, false, false, MULTI><<<grid, kBlockB1, 0, s>>>(p);
-        else sweep_b1<R, OP, REALV, B_IMAG, false, false, false, MULTI><<<grid, kBlockB1, 0, s>>>(p);
-        break;
+        return a_imag ? launch_b1(sweep_b1<R, OP, REALV, B_REAL, true, false, false, MULTI>, grid, pdl, s, p)
+                      : launch_b1(sweep_b1<R, OP, REALV, B_IMAG, false, false, false, MULTI>, grid, pdl, s, p);
     case SW_SECOND:
-        if (a_imag) sweep_b1<R, OP, REALV, B_ONE, true, false, false, MULTI><<<grid, kBlockB1, 0, s>>>(p);
-        else sweep_b1<R, OP, REALV, B_ONE, false, false, false, MULTI><<<grid, kBlockB1, 0, s>>>(p);
-        break;
+        return a_imag ? launch_b1(sweep_b1<R, OP, REALV, B_ONE, true, false, false, MULTI>, grid, pdl, s, p)
+                      : launch_b1(sweep_b1<R, OP, REALV, B_ONE, false, false, false, MULTI>, grid, pdl, s, p);
     case SW_MID:
-        if (a_imag) sweep_b1<R, OP, REALV, B_ONE, true, true, false, MULTI><<<grid, kBlockB1, 0, s>>>(p);
-        else sweep_b1<R, OP, REALV, B_ONE, false, true, false, MULTI><<<grid, kBlockB1, 0, s>>>(p);
-        break;
+        return a_imag ? launch_b1(sweep_b1<R, OP, REALV, B_ONE, true, true, false, MULTI>, grid, pdl, s, p)
+                      : launch_b1(sweep_b1<R, OP, REALV, B_ONE, false, true, false, MULTI>, grid, pdl, s, p);
     case SW_FINAL:
-        if (has_z) sweep_b1<R, OP, REALV, B_REAL, false, true, true, MULTI><<<grid, kBlockB1, 0, s>>>(p);
-        else sweep_b1<R, OP, REALV, B_REAL, false, false, true, MULTI><<<grid, kBlockB1, 0, s>>>(p);
-        break;
+        return has_z ? launch_b1(sweep_b1<R, OP, REALV, B_REAL, false, true, true, MULTI>, grid, pdl, s, p)
+                     : launch_b1(sweep_b1<R, OP, REALV, B_REAL, false, false, true, MULTI>, grid, pdl, s, p);
     }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 template <typename R, int OP, bool REALV>
-cudaError_t kpm_dispatch(const KpmParams &p, int grid, cudaStream_t s)
+cudaError_t kpm_dispatch(const KpmParams &p, int grid, bool pdl, cudaStream_t s)
 {
-    if (p.first) kpm_b1<R, OP, REALV, true><<<grid, kBlockB1, 0, s>>>(p);
-    else kpm_b1<R, OP, REALV, false><<<grid, kBlockB1, 0, s>>>(p);
-    return cudaGetLastError();
+    return p.first ? launch_b1(kpm_b1<R, OP, REALV, true>, grid, pdl, s, p)
+                   : launch_b1(kpm_b1<R, OP, REALV, false>, grid, pdl, s, p);
 }
 
 }  // namespace
@@ -284,25 +313,25 @@ cudaError_t launch_sweep(const SweepVariant &v, SweepKind kind, bool a_imag, boo
     if (v.precision == TBPM_FP64) {
         if (v.op == OP_SELL) {
             if (multi)
-                return v.real_values ? sweep_dispatch<double, OP_SELL, true, true>(kind, a_imag, has_z, p, grid, s)
-                                     : sweep_dispatch<double, OP_SELL, false, true>(kind, a_imag, has_z, p, grid, s);
-            return v.real_values ? sweep_dispatch<double, OP_SELL, true, false>(kind, a_imag, has_z, p, grid, s)
-                                 : sweep_dispatch<double, OP_SELL, false, false>(kind, a_imag, has_z, p, grid, s);
+                return v.real_values ? sweep_dispatch<double, OP_SELL, true, true>(kind, a_imag, has_z, p, grid, v.pdl, s)
+                                     : sweep_dispatch<double, OP_SELL, false, true>(kind, a_imag, has_z, p, grid, v.pdl, s);
+            return v.real_values ? sweep_dispatch<double, OP_SELL, true, false>(kind, a_imag, has_z, p, grid, v.pdl, s)
+                                 : sweep_dispatch<double, OP_SELL, false, false>(kind, a_imag, has_z, p, grid, v.pdl, s);
         }
         if (v.op == OP_STENCIL_MONO)
-            return sweep_dispatch<double, OP_STENCIL_MONO, true, false>(kind, a_imag, has_z, p, grid, s);
-        return sweep_dispatch<double, OP_STENCIL_BI, true, false>(kind, a_imag, has_z, p, grid, s);
+            return sweep_dispatch<double, OP_STENCIL_MONO, true, false>(kind, a_imag, has_z, p, grid, v.pdl, s);
+        return sweep_dispatch<double, OP_STENCIL_BI, true, false>(kind, a_imag, has_z, p, grid, v.pdl, s);
     }
     if (v.op == OP_SELL) {
         if (multi)
-            return v.real_values ? sweep_dispatch<float, OP_SELL, true, true>(kind, a_imag, has_z, p, grid, s)
-                                 : sweep_dispatch<float, OP_SELL, false, true>(kind, a_imag, has_z, p, grid, s);
-        return v.real_values ? sweep_dispatch<float, OP_SELL, true, false>(kind, a_imag, has_z, p, grid, s)
-                             : sweep_dispatch<float, OP_SELL, false, false>(kind, a_imag, has_z, p, grid, s);
+            return v.real_values ? sweep_dispatch<float, OP_SELL, true, true>(kind, a_imag, has_z, p, grid, v.pdl, s)
+                                 : sweep_dispatch<float, OP_SELL, false, true>(kind, a_imag, has_z, p, grid, v.pdl, s);
+        return v.real_values ? sweep_dispatch<float, OP_SELL, true, false>(kind, a_imag, has_z, p, grid, v.pdl, s)
+                             : sweep_dispatch<float, OP_SELL, false, false>(kind, a_imag, has_z, p, grid, v.pdl, s);
     }
     if (v.op == OP_STENCIL_MONO)
-        return sweep_dispatch<float, OP_STENCIL_MONO, true, false>(kind, a_imag, has_z, p, grid, s);
-    return sweep_dispatch<float, OP_STENCIL_BI, true, false>(kind, a_imag, has_z, p, grid, s);
+        return sweep_dispatch<float, OP_STENCIL_MONO, true, false>(kind, a_imag, has_z, p, grid, v.pdl, s);
+    return sweep_dispatch<float, OP_STENCIL_BI, true, false>(kind, a_imag, has_z, p, grid, v.pdl, s);
 }
 
 cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cudaStream_t s)
@@ -310,16 +339,16 @@ cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cuda
     if (v.states != 1) return cudaErrorInvalidValue;
     if (v.precision == TBPM_FP64) {
         if (v.op == OP_SELL)
-            return v.real_values ? kpm_dispatch<double, OP_SELL, true>(p, grid, s)
-                                 : kpm_dispatch<double, OP_SELL, false>(p, grid, s);
-        if (v.op == OP_STENCIL_MONO) return kpm_dispatch<double, OP_STENCIL_MONO, true>(p, grid, s);
-        return kpm_dispatch<double, OP_STENCIL_BI, true>(p, grid, s);
+            return v.real_values ? kpm_dispatch<double, OP_SELL, true>(p, grid, v.pdl, s)
+                                 : kpm_dispatch<double, OP_SELL, false>(p, grid, v.pdl, s);
+        if (v.op == OP_STENCIL_MONO) return kpm_dispatch<double, OP_STENCIL_MONO, true>(p, grid, v.pdl, s);
+        return kpm_dispatch<double, OP_STENCIL_BI, true>(p, grid, v.pdl, s);
     }
     if (v.op == OP_SELL)
-        return v.real_values ? kpm_dispatch<float, OP_SELL, true>(p, grid, s)
-                             : kpm_dispatch<float, OP_SELL, false>(p, grid, s);
-    if (v.op == OP_STENCIL_MONO) return kpm_dispatch<float, OP_STENCIL_MONO, true>(p, grid, s);
-    return kpm_dispatch<float, OP_STENCIL_BI, true>(p, grid, s);
+        return v.real_values ? kpm_dispatch<float, OP_SELL, true>(p, grid, v.pdl, s)
+                             : kpm_dispatch<float, OP_SELL, false>(p, grid, v.pdl, s);
+    if (v.op == OP_STENCIL_MONO) return kpm_dispatch<float, OP_STENCIL_MONO, true>(p, grid, v.pdl, s);
+    return kpm_dispatch<float, OP_STENCIL_BI, true>(p, grid, v.pdl, s);
 }
 
 // Grid of the KPM kernel: its own occupancy (it holds the dot sums in more

@@ -296,6 +296,7 @@ SweepVariant variant(const tbpm_ctx *ctx, int states)
     v.op = ctx->op;
     v.real_values = ctx->op == OP_SELL ? ctx->sell.real_values : true;
     v.states = states;
+    v.pdl = !(ctx->flags & TBPM_F_NO_PDL);
     return v;
 }
 
@@ -879,7 +880,7 @@ static int check_opts(const tbpm_opts *in, tbpm_opts *o)
     if (o->precision != TBPM_FP64 && o->precision != TBPM_FP32) return TBPM_ERR_ARG;
     if (o->path < TBPM_PATH_AUTO || o->path > TBPM_PATH_STENCIL) return TBPM_ERR_ARG;
     if (o->flags & ~(unsigned)(TBPM_F_NO_HERMITIAN_CHECK | TBPM_F_FORCE_RESCALE | TBPM_F_RENORM |
-                               TBPM_F_NO_CLUSTER | TBPM_F_AUTOTUNE | TBPM_F_NO_TBLOCK))
+                               TBPM_F_NO_CLUSTER | TBPM_F_AUTOTUNE | TBPM_F_NO_TBLOCK | TBPM_F_NO_PDL))
         return TBPM_ERR_ARG;
     if (o->bessel_tol == 0.0) o->bessel_tol = 1e-12;
     if (!(o->bessel_tol > 0.0 && o->bessel_tol < 1e-2)) return TBPM_ERR_ARG;

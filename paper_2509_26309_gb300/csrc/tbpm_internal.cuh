@@ -154,6 +154,7 @@ struct SweepVariant {
     int op;                       // OpKind
     bool real_values;
     int states;                   // B: 1 or 16
+    bool pdl;                     // B = 1 sweeps as programmatic dependent launches
 };
 
 // ---------------------------------------------------------------- context

@@ -38,6 +38,7 @@ TBPM_F_RENORM = 0x4
 TBPM_F_NO_CLUSTER = 0x8
 TBPM_F_AUTOTUNE = 0x10
 TBPM_F_NO_TBLOCK = 0x20
+TBPM_F_NO_PDL = 0x40
 TBPM_LATTICE_GRAPHENE = 0
 TBPM_LATTICE_AB_BILAYER = 1
 

@@ -256,3 +256,41 @@ def test_torch_device_buffers(orc):
     torch.cuda.synchronize()
     er, dr, _ = orc.dos_hann(hc[0], DT)
     assert np.max(np.abs(d.cpu().numpy() - dr)) < 1e-12
+
+
+@pytest.mark.parametrize("prec,flags,path", [
+    (tb.TBPM_FP64, 0, tb.TBPM_PATH_AUTO),
+    (tb.TBPM_FP32, tb.TBPM_F_RENORM, tb.TBPM_PATH_AUTO),
+    (tb.TBPM_FP64, 0, tb.TBPM_PATH_STENCIL),
+])
+def test_programmatic_launch_changes_nothing(orc, prec, flags, path):
+    """The single-state sweeps as programmatic dependent launches (the default)
+    and in plain stream order: bit-identical correlations, moments, propagated
+    states and quasi-eigenstates, and the FP64 results within the tolerance of
+    the oracle."""
+    l1, l2 = 96, 70
+    n = 2 * l1 * l2
+    eps = ti.anderson_onsite(n, 1.0, 6)
+    h = ti.graphene_csr(l1, l2, onsite=eps)
+    psi0 = ti.random_phase_state(n, 3)
+    ctxs = []
+    for extra in (0, tb.TBPM_F_NO_PDL):
+        o = tb.make_opts(precision=prec, path=path, flags=flags | extra | tb.TBPM_F_NO_CLUSTER)
+        if path == tb.TBPM_PATH_STENCIL:
+            ctxs.append(tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, l1, l2, ti.T_GRAPHENE, 0.0, eps, 9.0, o))
+        else:
+            ctxs.append(tb.tbpm_create(n, h.row_ptr, h.col, h.val, 9.0, o))
+    res = []
+    for c in ctxs:
+        corr = tb.tbpm_dos_corr(c, psi0, DT, 40)
+        mu = tb.kpm_moments(c, psi0, 64)
+        psi = tb.tbpm_propagate(c, psi0, DT, 7)
+        r = [corr, mu, psi]
+        if flags == 0:
+            r.append(tb.tbpm_quasi_eigenstates(c, psi0, DT, 5, np.array([-1.0, 0.3])))
+        res.append(r)
+    for x, y in zip(*res):
+        assert np.array_equal(x, y)
+    if prec == tb.TBPM_FP64:
+        assert np.max(np.abs(res[0][0] - orc.dos_corr(h, 9.0, psi0, DT, 40))) <= TOL
+        assert np.max(np.abs(res[0][1] - orc.kpm_moments(h, 9.0, psi0, 64))) <= TOL
