@@ -229,7 +229,22 @@ __global__ void qe_accumulate_kernel(const void *psi_, double2 *Q, const double 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += stride) {
         const V v = psi[i];
         const double vr = (double)v.x, vi = (double)v.y;
-        for (int e = 0; e < n_e; ++e) {
+        // four energies at a time: their loads issue together (the stores of
+        // one energy would otherwise hold back the loads of the next)
+        int e = 0;
+        for (; e + 4 <= n_e; e += 4) {
+            double2 q[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j] = Q[(int64_t)(e + j) * n_pad + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                q[j].x = fma(ph[e + j].x, vr, fma(-ph[e + j].y, vi, q[j].x));
+                q[j].y = fma(ph[e + j].x, vi, fma(ph[e + j].y, vr, q[j].y));
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Q[(int64_t)(e + j) * n_pad + i] = q[j];
+        }
+        for (; e < n_e; ++e) {
             double2 q = Q[(int64_t)e * n_pad + i];
             q.x = fma(ph[e].x, vr, fma(-ph[e].y, vi, q.x));
             q.y = fma(ph[e].x, vi, fma(ph[e].y, vr, q.y));

@@ -31,40 +31,6 @@ namespace {
 
 enum BMode { B_ONE = 0, B_REAL = 1, B_IMAG = 2 };
 
-// Programmatic dependent launch (sm_90 and later). A grid launched with the
-// programmatic-serialisation attribute may be scheduled once every block of the
-// previous kernel in the stream has started and released it; griddepcontrol.wait
-// then blocks until that kernel has completed and its writes are visible. The
-// single-state sweeps wait before their first memory access and release at
-// once, so the next sweep's blocks take each SM as this sweep's blocks leave it
-// and start the moment it completes. For a plain launch both instructions do
-// nothing.
-__device__ __forceinline__ void pdl_wait_release()
-{
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-template <typename P>
-cudaError_t launch_b1(void (*kern)(P), int grid, bool pdl, cudaStream_t s, const P &p)
-{
-    if (!pdl) {
-        kern<<<grid, kBlockB1, 0, s>>>(p);
-        return cudaGetLastError();
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(kBlockB1);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, p);
-}
-
 // Coefficients of one sweep: a on psi (real, or imaginary if AIMAG), beta on A x.
 // For a batch of instances, coefficients and the renormalisation scale are
 // those of the slice's instance.
@@ -280,17 +246,17 @@ cudaError_t sweep_dispatch(SweepKind kind, bool a_imag, bool has_z, const SweepP
 {
     switch (kind) {
     case SW_FIRST:
-        return a_imag ? launch_b1(sweep_b1<R, OP, REALV, B_REAL, true, false, false, MULTI>, grid, pdl, s, p)
-                      : launch_b1(sweep_b1<R, OP, REALV, B_IMAG, false, false, false, MULTI>, grid, pdl, s, p);
+        return a_imag ? launch_pdl(sweep_b1<R, OP, REALV, B_REAL, true, false, false, MULTI>, grid, kBlockB1, pdl, s, p)
+                      : launch_pdl(sweep_b1<R, OP, REALV, B_IMAG, false, false, false, MULTI>, grid, kBlockB1, pdl, s, p);
     case SW_SECOND:
-        return a_imag ? launch_b1(sweep_b1<R, OP, REALV, B_ONE, true, false, false, MULTI>, grid, pdl, s, p)
-                      : launch_b1(sweep_b1<R, OP, REALV, B_ONE, false, false, false, MULTI>, grid, pdl, s, p);
+        return a_imag ? launch_pdl(sweep_b1<R, OP, REALV, B_ONE, true, false, false, MULTI>, grid, kBlockB1, pdl, s, p)
+                      : launch_pdl(sweep_b1<R, OP, REALV, B_ONE, false, false, false, MULTI>, grid, kBlockB1, pdl, s, p);
     case SW_MID:
-        return a_imag ? launch_b1(sweep_b1<R, OP, REALV, B_ONE, true, true, false, MULTI>, grid, pdl, s, p)
-                      : launch_b1(sweep_b1<R, OP, REALV, B_ONE, false, true, false, MULTI>, grid, pdl, s, p);
+        return a_imag ? launch_pdl(sweep_b1<R, OP, REALV, B_ONE, true, true, false, MULTI>, grid, kBlockB1, pdl, s, p)
+                      : launch_pdl(sweep_b1<R, OP, REALV, B_ONE, false, true, false, MULTI>, grid, kBlockB1, pdl, s, p);
     case SW_FINAL:
-        return has_z ? launch_b1(sweep_b1<R, OP, REALV, B_REAL, false, true, true, MULTI>, grid, pdl, s, p)
-                     : launch_b1(sweep_b1<R, OP, REALV, B_REAL, false, false, true, MULTI>, grid, pdl, s, p);
+        return has_z ? launch_pdl(sweep_b1<R, OP, REALV, B_REAL, false, true, true, MULTI>, grid, kBlockB1, pdl, s, p)
+                     : launch_pdl(sweep_b1<R, OP, REALV, B_REAL, false, false, true, MULTI>, grid, kBlockB1, pdl, s, p);
     }
     return cudaErrorInvalidValue;
 }
@@ -298,8 +264,8 @@ cudaError_t sweep_dispatch(SweepKind kind, bool a_imag, bool has_z, const SweepP
 template <typename R, int OP, bool REALV>
 cudaError_t kpm_dispatch(const KpmParams &p, int grid, bool pdl, cudaStream_t s)
 {
-    return p.first ? launch_b1(kpm_b1<R, OP, REALV, true>, grid, pdl, s, p)
-                   : launch_b1(kpm_b1<R, OP, REALV, false>, grid, pdl, s, p);
+    return p.first ? launch_pdl(kpm_b1<R, OP, REALV, true>, grid, kBlockB1, pdl, s, p)
+                   : launch_pdl(kpm_b1<R, OP, REALV, false>, grid, kBlockB1, pdl, s, p);
 }
 
 }  // namespace

@@ -9,19 +9,65 @@
 // The vectors are kept unnormalised, v_n = s_n u_n, with the scalars s_n, b_n
 // on the device, so no pass only rescales: one pass forms w (sparse product
 // plus the b_n v_{n-1} term, written over u_{n-1}) with the dot <u_n|w>, one
-// elementwise pass forms u_{n+1} = w - a_n s_n u_n in place with ||u_{n+1}||^2,
-// and two single-block kernels reduce the per-warp FP64 partials in a fixed
-// order and update a_n, b_{n+1}, s_{n+1}. The stored operator is A = 2H/rescale,
-// so H x = (rescale/2) A x.
+// elementwise pass forms u_{n+1} = w - a_n s_n u_n in place with ||u_{n+1}||^2.
+// Each pass sums its dot per block in a fixed order; the last block of the grid
+// to finish (found by a ticket counter, nothing waits) adds the per-block sums
+// in block order, so the total does not depend on which block is last, and
+// updates a_n, or b_{n+1} and the scales. Two launches per level, both
+// programmatic dependent launches. The stored operator is A = 2H/rescale, so
+// H x = (rescale/2) A x.
 #include "sweep_ops.cuh"
 
 namespace tbpm {
 namespace {
 
-// scalars sc[]: 0 s_n (scale of u_n), 1 b_n, 2 s_{n-1}, 3 a_n
-template <typename R, int OP, bool REALV>
-__global__ void __launch_bounds__(kBlockB1) hay_apply(SweepParams p, const double *sc, double half_rescale)
+// Sum of one value per thread over the block, in a fixed order; the result is
+// valid in thread 0.
+__device__ double block_total(double v)
 {
+    __shared__ double ws[kBlockB1 / 32];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kBlockB1 / 32; ++i) t += ws[i];
+    return t;
+}
+
+// Stores the block's sum (thread 0's `mine`) in part[blockIdx.x] and takes a
+// ticket. The block that takes the last ticket returns true in all its threads,
+// with the sum of part[0 .. gridDim.x) in block order in thread 0's `total`,
+// and resets the ticket for the next launch. No block waits for another: the
+// others return false at once. Every thread of the block must call it.
+__device__ bool last_block_total(double mine, double *part, unsigned *ticket, double &total)
+{
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = mine;
+        __threadfence();                                // the partial before the ticket
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();                                    // every other block's partial is visible
+    if (threadIdx.x < 32) {
+        double t = 0.0;
+        for (unsigned i = threadIdx.x; i < gridDim.x; i += 32) t += __ldcg(part + i);
+        total = warp_sum(t);
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    return true;
+}
+
+// scalars sc[]: 0 s_n (scale of u_n), 1 b_n, 2 s_{n-1}, 3 a_n
+// a_n = s_n Re <u_n|w> -> sc[3] and a_out[*counter]
+template <typename R, int OP, bool REALV>
+__global__ void __launch_bounds__(kBlockB1) hay_apply(SweepParams p, double *sc, double half_rescale,
+                                                      double *part, unsigned *ticket, double *a_out,
+                                                      const int *counter)
+{
+    pdl_wait_release();
     typedef typename V2<R>::T V;
     const V *__restrict__ x = reinterpret_cast<const V *>(p.x);       // u_n
     V *y = reinterpret_cast<V *>(p.y);                                // in u_{n-1}, out w
@@ -49,15 +95,25 @@ __global__ void __launch_bounds__(kBlockB1) hay_apply(SweepParams p, const doubl
         // would cost two more FP64 operations per row, is not formed
         dr = fma(xr, wr, fma(xim, wi, dr));
     }
-    dr = warp_sum(dr);
-    if (lane == 0) p.partials[warp] = make_double2(dr, 0.0);
+    double t;
+    if (last_block_total(block_total(dr), part, ticket, t) && threadIdx.x == 0) {
+        const double a = sc[0] * t;
+        sc[3] = a;
+        a_out[*counter] = a;
+    }
 }
 
-// u_{n+1} = w - a_n s_n u_n (in place over w) and ||u_{n+1}||^2 per warp.
+// u_{n+1} = w - a_n s_n u_n (in place over w) and ||u_{n+1}||^2; the last block
+// forms b_{n+1} = ||u_{n+1}|| (to b_out[*counter]), shifts the scales and
+// advances the counter. A b_{n+1} at rounding level, <= 1e-12 (|a_n| + b_n),
+// ends the chain (an invariant subspace): it is stored as 0 and the scale 0
+// keeps every later vector, a and b at 0.
 template <typename R>
-__global__ void __launch_bounds__(kBlockB1) hay_update(const void *u_, void *w_, int64_t nslices,
-                                                       const double *sc, double2 *partials)
+__global__ void __launch_bounds__(kBlockB1) hay_update(const void *u_, void *w_, int64_t nslices, double *sc,
+                                                       double *part, unsigned *ticket, double *b_out,
+                                                       int *counter)
 {
+    pdl_wait_release();
     typedef typename V2<R>::T V;
     const V *u = reinterpret_cast<const V *>(u_);
     V *w = reinterpret_cast<V *>(w_);
@@ -76,8 +132,16 @@ __global__ void __launch_bounds__(kBlockB1) hay_update(const void *u_, void *w_,
         const double r = (double)wi.x, im = (double)wi.y;
         nn = fma(r, r, fma(im, im, nn));
     }
-    nn = warp_sum(nn);
-    if (lane == 0) partials[warp] = make_double2(nn, 0.0);
+    double t;
+    if (last_block_total(block_total(nn), part, ticket, t) && threadIdx.x == 0) {
+        double b = sqrt(t);
+        if (b <= 1e-12 * (fabs(sc[3]) + sc[1])) b = 0.0;
+        b_out[*counter] = b;
+        sc[2] = sc[0];
+        sc[0] = b > 0.0 ? 1.0 / b : 0.0;
+        sc[1] = b;
+        *counter += 1;
+    }
 }
 
 // Fixed-order block sum of W complex partials (one block of 256 threads).
@@ -96,7 +160,7 @@ __device__ double2 sum_partials(const double2 *p, int64_t W)
     return make_double2(sr[0], si[0]);
 }
 
-// s_0 = 1/||psi0||, b_0 = 0, s_{-1} = 0, iteration counter 0.
+// s_0 = 1/||psi0||, b_0 = 0, s_{-1} = 0, iteration counter and ticket 0.
 __global__ void hay_init(const double2 *partials, int64_t W, double *sc, int *counter)
 {
     const double2 t = sum_partials(partials, W);
@@ -105,36 +169,8 @@ __global__ void hay_init(const double2 *partials, int64_t W, double *sc, int *co
         sc[1] = 0.0;
         sc[2] = 0.0;
         sc[3] = 0.0;
-        *counter = 0;
-    }
-}
-
-// a_n = s_n Re <u_n|w>
-__global__ void hay_scalar1(const double2 *partials, int64_t W, double *sc, double *a_out,
-                            const int *counter)
-{
-    const double2 t = sum_partials(partials, W);
-    if (threadIdx.x == 0) {
-        const double a = sc[0] * t.x;
-        sc[3] = a;
-        a_out[*counter] = a;
-    }
-}
-
-// b_{n+1} = ||u_{n+1}||; shift the scales; n <- n + 1. A b_{n+1} at rounding
-// level, <= 1e-12 (|a_n| + b_n), ends the chain (an invariant subspace): it is
-// stored as 0 and the scale 0 keeps every later vector, a and b at 0.
-__global__ void hay_scalar2(const double2 *partials, int64_t W, double *sc, double *b_out, int *counter)
-{
-    const double2 t = sum_partials(partials, W);
-    if (threadIdx.x == 0) {
-        double b = sqrt(t.x);
-        if (b <= 1e-12 * (fabs(sc[3]) + sc[1])) b = 0.0;
-        b_out[*counter] = b;
-        sc[2] = sc[0];
-        sc[0] = b > 0.0 ? 1.0 / b : 0.0;
-        sc[1] = b;
-        *counter += 1;
+        counter[0] = 0;
+        counter[1] = 0;
     }
 }
 
@@ -159,45 +195,79 @@ __global__ void hay_ldos(const double *a, const double *b, int M, const double *
 }
 
 template <typename R, int OP, bool REALV>
-cudaError_t apply_t(const SweepParams &p, const double *sc, double hr, int grid, cudaStream_t s)
+cudaError_t apply_t(const SweepParams &p, double *sc, double hr, double *part, unsigned *ticket, double *a_out,
+                    const int *counter, int grid, bool pdl, cudaStream_t s)
 {
-    hay_apply<R, OP, REALV><<<grid, kBlockB1, 0, s>>>(p, sc, hr);
-    return cudaGetLastError();
+    return launch_pdl(hay_apply<R, OP, REALV>, grid, kBlockB1, pdl, s, p, sc, hr, part, ticket, a_out, counter);
 }
 
 }  // namespace
 
-cudaError_t launch_hay_apply(const SweepVariant &v, const SweepParams &p, const double *sc,
-                             double half_rescale, int grid, cudaStream_t s)
+cudaError_t launch_hay_apply(const SweepVariant &v, const SweepParams &p, double *sc, double half_rescale,
+                             double *part, unsigned *ticket, double *a_out, const int *counter, int grid,
+                             cudaStream_t s)
 {
+    const bool pdl = v.pdl;
     if (v.precision == TBPM_FP64) {
         if (v.op == OP_SELL)
-            return v.real_values ? apply_t<double, OP_SELL, true>(p, sc, half_rescale, grid, s)
-                                 : apply_t<double, OP_SELL, false>(p, sc, half_rescale, grid, s);
-        if (v.op == OP_STENCIL_MONO) return apply_t<double, OP_STENCIL_MONO, true>(p, sc, half_rescale, grid, s);
-        return apply_t<double, OP_STENCIL_BI, true>(p, sc, half_rescale, grid, s);
+            return v.real_values
+                       ? apply_t<double, OP_SELL, true>(p, sc, half_rescale, part, ticket, a_out, counter, grid, pdl, s)
+                       : apply_t<double, OP_SELL, false>(p, sc, half_rescale, part, ticket, a_out, counter, grid, pdl, s);
+        if (v.op == OP_STENCIL_MONO)
+            return apply_t<double, OP_STENCIL_MONO, true>(p, sc, half_rescale, part, ticket, a_out, counter, grid, pdl, s);
+        return apply_t<double, OP_STENCIL_BI, true>(p, sc, half_rescale, part, ticket, a_out, counter, grid, pdl, s);
     }
     if (v.op == OP_SELL)
-        return v.real_values ? apply_t<float, OP_SELL, true>(p, sc, half_rescale, grid, s)
-                             : apply_t<float, OP_SELL, false>(p, sc, half_rescale, grid, s);
-    if (v.op == OP_STENCIL_MONO) return apply_t<float, OP_STENCIL_MONO, true>(p, sc, half_rescale, grid, s);
-    return apply_t<float, OP_STENCIL_BI, true>(p, sc, half_rescale, grid, s);
+        return v.real_values
+                   ? apply_t<float, OP_SELL, true>(p, sc, half_rescale, part, ticket, a_out, counter, grid, pdl, s)
+                   : apply_t<float, OP_SELL, false>(p, sc, half_rescale, part, ticket, a_out, counter, grid, pdl, s);
+    if (v.op == OP_STENCIL_MONO)
+        return apply_t<float, OP_STENCIL_MONO, true>(p, sc, half_rescale, part, ticket, a_out, counter, grid, pdl, s);
+    return apply_t<float, OP_STENCIL_BI, true>(p, sc, half_rescale, part, ticket, a_out, counter, grid, pdl, s);
 }
 
-cudaError_t launch_hay_update(int precision, const void *u, void *w, int64_t nslices, const double *sc,
-                              double2 *partials, int grid, cudaStream_t s)
+cudaError_t launch_hay_update(const SweepVariant &v, const void *u, void *w, int64_t nslices, double *sc,
+                              double *part, unsigned *ticket, double *b_out, int *counter, int grid,
+                              cudaStream_t s)
 {
-    if (precision == TBPM_FP64) hay_update<double><<<grid, kBlockB1, 0, s>>>(u, w, nslices, sc, partials);
-    else hay_update<float><<<grid, kBlockB1, 0, s>>>(u, w, nslices, sc, partials);
-    return cudaGetLastError();
+    if (v.precision == TBPM_FP64)
+        return launch_pdl(hay_update<double>, grid, kBlockB1, v.pdl, s, u, w, nslices, sc, part, ticket, b_out,
+                          counter);
+    return launch_pdl(hay_update<float>, grid, kBlockB1, v.pdl, s, u, w, nslices, sc, part, ticket, b_out, counter);
 }
 
-cudaError_t launch_hay_scalar(int which, const double2 *partials, int64_t W, double *sc, double *out,
-                              int *counter, cudaStream_t s)
+// Grids of the two passes, whole waves of their own resident blocks: the
+// product pass holds more registers than the Clenshaw sweeps (up to 64 in FP64
+// against 40), so the sweep grid would leave a partial second wave.
+template <typename K>
+static int per_sm(K kern)
 {
-    if (which == 0) hay_init<<<1, 256, 0, s>>>(partials, W, sc, counter);
-    else if (which == 1) hay_scalar1<<<1, 256, 0, s>>>(partials, W, sc, out, counter);
-    else hay_scalar2<<<1, 256, 0, s>>>(partials, W, sc, out, counter);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kBlockB1, 0) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    return n < 1 ? 1 : n;
+}
+
+template <typename R>
+static int apply_per_sm(const SweepVariant &v)
+{
+    if (v.op == OP_STENCIL_MONO) return per_sm(hay_apply<R, OP_STENCIL_MONO, true>);
+    if (v.op == OP_STENCIL_BI) return per_sm(hay_apply<R, OP_STENCIL_BI, true>);
+    return v.real_values ? per_sm(hay_apply<R, OP_SELL, true>) : per_sm(hay_apply<R, OP_SELL, false>);
+}
+
+void hay_grids(const SweepVariant &v, int num_sms, int *apply_grid, int *update_grid)
+{
+    const bool f64 = v.precision == TBPM_FP64;
+    *apply_grid = (f64 ? apply_per_sm<double>(v) : apply_per_sm<float>(v)) * num_sms;
+    *update_grid = (f64 ? per_sm(hay_update<double>) : per_sm(hay_update<float>)) * num_sms;
+}
+
+cudaError_t launch_hay_init(const double2 *partials, int64_t W, double *sc, int *counter, cudaStream_t s)
+{
+    hay_init<<<1, 256, 0, s>>>(partials, W, sc, counter);
     return cudaGetLastError();
 }
 

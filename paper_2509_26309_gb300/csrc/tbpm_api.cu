@@ -510,19 +510,19 @@ int enqueue_hay_chunk(tbpm_ctx *ctx, int len, int M, cudaStream_t s, int64_t *la
     SweepParams p;
     fill_operator(ctx, p);
     p.partials = ctx->d_partials;
-    const int64_t W = (int64_t)ctx->nblk * (kBlockB1 / 32);
     double *aout = reinterpret_cast<double *>(ctx->d_out);
     double *bout = aout + M;
+    double *part = reinterpret_cast<double *>(ctx->d_partials);        // nblk per-block sums
+    unsigned *ticket = reinterpret_cast<unsigned *>(ctx->d_counter + 1);
+    const int ga = ctx->hay_grid[0], gu = ctx->hay_grid[1];
     void *U[2] = {ctx->d_psi, ctx->d_b0};
     for (int d = 0; d < len; ++d) {
         p.x = U[d & 1];
         p.y = U[(d + 1) & 1];
-        CU(launch_hay_apply(v, p, ctx->d_misc, 0.5 * ctx->rescale, ctx->nblk, s));
-        CU(launch_hay_scalar(1, ctx->d_partials, W, ctx->d_misc, aout, ctx->d_counter, s));
-        CU(launch_hay_update(ctx->precision, U[d & 1], U[(d + 1) & 1], p.nslices, ctx->d_misc, ctx->d_partials,
-                             ctx->nblk, s));
-        CU(launch_hay_scalar(2, ctx->d_partials, W, ctx->d_misc, bout, ctx->d_counter, s));
-        *launches += 4;
+        CU(launch_hay_apply(v, p, ctx->d_misc, 0.5 * ctx->rescale, part, ticket, aout, ctx->d_counter, ga, s));
+        CU(launch_hay_update(v, U[d & 1], U[(d + 1) & 1], p.nslices, ctx->d_misc, part, ticket, bout,
+                             ctx->d_counter, gu, s));
+        *launches += 2;
     }
     return TBPM_OK;
 }
@@ -805,7 +805,7 @@ int run_chunk(tbpm_ctx *ctx, int kind, int K, int len, int64_t *launches, int64_
         it = ctx->graphs.emplace(key, ex).first;
     } else {
         nl = kind == 1   ? (int64_t)len + 2
-             : kind == 4 ? 4 * (int64_t)len
+             : kind == 4 ? 2 * (int64_t)len
              : kind == 6 ? (int64_t)len * (3 * (K - 1) + 1) + 2
              : kind == 7 ? (int64_t)len * ((K - 2) / kTbS + 1) + 2
              : kind == 8 ? (int64_t)(len + kTbS - 1) / kTbS + 2
@@ -1576,6 +1576,21 @@ int tbpm_quasi_eigenstates(tbpm_ctx *ctx, const double *psi0, double dt, int n_s
     CU(launch_load_states(ctx->precision, src, n, n_pad, 1, 0, 1, ctx->d_psi0, ctx->d_psi, ctx->stream));
     const double pre = dt / (2.0 * 3.141592653589793238462643383279502884);
     CU(launch_qe_init(ctx->precision, ctx->d_psi0, ctx->d_qe, n_e, n_pad, pre, ctx->stream));
+    // the quasi-eigenstate graphs bake dt and the number of energies into their
+    // accumulation launches (the energies themselves are read from d_qe_e): they
+    // are kept across calls with the same two and rebuilt otherwise
+    if (dt != ctx->qe_graph_dt || n_e != ctx->qe_graph_ne) {
+        for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
+            if (std::get<0>(it->first) == 5) {
+                cudaGraphExecDestroy(it->second);
+                it = ctx->graphs.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        ctx->qe_graph_dt = dt;
+        ctx->qe_graph_ne = n_e;
+    }
     int64_t launches = 2, passes = 0;
     for (int dir = 0; dir < 2; ++dir) {
         const double h = dir == 0 ? dt : -dt;
@@ -1603,15 +1618,6 @@ int tbpm_quasi_eigenstates(tbpm_ctx *ctx, const double *psi0, double dt, int n_s
     CU(cudaMemcpy2DAsync(qe, sizeof(double2) * n, ctx->d_qe, sizeof(double2) * n_pad, sizeof(double2) * n, n_e,
                          q_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    // the quasi-eigenstate graphs bake this call's dt and energies
-    for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
-        if (std::get<0>(it->first) == 5) {
-            cudaGraphExecDestroy(it->second);
-            it = ctx->graphs.erase(it);
-        } else {
-            ++it;
-        }
-    }
     CU(cudaGetLastError());
     ctx->last_passes = passes;
     ctx->last_launches = launches;
@@ -1637,7 +1643,8 @@ int tbpm_haydock(tbpm_ctx *ctx, const double *psi0, int M, double *a, double *b)
     const int64_t W = (int64_t)ctx->nblk * (kBlockB1 / 32);
     CU(launch_dot(ctx->precision, ctx->d_psi, ctx->d_psi, ctx->n_pad / kSlice, ctx->d_partials, ctx->nblk, false,
                   ctx->stream));
-    CU(launch_hay_scalar(0, ctx->d_partials, W, ctx->d_misc, nullptr, ctx->d_counter, ctx->stream));
+    CU(launch_hay_init(ctx->d_partials, W, ctx->d_misc, ctx->d_counter, ctx->stream));
+    if (ctx->hay_grid[0] == 0) hay_grids(variant(ctx, 1), ctx->num_sms, &ctx->hay_grid[0], &ctx->hay_grid[1]);
     int64_t launches = 3;
     int done = 0;
     while (done < M) {

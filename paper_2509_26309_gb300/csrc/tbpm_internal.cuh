@@ -21,6 +21,44 @@ constexpr int kMaxTerms = 128;      // Chebyshev coefficients generated on devic
 constexpr int kChunk = 16;          // time steps (or KPM passes) per captured graph
 constexpr int kMaxBlockStates = 16; // states advanced together (FP32 batched)
 
+// ------------------------------------------------- programmatic launches
+
+// Programmatic dependent launch (sm_90 and later). A grid launched with the
+// programmatic-serialisation attribute may be scheduled once every block of the
+// previous kernel in the stream has started and released it;
+// griddepcontrol.wait then blocks until that kernel has completed and its
+// writes are visible. The kernels launched this way (the single-state sweeps,
+// the KPM passes, the Haydock passes) call pdl_wait_release() before their
+// first memory access, so the next grid's blocks take each SM as this grid's
+// blocks leave it and start the moment it completes. For a plain launch both
+// instructions do nothing.
+__device__ __forceinline__ void pdl_wait_release()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// kern<<<grid, block, 0, s>>>(args...), as a programmatic dependent launch if pdl.
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kern)(P...), int grid, int block, bool pdl, cudaStream_t s, A... args)
+{
+    if (!pdl) {
+        kern<<<grid, block, 0, s>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ---------------------------------------------------------------- layouts
 
 // Sliced ELLPACK with slice height 32 and no row sorting (the lattice order of
@@ -197,6 +235,7 @@ struct tbpm_ctx {
     size_t stage_cap = 0;
     int *d_counter = nullptr;        // chunk base counter for graphs
     double *d_misc = nullptr;        // small scratch (norms, moment bases)
+    int hay_grid[2] = {0, 0};        // Haydock product and update grids (set at first use)
     double *d_scale = nullptr;       // [16] 1/||psi_j|| for the renormalised FP32 path
     double2 *d_norm = nullptr;       // [kChunk][nblk][B] ||y||^2 partials (renormalisation)
     double2 *d_cpart = nullptr;      // [n_steps][nslices] partials of the cluster path
@@ -216,6 +255,8 @@ struct tbpm_ctx {
     size_t qe_cap = 0, qe_e_cap = 0;
     int qe_ne = 0, qe_N = 0;
     double qe_h = 0.0;
+    double qe_graph_dt = 0.0;        // dt and energy count the kind-5 graphs were built for
+    int qe_graph_ne = 0;
     // AC conductivity: current operators (tbpm_set_current) and their work buffers
     tbpm::CurrentOp cur;
     int64_t cur_nnz = 0;
@@ -310,18 +351,23 @@ cudaError_t launch_ac_cond(const double2 *corr, int n_steps, double dt, double b
 cudaError_t launch_store_column(int precision, const void *src, int64_t n, int B, int col,
                                 const double *scale, double *dst, cudaStream_t s);
 
-// Haydock recursion (haydock.cu). Device scalars sc[4] = {s_n, b_n, s_{n-1}, a_n}.
+// Haydock recursion (haydock.cu). Device scalars sc[4] = {s_n, b_n, s_{n-1}, a_n};
+// counter[0] = n, counter[1] the ticket of the last-block sums (zeroed by init).
 // apply: w = (rescale/2) s_n A u_n - b_n s_{n-1} u_{n-1} into p.y (= u_{n-1}),
-//        per-warp <u_n|w> partials into p.partials (p.x = u_n);
-// update: w <- w - a_n s_n u (in place), per-warp ||w||^2 partials;
-// scalar: 0 init from ||psi0||^2 partials, 1 a_n (to out[*counter]),
-//         2 b_{n+1} (to out[*counter]) and counter + 1.
-cudaError_t launch_hay_apply(const SweepVariant &v, const SweepParams &p, const double *sc,
-                             double half_rescale, int grid, cudaStream_t s);
-cudaError_t launch_hay_update(int precision, const void *u, void *w, int64_t nslices, const double *sc,
-                              double2 *partials, int grid, cudaStream_t s);
-cudaError_t launch_hay_scalar(int which, const double2 *partials, int64_t W, double *sc, double *out,
-                              int *counter, cudaStream_t s);
+//        p.x = u_n; a_n = s_n Re <u_n|w> to sc[3] and a_out[n];
+// update: w <- w - a_n s_n u (in place); b_{n+1} = ||w|| to b_out[n], the
+//        scales shifted, n + 1;
+// both use part[grid] doubles of per-block sums (grids from hay_grids);
+// init: s_0 from the ||psi0||^2 per-warp partials of launch_dot.
+cudaError_t launch_hay_apply(const SweepVariant &v, const SweepParams &p, double *sc, double half_rescale,
+                             double *part, unsigned *ticket, double *a_out, const int *counter, int grid,
+                             cudaStream_t s);
+cudaError_t launch_hay_update(const SweepVariant &v, const void *u, void *w, int64_t nslices, double *sc,
+                              double *part, unsigned *ticket, double *b_out, int *counter, int grid,
+                              cudaStream_t s);
+cudaError_t launch_hay_init(const double2 *partials, int64_t W, double *sc, int *counter, cudaStream_t s);
+// Whole-wave grids of the product and update passes for this operator.
+void hay_grids(const SweepVariant &v, int num_sms, int *apply_grid, int *update_grid);
 cudaError_t launch_hay_ldos(const double *a, const double *b, int M, const double *energies, int n_e,
                             double eta, double *ldos, cudaStream_t s);
 

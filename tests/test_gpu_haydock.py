@@ -49,6 +49,24 @@ def test_haydock_stencil_and_chain_stop(orc):
     assert abs(b2[0] - 8.1) < 1e-13 and np.all(b2[1:] == 0) and np.all(np.abs(a2) < 1e-12)
 
 
+def test_haydock_deterministic_and_launch_order_neutral(orc):
+    """Each pass's scalar is formed by whichever block finishes last, from the
+    per-block sums added in block order: repeated calls, and plain stream order
+    instead of programmatic launches, give the same bits."""
+    n = 2 * 300 * 200
+    h = ti.graphene_csr(300, 200, onsite=ti.anderson_onsite(n, 1.0, 8))
+    psi0 = ti.random_phase_state(n, 9)
+    runs = []
+    for flags in (0, 0, tb.TBPM_F_NO_PDL):
+        ctx = tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, 9.0, tb.make_opts(flags=flags))
+        runs.append(tb.tbpm_haydock(ctx, psi0, 200))
+        tb.tbpm_destroy(ctx)
+    for a, b in runs[1:]:
+        assert np.array_equal(a, runs[0][0]) and np.array_equal(b, runs[0][1])
+    ra, rb = orc.haydock(h, psi0, 200)
+    assert np.max(np.abs(runs[0][0] - ra)) <= 1e-9 and np.max(np.abs(runs[0][1] - rb)) <= 1e-9
+
+
 @pytest.mark.parametrize("prec,tol", [(tb.TBPM_FP64, 1e-10), (tb.TBPM_FP32, 1e-5)])
 def test_quasi_eigenstates(orc, prec, tol):
     h = ti.graphene_csr(20, 16, onsite=ti.anderson_onsite(640, 1.0, 2), bond_phases=[0.3, -0.2, 0.9])
@@ -63,3 +81,12 @@ def test_quasi_eigenstates(orc, prec, tol):
     # the ordinary correlation call still works on the same context afterwards
     c = tb.tbpm_dos_corr(ctx, psi0, dt, 20)
     assert np.max(np.abs(c - orc.dos_corr(h, 9.0, psi0, dt, 20))) <= max(tol, 1e-10) * 10
+    # the graphs of the first call serve a call with other energies of the same
+    # count (read from device memory at run time); another dt or count rebuilds them
+    E2 = E + 0.35
+    got2 = tb.tbpm_quasi_eigenstates(ctx, psi0, dt, 150, E2)
+    assert np.max(np.abs(got2 - orc.quasi_eigenstates(h, 9.0, psi0, dt, 150, E2))) <= tol
+    got3 = tb.tbpm_quasi_eigenstates(ctx, psi0, 0.8 * dt, 40, E2[:3])
+    assert np.max(np.abs(got3 - orc.quasi_eigenstates(h, 9.0, psi0, 0.8 * dt, 40, E2[:3]))) <= tol
+    got4 = tb.tbpm_quasi_eigenstates(ctx, psi0, dt, 150, E)
+    assert np.array_equal(got4, got)
