@@ -37,9 +37,11 @@ __device__ double block_total(double v)
 
 // Stores the block's sum (thread 0's `mine`) in part[blockIdx.x] and takes a
 // ticket. The block that takes the last ticket returns true in all its threads,
-// with the sum of part[0 .. gridDim.x) in block order in thread 0's `total`,
-// and resets the ticket for the next launch. No block waits for another: the
-// others return false at once. Every thread of the block must call it.
+// with the sum of part[0 .. gridDim.x) in thread 0's `total` (each thread loads
+// its strided share at once, then the fixed-order block sum: the same order
+// whichever block is last), and resets the ticket for the next launch. No
+// block waits for another: the others return false at once. Every thread of
+// the block must call it.
 __device__ bool last_block_total(double mine, double *part, unsigned *ticket, double &total)
 {
     __shared__ bool last;
@@ -51,11 +53,9 @@ __device__ bool last_block_total(double mine, double *part, unsigned *ticket, do
     __syncthreads();
     if (!last) return false;
     __threadfence();                                    // every other block's partial is visible
-    if (threadIdx.x < 32) {
-        double t = 0.0;
-        for (unsigned i = threadIdx.x; i < gridDim.x; i += 32) t += __ldcg(part + i);
-        total = warp_sum(t);
-    }
+    double t = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) t += __ldcg(part + i);
+    total = block_total(t);
     if (threadIdx.x == 0) *ticket = 0u;
     return true;
 }
