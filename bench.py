@@ -632,9 +632,10 @@ def run_variants(args, dev, stream):
     # per orbital and level: the product pass (3 hoppings: int32 column + FP64
     # value, FP64 diagonal, slice offsets; u_n gathered, u_{n-1} read, w
     # written) and the update pass (u_n, w read, u_{n+1} written); FP64
-    # operations 14 (product 12, Re <u_n|w> 2) + 4 (update 2, norm 2)
+    # operations 12 (product and the scaled u_{n-1} 10, Re <u_n|w> 2) + 4
+    # (update 2, norm 2)
     res["fp64_haydock_1024x1024"] = {"value": rate, "unit": "orbital-levels/s", "ms_per_call": msh, "levels": lv,
-                                     "roofline": dict(alu_roof(rate, 18),
+                                     "roofline": dict(alu_roof(rate, 16),
                                                       hbm=hbm_roof(rate, 3 * 12 + 8 + 0.5 + 48 + 48,
                                                                    "product + update pass per level"))}
     tb.tbpm_destroy(cac)

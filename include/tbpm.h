@@ -245,7 +245,9 @@ int tbpm_quasi_eigenstates(tbpm_ctx *ctx, const double *psi0, double dt, int n_s
  *   psi0  double[2n] start state (a site state e_i gives the LDOS at site i),
  *         host or device, not necessarily normalised
  *   M     >= 1 levels;  a, b  double[M] out: a[n] = a_n, b[n] = b_{n+1}
- * If some b_{n+1} is 0 (an invariant subspace) every later a and b is 0. */
+ * A b_{n+1} at rounding level, <= tol (|a_n| + b_n) with tol = 1e-12 for FP64
+ * contexts and 1e-6 for FP32 ones, marks an invariant subspace: it is returned
+ * as 0 and every later a and b is 0. */
 int tbpm_haydock(tbpm_ctx *ctx, const double *psi0, int M, double *a, double *b);
 
 /* tbpm_haydock_ldos: rho(E_j) = -Im G(E_j + i eta) / pi with the continued

@@ -6,10 +6,16 @@
 // From v_0 = psi0/||psi0||, v_{-1} = 0, b_0 = 0, for n = 0, 1, ...:
 //   w = H v_n - b_n v_{n-1},  a_n = Re <v_n|w>,  u = w - a_n v_n,
 //   b_{n+1} = ||u||,  v_{n+1} = u / b_{n+1}.
-// The vectors are kept unnormalised, v_n = s_n u_n, with the scalars s_n, b_n
-// on the device, so no pass only rescales: one pass forms w (sparse product
-// plus the b_n v_{n-1} term, written over u_{n-1}) with the dot <u_n|w>, one
-// elementwise pass forms u_{n+1} = w - a_n s_n u_n in place with ||u_{n+1}||^2.
+// The vectors are kept unnormalised, v_n = s_n u_n, with the scalars on the
+// device, so no pass only rescales, and every scale sits in a scalar: with
+// H = (rescale/2) A (the stored operator is A = 2H/rescale) and h = rescale/2,
+//   w = h s_n wt,  wt = A u_n - rho_n u_{n-1},  rho_n = b_n s_{n-1} / (h s_n),
+//   a_n = h s_n^2 Re <u_n|wt>,
+//   u_{n+1} = wt - (a_n / h) u_n,  so that  b_{n+1} = h s_n ||u_{n+1}||,
+//   s_{n+1} = 1 / ||u_{n+1}||,  rho_{n+1} = s_n^2 ||u_{n+1}||^2.
+// One pass forms wt over u_{n-1} (the sparse product plus one scaled vector:
+// 10 FP64 operations per row, 2 more for Re <u_n|wt>), one elementwise pass
+// forms u_{n+1} in place with ||u_{n+1}||^2.
 // Each pass sums its dot per block in a fixed order; the last block of the grid
 // to finish (found by a ticket counter, nothing waits) adds the per-block sums
 // in block order, so the total does not depend on which block is last, and
@@ -60,8 +66,10 @@ __device__ bool last_block_total(double mine, double *part, unsigned *ticket, do
     return true;
 }
 
-// scalars sc[]: 0 s_n (scale of u_n), 1 b_n, 2 s_{n-1}, 3 a_n
-// a_n = s_n Re <u_n|w> -> sc[3] and a_out[*counter]
+// scalars sc[]: 0 s_n (scale of u_n), 1 b_n, 2 s_{n-1}, 3 a_n, 4 rho_n,
+// 5 h s_n^2, 6 a_n / h. Once the chain has ended (s_n = +0, see hay_update) the
+// product pass writes zeros: wt would otherwise grow as A^k times the residual.
+// a_n -> sc[3], sc[6] and a_out[*counter]
 template <typename R, int OP, bool REALV>
 __global__ void __launch_bounds__(kBlockB1) hay_apply(SweepParams p, double *sc, double half_rescale,
                                                       double *part, unsigned *ticket, double *a_out,
@@ -70,54 +78,62 @@ __global__ void __launch_bounds__(kBlockB1) hay_apply(SweepParams p, double *sc,
     pdl_wait_release();
     typedef typename V2<R>::T V;
     const V *__restrict__ x = reinterpret_cast<const V *>(p.x);       // u_n
-    V *y = reinterpret_cast<V *>(p.y);                                // in u_{n-1}, out w
+    V *y = reinterpret_cast<V *>(p.y);                                // in u_{n-1}, out wt
     const R *diag = reinterpret_cast<const R *>(p.diag);
-    const R ca = (R)(half_rescale * sc[0]);
-    const R cb = (R)(sc[1] * sc[2]);
+    const bool ended = __double_as_longlong(sc[0]) == 0;            // s_n == +0
+    const R rho = (R)sc[4];
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double dr = 0.0;
-    for (int64_t s = warp; s < p.nslices; s += nwarps) {
+    for (int64_t s = warp; s < p.nslices && !ended; s += nwarps) {
         const int64_t row = (s << 5) + lane;
         const V xi = __ldg(x + row);
         const V up = y[row];
         const R d = diag ? ldm<R>(diag + row) : (R)0;
-        R ar = d * xi.x, ai = d * xi.y;
+        R ar = fma(d, xi.x, -rho * up.x), ai = fma(d, xi.y, -rho * up.y);
         if (OP == OP_SELL) sell_apply<R, REALV>(p, s, lane, x, ar, ai);
         else if (row < p.n) stencil_apply<R, OP>(p, row, x, ar, ai);
         V w;
-        w.x = fma(ca, ar, -cb * up.x);
-        w.y = fma(ca, ai, -cb * up.y);
+        w.x = ar;
+        w.y = ai;
         y[row] = w;
         const double xr = (double)xi.x, xim = (double)xi.y, wr = (double)w.x, wi = (double)w.y;
-        // Re <u_n|w>: a_n is real (H Hermitian), so the imaginary part, which
+        // Re <u_n|wt>: a_n is real (H Hermitian), so the imaginary part, which
         // would cost two more FP64 operations per row, is not formed
         dr = fma(xr, wr, fma(xim, wi, dr));
     }
+    if (ended) {
+        V zero;
+        zero.x = (R)0;
+        zero.y = (R)0;
+        for (int64_t s = warp; s < p.nslices; s += nwarps) y[(s << 5) + lane] = zero;
+    }
     double t;
     if (last_block_total(block_total(dr), part, ticket, t) && threadIdx.x == 0) {
-        const double a = sc[0] * t;
+        const double a = ended ? 0.0 : sc[5] * t;
         sc[3] = a;
+        sc[6] = a / half_rescale;
         a_out[*counter] = a;
     }
 }
 
-// u_{n+1} = w - a_n s_n u_n (in place over w) and ||u_{n+1}||^2; the last block
-// forms b_{n+1} = ||u_{n+1}|| (to b_out[*counter]), shifts the scales and
-// advances the counter. A b_{n+1} at rounding level, <= 1e-12 (|a_n| + b_n),
-// ends the chain (an invariant subspace): it is stored as 0 and the scale 0
-// keeps every later vector, a and b at 0.
+// u_{n+1} = wt - (a_n / h) u_n (in place over wt) and ||u_{n+1}||^2; the last
+// block forms b_{n+1} = h s_n ||u_{n+1}|| (to b_out[*counter]), the next
+// scalars, and advances the counter. A b_{n+1} at the rounding level of the
+// vectors' precision, <= tol (|a_n| + b_n) with tol = 1e-12 in FP64 and 1e-6
+// in FP32, ends the chain (an invariant subspace): it is stored as 0, and
+// s = +0 keeps every later vector, a and b at 0.
 template <typename R>
 __global__ void __launch_bounds__(kBlockB1) hay_update(const void *u_, void *w_, int64_t nslices, double *sc,
-                                                       double *part, unsigned *ticket, double *b_out,
-                                                       int *counter)
+                                                       double half_rescale, double *part, unsigned *ticket,
+                                                       double *b_out, int *counter)
 {
     pdl_wait_release();
     typedef typename V2<R>::T V;
     const V *u = reinterpret_cast<const V *>(u_);
     V *w = reinterpret_cast<V *>(w_);
-    const R c = (R)(sc[3] * sc[0]);
+    const R c = (R)sc[6];
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -134,12 +150,22 @@ __global__ void __launch_bounds__(kBlockB1) hay_update(const void *u_, void *w_,
     }
     double t;
     if (last_block_total(block_total(nn), part, ticket, t) && threadIdx.x == 0) {
-        double b = sqrt(t);
-        if (b <= 1e-12 * (fabs(sc[3]) + sc[1])) b = 0.0;
+        const double sn = sc[0];
+        double b = half_rescale * sn * sqrt(t);
+        const double tol = sizeof(R) == 4 ? 1e-6 : 1e-12;
+        if (b <= tol * (fabs(sc[3]) + sc[1])) b = 0.0;
         b_out[*counter] = b;
-        sc[2] = sc[0];
-        sc[0] = b > 0.0 ? 1.0 / b : 0.0;
+        sc[2] = sn;
         sc[1] = b;
+        if (b > 0.0) {
+            sc[0] = 1.0 / sqrt(t);
+            sc[4] = sn * sn * t;
+            sc[5] = half_rescale / t;
+        } else {
+            sc[0] = 0.0;
+            sc[4] = 0.0;
+            sc[5] = 0.0;
+        }
         *counter += 1;
     }
 }
@@ -160,15 +186,20 @@ __device__ double2 sum_partials(const double2 *p, int64_t W)
     return make_double2(sr[0], si[0]);
 }
 
-// s_0 = 1/||psi0||, b_0 = 0, s_{-1} = 0, iteration counter and ticket 0.
-__global__ void hay_init(const double2 *partials, int64_t W, double *sc, int *counter)
+// s_0 = 1/||psi0||, b_0 = 0, s_{-1} = 0, rho_0 = 0, h s_0^2; iteration
+// counter and ticket 0.
+__global__ void hay_init(const double2 *partials, int64_t W, double *sc, double half_rescale, int *counter)
 {
     const double2 t = sum_partials(partials, W);
     if (threadIdx.x == 0) {
-        sc[0] = t.x > 0.0 ? 1.0 / sqrt(t.x) : 0.0;
+        const bool ok = t.x > 0.0;
+        sc[0] = ok ? 1.0 / sqrt(t.x) : 0.0;
         sc[1] = 0.0;
         sc[2] = 0.0;
         sc[3] = 0.0;
+        sc[4] = 0.0;
+        sc[5] = ok ? half_rescale / t.x : 0.0;
+        sc[6] = 0.0;
         counter[0] = 0;
         counter[1] = 0;
     }
@@ -227,13 +258,14 @@ cudaError_t launch_hay_apply(const SweepVariant &v, const SweepParams &p, double
 }
 
 cudaError_t launch_hay_update(const SweepVariant &v, const void *u, void *w, int64_t nslices, double *sc,
-                              double *part, unsigned *ticket, double *b_out, int *counter, int grid,
-                              cudaStream_t s)
+                              double half_rescale, double *part, unsigned *ticket, double *b_out, int *counter,
+                              int grid, cudaStream_t s)
 {
     if (v.precision == TBPM_FP64)
-        return launch_pdl(hay_update<double>, grid, kBlockB1, v.pdl, s, u, w, nslices, sc, part, ticket, b_out,
-                          counter);
-    return launch_pdl(hay_update<float>, grid, kBlockB1, v.pdl, s, u, w, nslices, sc, part, ticket, b_out, counter);
+        return launch_pdl(hay_update<double>, grid, kBlockB1, v.pdl, s, u, w, nslices, sc, half_rescale, part,
+                          ticket, b_out, counter);
+    return launch_pdl(hay_update<float>, grid, kBlockB1, v.pdl, s, u, w, nslices, sc, half_rescale, part, ticket,
+                      b_out, counter);
 }
 
 // Grids of the two passes, whole waves of their own resident blocks: the
@@ -265,9 +297,10 @@ void hay_grids(const SweepVariant &v, int num_sms, int *apply_grid, int *update_
     *update_grid = (f64 ? per_sm(hay_update<double>) : per_sm(hay_update<float>)) * num_sms;
 }
 
-cudaError_t launch_hay_init(const double2 *partials, int64_t W, double *sc, int *counter, cudaStream_t s)
+cudaError_t launch_hay_init(const double2 *partials, int64_t W, double *sc, double half_rescale, int *counter,
+                            cudaStream_t s)
 {
-    hay_init<<<1, 256, 0, s>>>(partials, W, sc, counter);
+    hay_init<<<1, 256, 0, s>>>(partials, W, sc, half_rescale, counter);
     return cudaGetLastError();
 }
 

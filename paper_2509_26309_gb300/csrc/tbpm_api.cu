@@ -520,8 +520,8 @@ int enqueue_hay_chunk(tbpm_ctx *ctx, int len, int M, cudaStream_t s, int64_t *la
         p.x = U[d & 1];
         p.y = U[(d + 1) & 1];
         CU(launch_hay_apply(v, p, ctx->d_misc, 0.5 * ctx->rescale, part, ticket, aout, ctx->d_counter, ga, s));
-        CU(launch_hay_update(v, U[d & 1], U[(d + 1) & 1], p.nslices, ctx->d_misc, part, ticket, bout,
-                             ctx->d_counter, gu, s));
+        CU(launch_hay_update(v, U[d & 1], U[(d + 1) & 1], p.nslices, ctx->d_misc, 0.5 * ctx->rescale, part, ticket,
+                             bout, ctx->d_counter, gu, s));
         *launches += 2;
     }
     return TBPM_OK;
@@ -1643,7 +1643,7 @@ int tbpm_haydock(tbpm_ctx *ctx, const double *psi0, int M, double *a, double *b)
     const int64_t W = (int64_t)ctx->nblk * (kBlockB1 / 32);
     CU(launch_dot(ctx->precision, ctx->d_psi, ctx->d_psi, ctx->n_pad / kSlice, ctx->d_partials, ctx->nblk, false,
                   ctx->stream));
-    CU(launch_hay_init(ctx->d_partials, W, ctx->d_misc, ctx->d_counter, ctx->stream));
+    CU(launch_hay_init(ctx->d_partials, W, ctx->d_misc, 0.5 * ctx->rescale, ctx->d_counter, ctx->stream));
     if (ctx->hay_grid[0] == 0) hay_grids(variant(ctx, 1), ctx->num_sms, &ctx->hay_grid[0], &ctx->hay_grid[1]);
     int64_t launches = 3;
     int done = 0;

@@ -351,21 +351,24 @@ cudaError_t launch_ac_cond(const double2 *corr, int n_steps, double dt, double b
 cudaError_t launch_store_column(int precision, const void *src, int64_t n, int B, int col,
                                 const double *scale, double *dst, cudaStream_t s);
 
-// Haydock recursion (haydock.cu). Device scalars sc[4] = {s_n, b_n, s_{n-1}, a_n};
-// counter[0] = n, counter[1] the ticket of the last-block sums (zeroed by init).
-// apply: w = (rescale/2) s_n A u_n - b_n s_{n-1} u_{n-1} into p.y (= u_{n-1}),
-//        p.x = u_n; a_n = s_n Re <u_n|w> to sc[3] and a_out[n];
-// update: w <- w - a_n s_n u (in place); b_{n+1} = ||w|| to b_out[n], the
-//        scales shifted, n + 1;
+// Haydock recursion (haydock.cu). Device scalars sc[7] = {s_n, b_n, s_{n-1},
+// a_n, rho_n, h s_n^2, a_n / h} (h = rescale/2; the stored vectors are scaled,
+// v_n = s_n u_n); counter[0] = n, counter[1] the ticket of the last-block sums
+// (zeroed by init).
+// apply: wt = A u_n - rho_n u_{n-1} into p.y (= u_{n-1}), p.x = u_n;
+//        a_n = h s_n^2 Re <u_n|wt> to sc[3] and a_out[n];
+// update: u_{n+1} = wt - (a_n / h) u_n (in place); b_{n+1} = h s_n ||u_{n+1}||
+//        to b_out[n], the next scalars, n + 1;
 // both use part[grid] doubles of per-block sums (grids from hay_grids);
 // init: s_0 from the ||psi0||^2 per-warp partials of launch_dot.
 cudaError_t launch_hay_apply(const SweepVariant &v, const SweepParams &p, double *sc, double half_rescale,
                              double *part, unsigned *ticket, double *a_out, const int *counter, int grid,
                              cudaStream_t s);
 cudaError_t launch_hay_update(const SweepVariant &v, const void *u, void *w, int64_t nslices, double *sc,
-                              double *part, unsigned *ticket, double *b_out, int *counter, int grid,
-                              cudaStream_t s);
-cudaError_t launch_hay_init(const double2 *partials, int64_t W, double *sc, int *counter, cudaStream_t s);
+                              double half_rescale, double *part, unsigned *ticket, double *b_out, int *counter,
+                              int grid, cudaStream_t s);
+cudaError_t launch_hay_init(const double2 *partials, int64_t W, double *sc, double half_rescale, int *counter,
+                            cudaStream_t s);
 // Whole-wave grids of the product and update passes for this operator.
 void hay_grids(const SweepVariant &v, int num_sms, int *apply_grid, int *update_grid);
 cudaError_t launch_hay_ldos(const double *a, const double *b, int M, const double *energies, int n_e,

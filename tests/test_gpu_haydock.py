@@ -47,6 +47,12 @@ def test_haydock_stencil_and_chain_stop(orc):
     a2, b2 = tb.tbpm_haydock(c2, ti.site_state(2, 0), 6)
     # (the GPU applies (rescale/2) * (2H/rescale), so the zero is exact only to rounding)
     assert abs(b2[0] - 8.1) < 1e-13 and np.all(b2[1:] == 0) and np.all(np.abs(a2) < 1e-12)
+    # a long run past the end stays at exact zeros (no growth of the residual), FP64 and FP32
+    for prec in (tb.TBPM_FP64, tb.TBPM_FP32):
+        c3 = tb.tbpm_create(h2.n, h2.row_ptr, h2.col, h2.val, 9.0, tb.make_opts(precision=prec))
+        a3, b3 = tb.tbpm_haydock(c3, ti.site_state(2, 0), 1500)
+        assert np.all(np.isfinite(a3)) and np.all(np.isfinite(b3))
+        assert np.all(b3[1:] == 0) and np.all(a3[2:] == 0) and abs(b3[0] - 8.1) < 1e-5
 
 
 def test_haydock_deterministic_and_launch_order_neutral(orc):
