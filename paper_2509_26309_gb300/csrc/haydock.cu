@@ -18,10 +18,9 @@
 // forms u_{n+1} in place with ||u_{n+1}||^2.
 // Each pass sums its dot per block in a fixed order; the last block of the grid
 // to finish (found by a ticket counter, nothing waits) adds the per-block sums
-// in block order, so the total does not depend on which block is last, and
-// updates a_n, or b_{n+1} and the scales. Two launches per level, both
-// programmatic dependent launches. The stored operator is A = 2H/rescale, so
-// H x = (rescale/2) A x.
+// in a fixed order, so the total does not depend on which block is last, and
+// updates a_n, or b_{n+1} and the scalars. Two launches per level, both
+// programmatic dependent launches.
 #include "sweep_ops.cuh"
 
 namespace tbpm {
