@@ -130,9 +130,10 @@ def tbpm_strerror(status: int) -> str:
     return lib().tbpm_strerror(int(status)).decode()
 
 
-def _check(status: int, what: str):
+def _check(status: int, what: str, ctx: "Ctx | None" = None):
     if status != TBPM_OK:
-        raise TbpmError(status, what)
+        detail = lib().tbpm_last_error(ctx.handle).decode() if ctx is not None and ctx.handle else ""
+        raise TbpmError(status, f"{what} [{detail}]" if detail else what)
 
 
 # ------------------------------------------------------------ marshalling
@@ -266,7 +267,7 @@ def tbpm_batch_dos_corr(ctx: Ctx, psi0, dt, n_steps: int, out=None):
     if out is None:
         out = _alloc((g, n_steps + 1), np.complex128, cuda, a.device if cuda else None)
     _check(lib().tbpm_batch_dos_corr(ctx.handle, _ptr(a), dt.ctypes.data_as(C.c_void_p), int(n_steps),
-                                     _ptr(out)), "tbpm_batch_dos_corr")
+                                     _ptr(out)), "tbpm_batch_dos_corr", ctx)
     return out
 
 
@@ -296,7 +297,7 @@ def tbpm_dos_corr(ctx: Ctx, psi0, dt: float, n_steps: int, out=None):
     if out is None:
         out = _alloc((ns, n_steps + 1), np.complex128, cuda, a.device if cuda else None)
     _check(lib().tbpm_dos_corr(ctx.handle, _ptr(a), ns, float(dt), int(n_steps), _ptr(out)),
-           "tbpm_dos_corr")
+           "tbpm_dos_corr", ctx)
     return out[0] if (a.ndim == 1 and out.shape[0] == 1) else out
 
 
@@ -307,7 +308,7 @@ def tbpm_propagate(ctx: Ctx, psi0, dt: float, n_steps: int, with_corr: bool = Fa
     psi = _alloc((ns, ctx.n), np.complex128, cuda, dev)
     corr = _alloc((ns, n_steps + 1), np.complex128, cuda, dev) if with_corr else None
     _check(lib().tbpm_propagate(ctx.handle, _ptr(a), ns, float(dt), int(n_steps), _ptr(psi),
-                                _ptr(corr) if corr is not None else None), "tbpm_propagate")
+                                _ptr(corr) if corr is not None else None), "tbpm_propagate", ctx)
     if a.ndim == 1:
         psi = psi[0]
         corr = corr[0] if corr is not None else None
@@ -319,7 +320,7 @@ def kpm_moments(ctx: Ctx, psi0, M: int, out=None):
     a, ns, cuda = _complex_in(psi0, ctx.n)
     if out is None:
         out = _alloc((ns, M), np.complex128, cuda, a.device if cuda else None)
-    _check(lib().kpm_moments(ctx.handle, _ptr(a), ns, int(M), _ptr(out)), "kpm_moments")
+    _check(lib().kpm_moments(ctx.handle, _ptr(a), ns, int(M), _ptr(out)), "kpm_moments", ctx)
     return out[0] if (a.ndim == 1 and out.shape[0] == 1) else out
 
 
@@ -333,7 +334,7 @@ def tbpm_quasi_eigenstates(ctx: Ctx, psi0, dt: float, n_steps: int, energies):
     n_e = int(energies.shape[0])
     out = _alloc((n_e, ctx.n), np.complex128, cuda, a.device if cuda else None)
     _check(lib().tbpm_quasi_eigenstates(ctx.handle, _ptr(a), float(dt), int(n_steps), _ptr(energies), n_e,
-                                        _ptr(out)), "tbpm_quasi_eigenstates")
+                                        _ptr(out)), "tbpm_quasi_eigenstates", ctx)
     return out
 
 
@@ -345,7 +346,7 @@ def tbpm_haydock(ctx: Ctx, psi0, M: int):
     dev = a_.device if cuda else None
     a = _alloc((M,), np.float64, cuda, dev)
     b = _alloc((M,), np.float64, cuda, dev)
-    _check(lib().tbpm_haydock(ctx.handle, _ptr(a_), int(M), _ptr(a), _ptr(b)), "tbpm_haydock")
+    _check(lib().tbpm_haydock(ctx.handle, _ptr(a_), int(M), _ptr(a), _ptr(b)), "tbpm_haydock", ctx)
     return a, b
 
 
@@ -358,7 +359,7 @@ def tbpm_haydock_ldos(ctx: Ctx, a, b, energies, eta: float):
         energies = np.ascontiguousarray(energies, dtype=np.float64)
     out = _alloc((energies.shape[0],), np.float64, cuda, a.device if cuda else None)
     _check(lib().tbpm_haydock_ldos(ctx.handle, _ptr(a), _ptr(b), int(a.shape[0]), _ptr(energies),
-                                   int(energies.shape[0]), float(eta), _ptr(out)), "tbpm_haydock_ldos")
+                                   int(energies.shape[0]), float(eta), _ptr(out)), "tbpm_haydock_ldos", ctx)
     return out
 
 
@@ -372,7 +373,7 @@ def tbpm_dos_from_corr(ctx: Ctx, corr, dt: float):
     e = _alloc((2 * n_steps,), np.float64, cuda, dev)
     d = _alloc((2 * n_steps,), np.float64, cuda, dev)
     _check(lib().tbpm_dos_from_corr(ctx.handle, _ptr(corr), int(n_steps), float(dt), _ptr(e), _ptr(d)),
-           "tbpm_dos_from_corr")
+           "tbpm_dos_from_corr", ctx)
     return e, d
 
 
@@ -385,7 +386,7 @@ def kpm_dos_jackson(ctx: Ctx, mu, n_e: int):
     e = _alloc((n_e,), np.float64, cuda, dev)
     r = _alloc((n_e,), np.float64, cuda, dev)
     _check(lib().kpm_dos_jackson(ctx.handle, _ptr(mu), int(mu.shape[-1]), int(n_e), _ptr(e), _ptr(r)),
-           "kpm_dos_jackson")
+           "kpm_dos_jackson", ctx)
     return e, r
 
 
@@ -401,7 +402,8 @@ def tbpm_set_current(ctx: Ctx, row_ptr, col, jx, jy) -> None:
     nnz = int(row_ptr[-1])
     if col.shape != (nnz,) or jx.shape != (nnz,) or jy.shape != (nnz,):
         raise ValueError("col, jx and jy must have row_ptr[n] entries")
-    _check(lib().tbpm_set_current(ctx.handle, _ptr(row_ptr), _ptr(col), _ptr(jx), _ptr(jy)), "tbpm_set_current")
+    _check(lib().tbpm_set_current(ctx.handle, _ptr(row_ptr), _ptr(col), _ptr(jx), _ptr(jy)), "tbpm_set_current",
+           ctx)
 
 
 def tbpm_ac_corr(ctx: Ctx, psi0, beta: float, mu: float, dt: float, n_steps: int, out=None):
@@ -412,7 +414,7 @@ def tbpm_ac_corr(ctx: Ctx, psi0, beta: float, mu: float, dt: float, n_steps: int
     if out is None:
         out = _alloc((4, n_steps + 1), np.complex128, cuda, a.device if cuda else None)
     _check(lib().tbpm_ac_corr(ctx.handle, _ptr(a), float(beta), float(mu), float(dt), int(n_steps), _ptr(out)),
-           "tbpm_ac_corr")
+           "tbpm_ac_corr", ctx)
     return out
 
 
@@ -429,7 +431,7 @@ def tbpm_ac_cond(ctx: Ctx, corr, dt: float, beta: float, area: float, omegas):
     n_w = int(omegas.shape[0])
     out = _alloc((4, n_w), np.float64, cuda, corr.device if cuda else None)
     _check(lib().tbpm_ac_cond(ctx.handle, _ptr(corr), n_steps, float(dt), float(beta), float(area), _ptr(omegas),
-                              n_w, _ptr(out)), "tbpm_ac_cond")
+                              n_w, _ptr(out)), "tbpm_ac_cond", ctx)
     return out
 
 
@@ -440,5 +442,5 @@ def tbpm_last_error(ctx: Ctx) -> str:
 
 def tbpm_get_info(ctx: Ctx) -> dict:
     info = tbpm_info()
-    _check(lib().tbpm_get_info(ctx.handle, C.byref(info)), "tbpm_get_info")
+    _check(lib().tbpm_get_info(ctx.handle, C.byref(info)), "tbpm_get_info", ctx)
     return {name: getattr(info, name) for name, _ in tbpm_info._fields_}

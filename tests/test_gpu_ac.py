@@ -122,6 +122,7 @@ def test_ac_errors():
         tb.tbpm_ac_corr(ctx, psi0, 5.0, 0.0, 0.3, 4)              # no current operators
     assert e.value.status == tb.TBPM_ERR_ARG
     assert "tbpm_set_current" in tb.tbpm_last_error(ctx)
+    assert "no current operators" in str(e.value)                 # the detail rides on the exception
     tb.tbpm_set_current(ctx, *cur.as_tuple())
     with pytest.raises(tb.TbpmError) as e:
         tb.tbpm_ac_corr(ctx, psi0, 5000.0, 0.0, 0.3, 4)           # Fermi series too long
