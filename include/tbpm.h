@@ -46,7 +46,9 @@ extern "C" {
 #define TBPM_ERR_TIMEOUT       -7  /* a bounded device wait gave up (reserved: no
                                        kernel of this library waits on a flag; all
                                        device-side waits are block or cluster
-                                       barriers)                                  */
+                                       barriers and the hardware wait of a
+                                       programmatic launch for the kernel before
+                                       it in the stream)                         */
 #define TBPM_ERR_NO_DEVICE     -8  /* no usable sm_103 GPU                         */
 #define TBPM_ERR_UNSUPPORTED   -9  /* valid request this build does not serve     */
 
