@@ -73,9 +73,11 @@ extern "C" {
                                           16 x 8192 (FP32) padded rows; the result
                                           is the same either way                   */
 #define TBPM_F_AUTOTUNE           0x10u /* at create, time middle sweeps of this
-                                          operator for grids of 1 .. occupancy
-                                          blocks per SM (and twice occupancy) and
-                                          keep the fastest for the context's life */
+                                          operator over launch shapes (block width
+                                          128 .. 1024 threads, 1, 2 or 4 32-row
+                                          slices per warp iteration, grids of
+                                          whole waves) and keep the fastest for the
+                                          context's life (tbpm_info reports it)   */
 #define TBPM_F_NO_TBLOCK          0x20u /* FP32 monolayer stencil contexts run each
                                           time step's sweeps in temporally blocked
                                           launches (several sweeps per pass over a
@@ -97,10 +99,19 @@ typedef struct tbpm_opts {
     void *stream;        /* cudaStream_t to order work on; NULL = the legacy
                             default stream of the device                           */
     double bessel_tol;   /* Chebyshev cutoff |J_k| < tol; 0 selects 1e-12          */
+    int block_threads;   /* launch shape of the single-state sweeps: threads per
+                            block, 128 | 256 | 512 | 1024; 0 selects 512. 1024 and
+                            slices_per_warp > 1 are built for the stored-matrix
+                            path only (TBPM_ERR_UNSUPPORTED on a stencil)         */
+    int slices_per_warp; /* 32-row slices a warp works on at once: 1 | 2 | 4 (2
+                            and 4 with at most 512 threads); 0 selects 1. The
+                            grid is whole waves of the shape's occupancy.
+                            TBPM_F_AUTOTUNE replaces both with the tuned shape    */
 } tbpm_opts;
 
 /* Fills *opts with the defaults: FP64, PATH_AUTO, no flags, current device,
- * legacy default stream, tolerance 1e-12. Returns TBPM_ERR_ARG if opts is NULL. */
+ * legacy default stream, tolerance 1e-12, the default launch shape (512
+ * threads, one slice per warp). Returns TBPM_ERR_ARG if opts is NULL. */
 int tbpm_default_opts(tbpm_opts *opts);
 
 typedef struct tbpm_ctx tbpm_ctx;
@@ -333,12 +344,16 @@ int tbpm_ac_cond(tbpm_ctx *ctx, const double *corr, int n_steps, double dt, doub
  *   rescale  > 0;  psi0 DEVICE double[2n];  dt, n_steps as tbpm_dos_corr
  *   corr     DEVICE double[2(n_steps+1)]: C(t_0..t_n_steps)
  *   stream   cudaStream_t, or NULL for the legacy default stream
- * The call blocks until the number of series terms is known (one 4-byte
+ * Every call waits on `stream` for the number of series terms (one 4-byte
  * device-to-host read), then enqueues the sweeps on `stream` and returns;
- * synchronise the stream before reading corr. Its first call on a device
- * looks up the static array's device address, so make that first call before
- * any stream capture. All calls share the array: calls that overlap on the
- * GPU (other streams, threads or processes on the same device) race on it. */
+ * synchronise the stream before reading corr. The first call on a device
+ * (and the first after that device's context was reset) looks up the static
+ * array's device address with that device current; make that first call
+ * before any stream capture. The array is per process and per device: all
+ * calls of one process on one device share it and it keeps the last call's
+ * contents, so calls of one process that overlap on the GPU (other streams
+ * or host threads on the same device) race on it. Other processes have their
+ * own copy. */
 int tbpm_dos_corr_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col,
                           const double *val, double rescale, const double *psi0, double dt,
                           int n_steps, double *corr, void *stream);
@@ -378,12 +393,28 @@ typedef struct tbpm_info {
     double gershgorin;         /* max_i sum_j |H_ij|                            */
     double rescale;
     int grid_blocks;           /* blocks of the single-state sweep grid         */
-    int tuned;                 /* 1 when the grid was chosen by the autotuner   */
+    int tuned;                 /* 1 when the shape was chosen by the autotuner  */
     int fermi_terms;           /* Fermi series length of the last tbpm_ac_corr  */
+    int block_threads;         /* threads per block of the single-state sweeps  */
+    int slices_per_warp;       /* 32-row slices a warp works on at once         */
+    int tune_candidates;       /* launch shapes the autotuner timed (0: none)   */
+    double tune_default_us;    /* autotuner: middle sweep at the default shape  */
+    double tune_best_us;       /* autotuner: middle sweep at the chosen shape   */
 } tbpm_info;
 
 /* Fills *info with the context's layout and the counters of its last call. */
 int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info);
+
+/* tbpm_fp64_peak: a measurement helper with no counterpart in the paper. It
+ * times `reps` launches (after one warm-up) of a kernel that issues only
+ * independent FP64 FMAs (8 chains per thread, `iters` rounds, 1024 threads on
+ * every SM of `device`; -1 = the current device) and reports the fastest as
+ * FP64 TFLOP/s (2 per FMA) in *tflops and its duration in *ms_per_launch (may
+ * be NULL): the measured ceiling of the FP64 sweeps, whose FP64 instructions
+ * bound them on GB300. Allocates and frees a small device buffer; blocks the
+ * host. 1 <= iters <= 2^26, reps >= 1, else TBPM_ERR_ARG; no GPU:
+ * TBPM_ERR_NO_DEVICE. */
+int tbpm_fp64_peak(int device, int iters, int reps, double *tflops, double *ms_per_launch);
 
 /* A static, human-readable name for a status code. */
 const char *tbpm_strerror(int status);

@@ -10,7 +10,7 @@ from .tbpm import (  # noqa: F401
     tbpm_dos_from_corr, kpm_dos_jackson, tbpm_get_info, tbpm_strerror,
     tbpm_create_batch, tbpm_batch_dos_corr, tbpm_propagate, tbpm_dos_corr_noalloc,
     tbpm_haydock, tbpm_haydock_ldos, tbpm_quasi_eigenstates,
-    tbpm_set_current, tbpm_ac_corr, tbpm_ac_cond, TBPM_FERMI_MAX_TERMS, tbpm_last_error,
+    tbpm_set_current, tbpm_ac_corr, tbpm_ac_cond, TBPM_FERMI_MAX_TERMS, tbpm_last_error, tbpm_fp64_peak,
     TBPM_OK, TBPM_ERR_ARG, TBPM_ERR_CSR, TBPM_ERR_NOT_HERMITIAN, TBPM_ERR_RESCALE,
     TBPM_ERR_OOM, TBPM_ERR_CUDA, TBPM_ERR_TIMEOUT, TBPM_ERR_NO_DEVICE, TBPM_ERR_UNSUPPORTED,
     TBPM_FP64, TBPM_FP32, TBPM_PATH_AUTO, TBPM_PATH_SELL, TBPM_PATH_STENCIL,

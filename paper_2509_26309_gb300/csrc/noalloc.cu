@@ -12,16 +12,24 @@
 // calls no cudaMalloc, cudaFree or other allocating routine.
 //
 // The array's host-side name is only a stand-in for the device symbol, so the
-// host never passes it to a kernel: on its first call on a device, with that
-// device current, the entry point looks the device address up with
-// cudaGetSymbolAddress and caches it; that first call should therefore come
-// before any stream capture. All calls share the array and it keeps the last
-// call's contents: every call writes each scratch element before reading it
-// (the coefficient kernel fills the coefficients and K, psi is copied from
-// psi0, each Clenshaw term is written in full before it is read, and each
-// step's dot partials are written before they are reduced), so nothing has
-// to start at zero. Calls that overlap on the GPU (on different streams,
-// threads or processes of the same device context) race on the array.
+// host never passes it to a kernel. The device address is looked up with
+// cudaGetSymbolAddress, with the device current, on the first call on each
+// device, and again on the first call after that device's context has been
+// replaced (cudaDeviceReset reloads the module, and the array may move): the
+// cache is keyed by the context's process-unique id. That first call should
+// therefore come before any stream capture. Every call waits on its stream for
+// the term count (a 4-byte device-to-host read).
+//
+// The array is per process and per device. All calls of one process on one
+// device share it, and it keeps the last call's contents: every call writes
+// each scratch element before reading it (the coefficient kernel fills the
+// coefficients and K, psi is copied from psi0, each Clenshaw term is written in
+// full before it is read, and each step's dot partials are written before they
+// are reduced), so nothing has to start at zero. Calls of one process that
+// overlap on the GPU (other streams or host threads on the same device) race on
+// the array; other processes have their own copy.
+#include <cuda.h>      // CUcontext and CUresult only: the two driver calls are reached through the runtime
+
 #include <cmath>
 #include <mutex>
 
@@ -43,7 +51,11 @@ constexpr size_t kScratchBytes = kPsiOff + 3 * kVecBytes;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;
-void *g_addr[64] = {};                                // device address of g_scratch per device
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;                    // context the address belongs to (0: none yet)
+    void *addr = nullptr;
+};
+ScratchAddr g_addr[64];                               // device address of g_scratch per device
 
 // Clenshaw sweep on a plain CSR matrix with complex values (the operator is
 // scaled in the kernel): y = a psi + beta (s H x) - z, s = 2/rescale. The kinds
@@ -127,7 +139,35 @@ __global__ void __launch_bounds__(kBlock) self_dot(int64_t n, const double2 *a, 
     }
 }
 
-// Device address of g_scratch for the current device (looked up once per device).
+// Process-unique id of the calling thread's current context (0 if there is
+// none yet). The driver's cuCtxGetCurrent and cuCtxGetId are reached through
+// the runtime's entry-point query, so the library needs no link to libcuda.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+cudaError_t current_context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {                    // called under g_mu
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess || q1 != cudaDriverEntryPointSuccess || !f1) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess || q2 != cudaDriverEntryPointSuccess || !f2) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS) return cudaErrorUnknown;
+    *id = 0;
+    if (c && get_id(c, id) != CUDA_SUCCESS) return cudaErrorUnknown;
+    return cudaSuccess;
+}
+
+// Device address of g_scratch for the current device, looked up (with the
+// device current) once per device and context.
 cudaError_t scratch_address(unsigned char **out)
 {
     int dev = 0;
@@ -135,13 +175,18 @@ cudaError_t scratch_address(unsigned char **out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    unsigned long long id = 0;
+    if ((e = current_context_id(&id)) != cudaSuccess) return e;
+    if (id == 0 || id != g_addr[dev].ctx_id || !g_addr[dev].addr) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
+        e = cudaGetSymbolAddress(&p, g_scratch);      // also makes the device's context current
         if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
+        if ((e = current_context_id(&id)) != cudaSuccess) return e;
+        if (id == 0) return cudaErrorDeviceUninitialized;
+        g_addr[dev].ctx_id = id;
+        g_addr[dev].addr = p;
     }
-    *out = static_cast<unsigned char *>(g_addr[dev]);
+    *out = static_cast<unsigned char *>(g_addr[dev].addr);
     return cudaSuccess;
 }
 

@@ -183,13 +183,13 @@ __device__ __forceinline__ void warp_sum_f2(F2Sum &a)
     }
 }
 
-// Block sum of NV two-sum pairs for blocks of kBlockB1 threads, in FP32 up to
-// one FP64 conversion per value; the results are valid in thread 0. Every
+// Block sum of NV two-sum pairs for blocks of up to 1024 threads, in FP32 up
+// to one FP64 conversion per value; the results are valid in thread 0. Every
 // thread of the block calls it.
 template <int NV>
 __device__ __forceinline__ void block_sum_f2(F2Sum (&a)[NV], double (&out)[NV])
 {
-    __shared__ float2 sm[NV][kBlockB1 / 32];
+    __shared__ float2 sm[NV][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {

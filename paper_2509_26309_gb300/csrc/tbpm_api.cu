@@ -297,8 +297,14 @@ SweepVariant variant(const tbpm_ctx *ctx, int states)
     v.real_values = ctx->op == OP_SELL ? ctx->sell.real_values : true;
     v.states = states;
     v.pdl = !(ctx->flags & TBPM_F_NO_PDL);
+    v.block = ctx->sw_block;
+    v.spw = ctx->sw_spw;
     return v;
 }
+
+// Warps of the single-state sweep grid: the number of per-warp dot partials a
+// final sweep of one instance writes per slot.
+int64_t sweep_warps(const tbpm_ctx *ctx) { return (int64_t)ctx->nblk * ctx->sw_block / 32; }
 
 void fill_operator(const tbpm_ctx *ctx, SweepParams &p)
 {
@@ -345,7 +351,9 @@ int ensure_work(tbpm_ctx *ctx, int states, size_t out_elems, size_t stage_double
         CU(cudaMemsetAsync(ctx->d_b1, 0, vb, ctx->stream));
         // single-state partials: one per slice; 16-state partials: one per block and state
         const size_t nsl = (size_t)(ctx->n_pad / kSlice);
-        const size_t W = (size_t)std::max(ctx->nblk, ctx->nblk_kpm) * (kBlockB1 / 32);
+        // (the sweeps' per-warp partials, and those of the 512-thread dot and KPM kernels)
+        const size_t W = std::max<size_t>((size_t)sweep_warps(ctx),
+                                          (size_t)std::max(ctx->nblk, ctx->nblk_kpm) * (kBlockB1 / 32));
         const size_t per_slot = std::max<size_t>(std::max(std::max(2 * nsl, 2 * W), (size_t)ctx->num_sms * 32),
                                                  (size_t)ctx->nblk16 * kMaxBlockStates);
         ctx->partials_cap = (size_t)(kChunk + 1) * per_slot;
@@ -416,7 +424,7 @@ int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, int B, int64_t ld, cudaStre
     const int nseg = std::max(1, ctx->ninst);
     p.slice_inst = ctx->d_slice_inst;                    // nullptr for a single instance
     // partials per slot: per slice for a batch, per warp of the grid otherwise
-    const int64_t npart = ctx->ninst > 0 ? p.nslices : (int64_t)ctx->nblk * (kBlockB1 / 32);
+    const int64_t npart = ctx->ninst > 0 ? p.nslices : sweep_warps(ctx);
     void *Bv[2] = {ctx->d_b0, ctx->d_b1};
     for (int d = 0; d < len; ++d) {
         // FIRST: b_{K-2} = c_{K-2} psi + c_{K-1} A psi  -> B[0]
@@ -853,6 +861,8 @@ int tbpm_default_opts(tbpm_opts *o)
     o->device = -1;
     o->stream = nullptr;
     o->bessel_tol = 0.0;
+    o->block_threads = 0;
+    o->slices_per_warp = 0;
     return TBPM_OK;
 }
 
@@ -884,6 +894,29 @@ static int check_opts(const tbpm_opts *in, tbpm_opts *o)
         return TBPM_ERR_ARG;
     if (o->bessel_tol == 0.0) o->bessel_tol = 1e-12;
     if (!(o->bessel_tol > 0.0 && o->bessel_tol < 1e-2)) return TBPM_ERR_ARG;
+    if (o->block_threads == 0) o->block_threads = kBlockB1;
+    if (o->slices_per_warp == 0) o->slices_per_warp = 1;
+    if (o->block_threads != 128 && o->block_threads != 256 && o->block_threads != 512 && o->block_threads != 1024)
+        return TBPM_ERR_ARG;
+    if (o->slices_per_warp != 1 && o->slices_per_warp != 2 && o->slices_per_warp != 4) return TBPM_ERR_ARG;
+    return TBPM_OK;
+}
+
+// Applies the requested launch shape of the single-state sweeps once the
+// operator is known: TBPM_ERR_UNSUPPORTED if it is not built for this operator;
+// the grid is whole waves of the shape's middle-sweep occupancy.
+static int apply_shape(tbpm_ctx *ctx, const tbpm_opts &o)
+{
+    if (o.block_threads == kBlockB1 && o.slices_per_warp == 1) return TBPM_OK;
+    SweepVariant v = variant(ctx, 1);
+    v.block = o.block_threads;
+    v.spw = o.slices_per_warp;
+    if (!sweep_shape_built(v)) return TBPM_ERR_UNSUPPORTED;
+    const int occ = sweep_shape_occupancy(v, ctx->d_slice_inst != nullptr);
+    if (occ < 1) return TBPM_ERR_UNSUPPORTED;
+    ctx->sw_block = v.block;
+    ctx->sw_spw = v.spw;
+    ctx->nblk = occ * ctx->num_sms;
     return TBPM_OK;
 }
 
@@ -898,16 +931,21 @@ static int finish_create(tbpm_ctx *ctx, const tbpm_opts &o)
 }
 
 // Autotuner (TBPM_F_AUTOTUNE): times middle sweeps of this context's operator
-// for grids of 1 .. occupancy blocks per SM (and twice the occupancy) and
-// keeps the fastest. The dot partials are per warp of the chosen grid, which
-// is then fixed for the life of the context, so results stay reproducible
-// from call to call. Runs once, before any graph is captured.
+// over launch shapes: block widths of 128, 256, 512 and 1024 threads, 1, 2 or
+// 4 consecutive 32-row slices per warp iteration (the shapes sweep_shape_built
+// accepts for this operator), and for each the grids of occupancy/2,
+// occupancy and twice the occupancy blocks per SM (all of 1 .. occupancy when
+// that is at most 4). Every candidate is timed over 3 sweeps after one
+// warm-up; the four fastest and the default shape (512 threads, one slice,
+// the occupancy grid) are timed again over 10 sweeps, and the fastest of
+// those is kept for the life of the context. The single-instance dot
+// partials are per warp of the chosen grid, which is then fixed, so results
+// stay reproducible from call to call. Runs once, before any graph is captured.
 static int autotune(tbpm_ctx *ctx)
 {
     if (ctx->tuned) return TBPM_OK;
     int rc;
     if ((rc = ensure_work(ctx, 1, 1, 0))) return rc;
-    const int occ = std::max(1, ctx->nblk / ctx->num_sms);
     CU(cudaMemsetAsync(ctx->d_coef, 0, sizeof(double2) * kMaxTerms * std::max(1, ctx->ninst), ctx->stream));
     ctx->K_cached = -1;
     ctx->dt_cached.clear();
@@ -920,33 +958,82 @@ static int autotune(tbpm_ctx *ctx)
     p.z = ctx->d_b1;
     p.ia = 1; p.ib = -1; p.ic = -1; p.bscale = 1.0;
     p.slice_inst = ctx->d_slice_inst;
-    const SweepVariant v = variant(ctx, 1);
+    const bool multi = ctx->d_slice_inst != nullptr;
+    struct Cand {
+        int block, spw, grid;
+        double us;
+    };
+    std::vector<Cand> cands;
+    const SweepVariant base = variant(ctx, 1);
+    const int def_grid = ctx->nblk;
+    for (int block : {128, 256, 512, 1024})
+        for (int spw : {1, 2, 4}) {
+            SweepVariant v = base;
+            v.block = block;
+            v.spw = spw;
+            if (!sweep_shape_built(v)) continue;
+            const int occ = sweep_shape_occupancy(v, multi);
+            if (occ < 1) continue;
+            std::vector<int> ks;
+            if (occ <= 4)
+                for (int k = 1; k <= occ; ++k) ks.push_back(k);
+            else
+                ks = {occ / 2, occ};
+            ks.push_back(2 * occ);
+            for (int k : ks) cands.push_back({block, spw, k * ctx->num_sms, 0.0});
+        }
+    bool have_def = false;
+    for (const Cand &c : cands) have_def |= c.block == kBlockB1 && c.spw == 1 && c.grid == def_grid;
+    if (!have_def) cands.push_back({kBlockB1, 1, def_grid, 0.0});
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_g = ctx->nblk;
-    ctx->tune_ms.clear();
-    for (int k = 1; k <= 2 * occ; ++k) {
-        if (k > occ && k != 2 * occ) continue;
-        const int grid = k * ctx->num_sms;
-        CU(launch_sweep(v, SW_MID, true, true, p, grid, ctx->stream));        // warm
+    auto time_us = [&](const Cand &c, int reps, double *us) -> int {
+        SweepVariant v = base;
+        v.block = c.block;
+        v.spw = c.spw;
+        CU(launch_sweep(v, SW_MID, true, true, p, c.grid, ctx->stream));        // warm
         CU(cudaEventRecord(e0, ctx->stream));
-        for (int r = 0; r < 3; ++r) CU(launch_sweep(v, SW_MID, true, true, p, grid, ctx->stream));
+        for (int r = 0; r < reps; ++r) CU(launch_sweep(v, SW_MID, true, true, p, c.grid, ctx->stream));
         CU(cudaEventRecord(e1, ctx->stream));
         CU(cudaEventSynchronize(e1));
         float ms = 0.f;
         CU(cudaEventElapsedTime(&ms, e0, e1));
-        ctx->tune_ms.emplace_back(k, ms / 3);
-        if (ms < best) { best = ms; best_g = grid; }
+        *us = 1e3 * ms / reps;
+        return TBPM_OK;
+    };
+    for (Cand &c : cands)
+        if ((rc = time_us(c, 3, &c.us))) break;
+    std::vector<Cand> fin;
+    if (!rc) {
+        std::vector<Cand> sorted = cands;
+        std::sort(sorted.begin(), sorted.end(), [](const Cand &a, const Cand &b) { return a.us < b.us; });
+        for (size_t i = 0; i < sorted.size() && i < 4; ++i) fin.push_back(sorted[i]);
+        bool def_in = false;
+        for (const Cand &c : fin) def_in |= c.block == kBlockB1 && c.spw == 1 && c.grid == def_grid;
+        if (!def_in) fin.push_back({kBlockB1, 1, def_grid, 0.0});
+        for (Cand &c : fin)
+            if ((rc = time_us(c, 10, &c.us))) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    // work buffers and graphs depend on the grid: rebuild them for the new one
+    if (rc) return rc;
+    Cand best = fin[0];
+    double def_us = 0.0;
+    for (const Cand &c : fin) {
+        if (c.us < best.us) best = c;
+        if (c.block == kBlockB1 && c.spw == 1 && c.grid == def_grid) def_us = c.us;
+    }
+    // work buffers and graphs depend on the shape: rebuild them for the new one
     destroy_graphs(ctx);
-    ctx->nblk = best_g;
+    ctx->nblk = best.grid;
+    ctx->sw_block = best.block;
+    ctx->sw_spw = best.spw;
     ctx->cap_states = 0;
     ctx->tuned = true;
+    ctx->tune_candidates = (int)cands.size();
+    ctx->tune_default_us = def_us;
+    ctx->tune_best_us = best.us;
     return TBPM_OK;
 }
 
@@ -980,7 +1067,7 @@ int tbpm_create(tbpm_ctx **out, int64_t n, const int64_t *row_ptr, const int32_t
     ctx->n_pad = (n + kSlice - 1) / kSlice * kSlice;
     ctx->rescale = rescale;
     ctx->gershgorin = m.gershgorin;
-    if ((rc = finish_create(ctx, o)) || (rc = setup_sell(ctx, m)) ||
+    if ((rc = finish_create(ctx, o)) || (rc = setup_sell(ctx, m)) || (rc = apply_shape(ctx, o)) ||
         ((o.flags & TBPM_F_AUTOTUNE) && (rc = autotune(ctx)))) {
         tbpm_destroy(ctx);
         return rc;
@@ -1057,6 +1144,7 @@ int tbpm_create_lattice(tbpm_ctx **out, const tbpm_lattice *lat, double rescale,
             }
         }
     }
+    if (!rc) rc = apply_shape(ctx, o);
     if (!rc && (o.flags & TBPM_F_AUTOTUNE)) rc = autotune(ctx);
     if (rc) {
         tbpm_destroy(ctx);
@@ -1456,7 +1544,7 @@ int tbpm_create_batch(tbpm_ctx **out, int ninst, const tbpm_instance *inst, cons
     for (int g = 0; g < ninst; ++g)
         for (int64_t q = seg[g]; q < seg[g + 1]; ++q) sinst[q] = g;
     if ((rc = upload(ctx, (void **)&ctx->d_slice_inst, sinst)) || (rc = upload(ctx, (void **)&ctx->d_seg_off, seg)) ||
-        ((o.flags & TBPM_F_AUTOTUNE) && (rc = autotune(ctx)))) {
+        (rc = apply_shape(ctx, o)) || ((o.flags & TBPM_F_AUTOTUNE) && (rc = autotune(ctx)))) {
         tbpm_destroy(ctx);
         return rc;
     }
@@ -1941,6 +2029,11 @@ int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info)
     info->grid_blocks = ctx->nblk;
     info->tuned = ctx->tuned ? 1 : 0;
     info->fermi_terms = ctx->fermi_K;
+    info->block_threads = ctx->sw_block;
+    info->slices_per_warp = ctx->sw_spw;
+    info->tune_candidates = ctx->tune_candidates;
+    info->tune_default_us = ctx->tune_default_us;
+    info->tune_best_us = ctx->tune_best_us;
     return TBPM_OK;
 }
 

@@ -193,6 +193,8 @@ struct SweepVariant {
     bool real_values;
     int states;                   // B: 1 or 16
     bool pdl;                     // B = 1 sweeps as programmatic dependent launches
+    int block = kBlockB1;         // B = 1 sweeps: threads per block (32 .. 1024)
+    int spw = 1;                  // B = 1 sweeps: 32-row slices a warp works on at once
 };
 
 // ---------------------------------------------------------------- context
@@ -271,9 +273,15 @@ struct tbpm_ctx {
     int tb_grid = 0;
     int tb_kpm_grid = 0;
     int fermi_K = 0;                     // 0: no coefficients cached
-    // autotuner: (blocks per SM, ms per middle sweep) of each candidate grid
+    // launch shape of the single-state sweeps (nblk blocks of sw_block threads,
+    // sw_spw slices per warp iteration); dot partials: one per warp of that grid
+    int sw_block = tbpm::kBlockB1;
+    int sw_spw = 1;
+    // autotuner: candidates timed, middle-sweep microseconds at the default and
+    // at the chosen shape
     bool tuned = false;
-    std::vector<std::pair<int, float>> tune_ms;
+    int tune_candidates = 0;
+    double tune_default_us = 0.0, tune_best_us = 0.0;
     // cached executable graphs keyed by (kind, len, K, states)
     std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
     // counters of the last call
@@ -291,10 +299,27 @@ namespace tbpm {
 // Chebyshev coefficients c_k, k < kMaxTerms, and K into d_K (bessel.cu).
 cudaError_t launch_bessel(double x, double tol, double2 *d_coef, int *d_K, cudaStream_t s);
 
-// One Clenshaw sweep of the given kind (cheb_sweep.cu).
+// One Clenshaw sweep of the given kind (cheb_sweep.cu) at the launch shape
+// v.block x v.spw: every operator takes spw = 1 with blocks of up to 512
+// threads; the stored matrix also takes spw = 1 with 1024 threads and spw = 2
+// or 4 with up to 512 (cheb_sweep_shapes*.cu). Other shapes are refused
+// (cudaErrorInvalidValue).
 enum SweepKind { SW_FIRST = 0, SW_SECOND = 1, SW_MID = 2, SW_FINAL = 3 };
 cudaError_t launch_sweep(const SweepVariant &v, SweepKind kind, bool a_imag, bool has_z,
                          const SweepParams &p, int grid, cudaStream_t s);
+// Resident blocks per SM of the middle sweep at v's shape (0: shape not built).
+int sweep_shape_occupancy(const SweepVariant &v, bool multi);
+bool sweep_shape_built(const SweepVariant &v);
+// The stored-matrix shapes built in their own translation units.
+cudaError_t launch_sell_s1_b1024(const SweepVariant &v, SweepKind kind, bool a_imag, bool has_z,
+                                 const SweepParams &p, int grid, cudaStream_t s);
+cudaError_t launch_sell_s2_b512(const SweepVariant &v, SweepKind kind, bool a_imag, bool has_z,
+                                const SweepParams &p, int grid, cudaStream_t s);
+cudaError_t launch_sell_s4_b512(const SweepVariant &v, SweepKind kind, bool a_imag, bool has_z,
+                                const SweepParams &p, int grid, cudaStream_t s);
+int occupancy_sell_s1_b1024(const SweepVariant &v, bool multi);
+int occupancy_sell_s2_b512(const SweepVariant &v, bool multi);
+int occupancy_sell_s4_b512(const SweepVariant &v, bool multi);
 
 // KPM sweep (cheb_sweep.cu).
 cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cudaStream_t s);

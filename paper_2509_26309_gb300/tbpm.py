@@ -45,7 +45,8 @@ TBPM_LATTICE_AB_BILAYER = 1
 
 class tbpm_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("path", C.c_int), ("flags", C.c_uint),
-                ("device", C.c_int), ("stream", C.c_void_p), ("bessel_tol", C.c_double)]
+                ("device", C.c_int), ("stream", C.c_void_p), ("bessel_tol", C.c_double),
+                ("block_threads", C.c_int), ("slices_per_warp", C.c_int)]
 
 
 class tbpm_lattice(C.Structure):
@@ -57,7 +58,9 @@ class tbpm_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("path", C.c_int), ("precision", C.c_int),
                 ("real_values", C.c_int), ("num_terms", C.c_int), ("passes", C.c_int64),
                 ("kernel_launches", C.c_int64), ("gershgorin", C.c_double), ("rescale", C.c_double),
-                ("grid_blocks", C.c_int), ("tuned", C.c_int), ("fermi_terms", C.c_int)]
+                ("grid_blocks", C.c_int), ("tuned", C.c_int), ("fermi_terms", C.c_int),
+                ("block_threads", C.c_int), ("slices_per_warp", C.c_int), ("tune_candidates", C.c_int),
+                ("tune_default_us", C.c_double), ("tune_best_us", C.c_double)]
 
 
 class TbpmError(RuntimeError):
@@ -94,6 +97,7 @@ SIGNATURES = {
     "tbpm_batch_dos_corr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "tbpm_dos_corr_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                         C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p]),
+    "tbpm_fp64_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "tbpm_set_current": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tbpm_ac_corr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_int,
                                C.c_void_p]),
@@ -199,12 +203,14 @@ class Ctx:
 
 
 def make_opts(precision: int = TBPM_FP64, path: int = TBPM_PATH_AUTO, flags: int = 0,
-              device: int = -1, stream=None, bessel_tol: float = 0.0) -> tbpm_opts:
+              device: int = -1, stream=None, bessel_tol: float = 0.0, block_threads: int = 0,
+              slices_per_warp: int = 0) -> tbpm_opts:
     o = tbpm_opts()
     _check(lib().tbpm_default_opts(C.byref(o)), "tbpm_default_opts")
     o.precision, o.path, o.flags, o.device = precision, path, flags, device
     o.stream = stream if stream is None else C.c_void_p(int(stream))
     o.bessel_tol = bessel_tol
+    o.block_threads, o.slices_per_warp = block_threads, slices_per_warp
     return o
 
 
@@ -273,16 +279,53 @@ def tbpm_batch_dos_corr(ctx: Ctx, psi0, dt, n_steps: int, out=None):
 
 def tbpm_dos_corr_noalloc(n: int, row_ptr, col, val, rescale: float, psi0, dt: float,
                           n_steps: int, corr, stream=None) -> None:
-    """The allocation-free correlation call. Every array is a caller-owned CUDA
-    tensor (int64 row_ptr, int32 col, complex128 val, psi0 and corr); the call
-    allocates nothing and leaves corr to be read after the stream synchronises."""
-    for t in (row_ptr, col, val, psi0, corr):
+    """The allocation-free correlation call. Every array is a caller-owned,
+    contiguous CUDA tensor on one device: int64 row_ptr[n+1], int32 col[nnz],
+    complex128 val[nnz] (nnz = row_ptr[n]), psi0[n] and corr[>= n_steps+1].
+    The C call reads these buffers on the device only and cannot check their
+    sizes, so they are checked here before it runs (on psi0's device). The
+    call allocates nothing and leaves corr to be read after the stream
+    synchronises."""
+    import torch
+    want = (("row_ptr", row_ptr, torch.int64), ("col", col, torch.int32), ("val", val, torch.complex128),
+            ("psi0", psi0, torch.complex128), ("corr", corr, torch.complex128))
+    for name, t, dtype in want:
         if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
-            raise TypeError("tbpm_dos_corr_noalloc takes contiguous CUDA tensors")
+            raise TypeError(f"tbpm_dos_corr_noalloc: {name} must be a contiguous CUDA tensor")
+        if t.dtype != dtype:
+            raise TypeError(f"tbpm_dos_corr_noalloc: {name} must be {dtype}, not {t.dtype}")
+    for name, t, _ in want:
+        if t.device != psi0.device:
+            raise ValueError(f"tbpm_dos_corr_noalloc: {name} is on {t.device}, psi0 on {psi0.device}")
+    n, n_steps = int(n), int(n_steps)
+    if n >= 1:
+        if row_ptr.numel() != n + 1:
+            raise ValueError(f"tbpm_dos_corr_noalloc: row_ptr has {row_ptr.numel()} entries, not n + 1 = {n + 1}")
+        if psi0.numel() != n:
+            raise ValueError(f"tbpm_dos_corr_noalloc: psi0 has {psi0.numel()} entries, not n = {n}")
+        if n_steps >= 0 and corr.numel() < n_steps + 1:
+            raise ValueError(f"tbpm_dos_corr_noalloc: corr has {corr.numel()} entries, needs {n_steps + 1}")
+        if n <= TBPM_NOALLOC_MAX_N:
+            # the structure must lie inside col and val: row_ptr[0] = 0 and
+            # row_ptr[n] = nnz (two 8-byte reads into host scalars, no device
+            # allocation; monotonicity is the caller's)
+            r0, rn = int(row_ptr[0].item()), int(row_ptr[n].item())
+            if r0 != 0 or rn != col.numel() or col.numel() != val.numel():
+                raise ValueError("tbpm_dos_corr_noalloc: row_ptr[0] must be 0 and row_ptr[n] = col.numel() "
+                                 "= val.numel()")
     s = None if stream is None else C.c_void_p(int(stream))
-    _check(lib().tbpm_dos_corr_noalloc(int(n), _ptr(row_ptr), _ptr(col), _ptr(val), float(rescale),
-                                       _ptr(psi0), float(dt), int(n_steps), _ptr(corr), s),
-           "tbpm_dos_corr_noalloc")
+    with torch.cuda.device(psi0.device):
+        _check(lib().tbpm_dos_corr_noalloc(n, _ptr(row_ptr), _ptr(col), _ptr(val), float(rescale),
+                                           _ptr(psi0), float(dt), n_steps, _ptr(corr), s),
+               "tbpm_dos_corr_noalloc")
+
+
+def tbpm_fp64_peak(device: int = -1, iters: int = 50000, reps: int = 3) -> tuple[float, float]:
+    """(FP64 TFLOP/s, ms per launch) of an FMA-only kernel on the device: the
+    measured ceiling of the FP64 sweeps."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib().tbpm_fp64_peak(int(device), int(iters), int(reps), C.byref(tf), C.byref(ms)), "tbpm_fp64_peak")
+    return tf.value, ms.value
 
 
 def tbpm_destroy(ctx: Ctx) -> None:

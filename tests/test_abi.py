@@ -98,6 +98,11 @@ def test_rejects_small_rescale_and_bad_args():
     assert _create(h, opts=tb.make_opts(flags=every)) != tb.TBPM_ERR_ARG
     val = h.val.copy(); val[2] = np.nan
     assert _create(h, val=val) == tb.TBPM_ERR_ARG
+    # launch shapes: block widths 128..1024, 1, 2 or 4 slices per warp
+    for bt, spw in ((64, 1), (384, 1), (2048, 1), (512, 3), (512, 8), (-1, 1), (512, -2)):
+        assert _create(h, opts=tb.make_opts(block_threads=bt, slices_per_warp=spw)) == tb.TBPM_ERR_ARG, (bt, spw)
+    for bt, spw in ((128, 1), (256, 2), (512, 4), (1024, 1), (0, 0)):
+        assert _create(h, opts=tb.make_opts(block_threads=bt, slices_per_warp=spw)) != tb.TBPM_ERR_ARG, (bt, spw)
     l = B.lib()
     out = C.c_void_p()
     assert l.tbpm_create(C.byref(out), 0, None, None, None, 9.0, None) == tb.TBPM_ERR_ARG

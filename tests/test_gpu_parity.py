@@ -208,8 +208,9 @@ def test_propagate_fp32_renorm_and_batched(orc):
 
 
 def test_autotuned_grid(orc):
-    """The autotuner picks a grid (whole blocks per SM) once at create;
-    results match the oracle and repeat bit for bit on the context."""
+    """The autotuner picks a launch shape (block width, slices per warp, a grid
+    of whole blocks per SM) once at create; results match the oracle and repeat
+    bit for bit on the context."""
     h = ti.graphene_csr(128, 100, onsite=ti.anderson_onsite(25600, 1.0, 2))
     psi0 = ti.random_phase_state(h.n, 1)
     ctx = create(h, flags=tb.TBPM_F_AUTOTUNE | tb.TBPM_F_NO_CLUSTER)
@@ -217,11 +218,50 @@ def test_autotuned_grid(orc):
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert info["tuned"] == 1 and info["grid_blocks"] % sms == 0
+    assert info["block_threads"] in (128, 256, 512, 1024) and info["slices_per_warp"] in (1, 2, 4)
+    assert info["tune_candidates"] >= 10
+    assert 0 < info["tune_best_us"] <= info["tune_default_us"]
     c = tb.tbpm_dos_corr(ctx, psi0, DT, 40)
     assert np.max(np.abs(c - orc.dos_corr(h, 9.0, psi0, DT, 40))) <= TOL
     assert np.array_equal(c, tb.tbpm_dos_corr(ctx, psi0, DT, 40))
     mu = tb.kpm_moments(ctx, psi0, 100)
     assert np.max(np.abs(mu - orc.kpm_moments(h, 9.0, psi0, 100))) <= TOL
+
+
+SHAPES = [(128, 1), (256, 1), (512, 1), (1024, 1), (128, 2), (256, 2), (512, 2), (128, 4), (256, 4), (512, 4)]
+
+
+@pytest.mark.parametrize("bt,spw", SHAPES)
+def test_sweep_launch_shapes(orc, bt, spw):
+    """Every launch shape the autotuner can pick, on the stored-matrix path:
+    graphene with real and with complex hoppings (uniform slice width 3, a
+    ragged last group), a random Hermitian matrix with complex values (mixed
+    slice widths), FP64 and FP32, against the oracle."""
+    cases = [(ti.graphene_csr(37, 29, onsite=ti.anderson_onsite(2146, 1.0, 4)), tb.TBPM_FP64, TOL),
+             (ti.graphene_csr(37, 29, onsite=ti.anderson_onsite(2146, 1.0, 4), bond_phases=[0.3, 0.1, 0.2]),
+              tb.TBPM_FP64, TOL),
+             (ti.random_hermitian_csr(2500, 4, seed=6, scale=1.0), tb.TBPM_FP64, TOL),
+             (ti.graphene_csr(37, 29, onsite=ti.anderson_onsite(2146, 1.0, 4)), tb.TBPM_FP32, 3e-5)]
+    for h, prec, tol in cases:
+        rescale = max(9.0, 1.02 * ti.gershgorin_bound(h))
+        dt = math.pi / rescale
+        psi0 = ti.random_phase_state(h.n, 3)
+        ctx = tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, rescale,
+                             tb.make_opts(precision=prec, flags=tb.TBPM_F_NO_CLUSTER, block_threads=bt,
+                                          slices_per_warp=spw))
+        info = tb.tbpm_get_info(ctx)
+        assert (info["block_threads"], info["slices_per_warp"]) == (bt, spw)
+        c = tb.tbpm_dos_corr(ctx, psi0, dt, 60)
+        assert np.max(np.abs(c - orc.dos_corr(h, rescale, psi0, dt, 60))) <= tol, (bt, spw, prec)
+        assert np.array_equal(c, tb.tbpm_dos_corr(ctx, psi0, dt, 60))
+
+
+def test_stencil_rejects_stored_matrix_shapes():
+    for bt, spw in ((1024, 1), (512, 2)):
+        with pytest.raises(tb.TbpmError) as e:
+            tb.tbpm_create_lattice(tb.TBPM_LATTICE_GRAPHENE, 8, 8, ti.T_GRAPHENE, 0.0, None, 9.0,
+                                   tb.make_opts(path=tb.TBPM_PATH_STENCIL, block_threads=bt, slices_per_warp=spw))
+        assert e.value.status == tb.TBPM_ERR_UNSUPPORTED
 
 
 def test_dos_transforms(orc):
