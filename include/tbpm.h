@@ -72,12 +72,13 @@ extern "C" {
                                           systems of up to 16 x 4096 (FP64) or
                                           16 x 8192 (FP32) padded rows; the result
                                           is the same either way                   */
-#define TBPM_F_AUTOTUNE           0x10u /* at create, time middle sweeps of this
-                                          operator over launch shapes (block width
-                                          128 .. 1024 threads, 1, 2 or 4 32-row
-                                          slices per warp iteration, grids of
-                                          whole waves) and keep the fastest for the
-                                          context's life (tbpm_info reports it)   */
+#define TBPM_F_AUTOTUNE           0x10u /* at create, time whole time steps of
+                                          this operator's sweeps over launch
+                                          shapes (block width 128 .. 1024 threads,
+                                          1, 2 or 4 32-row slices per warp
+                                          iteration, grids of whole waves) and keep
+                                          the fastest for the context's life
+                                          (tbpm_info reports it)                  */
 #define TBPM_F_NO_TBLOCK          0x20u /* FP32 monolayer stencil contexts run each
                                           time step's sweeps in temporally blocked
                                           launches (several sweeps per pass over a
@@ -398,19 +399,21 @@ typedef struct tbpm_info {
     int block_threads;         /* threads per block of the single-state sweeps  */
     int slices_per_warp;       /* 32-row slices a warp works on at once         */
     int tune_candidates;       /* launch shapes the autotuner timed (0: none)   */
-    double tune_default_us;    /* autotuner: middle sweep at the default shape  */
-    double tune_best_us;       /* autotuner: middle sweep at the chosen shape   */
+    double tune_default_us;    /* autotuner: us per sweep (average over a time
+                                  step) at the default shape                    */
+    double tune_best_us;       /* autotuner: the same at the chosen shape       */
 } tbpm_info;
 
 /* Fills *info with the context's layout and the counters of its last call. */
 int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info);
 
 /* tbpm_fp64_peak: a measurement helper with no counterpart in the paper. It
- * times `reps` launches (after one warm-up) of a kernel that issues only
- * independent FP64 FMAs (8 chains per thread, `iters` rounds, 1024 threads on
- * every SM of `device`; -1 = the current device) and reports the fastest as
- * FP64 TFLOP/s (2 per FMA) in *tflops and its duration in *ms_per_launch (may
- * be NULL): the measured ceiling of the FP64 sweeps, whose FP64 instructions
+ * times `reps` launches (after one warm-up each) of a kernel that issues only
+ * independent FP64 FMAs on every SM of `device` (-1 = the current device), at
+ * three shapes (8 chains per thread with 1024 or 2048 threads per SM, 16 chains
+ * with 1024; `iters` rounds per chain), and reports the fastest launch as FP64
+ * TFLOP/s (2 per FMA) in *tflops and its duration in *ms_per_launch (may be
+ * NULL): the measured ceiling of the FP64 sweeps, whose FP64 instructions
  * bound them on GB300. Allocates and frees a small device buffer; blocks the
  * host. 1 <= iters <= 2^26, reps >= 1, else TBPM_ERR_ARG; no GPU:
  * TBPM_ERR_NO_DEVICE. */

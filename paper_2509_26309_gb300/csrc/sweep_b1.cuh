@@ -79,9 +79,12 @@ __device__ __forceinline__ void sell_group(const SweepParams &p, const int64_t (
 // FP64 is GB300's scarce pipe, and a butterfly per slice would cost as many FP64
 // instructions as the sparse product. For a batch of instances (MULTI) the
 // coefficients are those of each slice's instance and the partials are stored
-// per slice, partials[delta * nslices + slice], so that instances stay apart.
+// per slice, partials[delta * nslices + slice], so that instances stay apart:
+// a warp sums its consecutive visits to one instance's slices per lane and
+// writes the run's sum to the slot of the run's first slice (zeros to the
+// others), one butterfly per run instead of one per slice.
 // Each row's arithmetic is the same for every shape; only the grouping of the
-// single-instance dot partials follows the grid.
+// dot partials follows the grid.
 template <typename R, int OP, bool REALV, int BM, bool AIMAG, bool HASZ, bool FINAL, bool MULTI, int SPW, int LB>
 __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
 {
@@ -106,6 +109,21 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
     constexpr bool kF32 = sizeof(R) == 4;
 
     int cur_inst = 0;                   // instance whose coefficients a, beta hold
+    // batch final sweep: the warp's dot sums run over consecutive visits to
+    // slices of one instance; the run's sum goes to the slot of its first
+    // slice, and every other visited slice's slot gets zero
+    int64_t run_slot = -1;
+    int run_inst = -1;
+    auto flush_run = [&]() {
+        const double sr = warp_sum(dr), si = warp_sum(di);
+        if (lane == 0) p.partials[(int64_t)p.delta * p.nslices + run_slot] = make_double2(sr, si);
+        if (p.norm_partials) {
+            const double sn = warp_sum(nn);
+            if (lane == 0) p.norm_partials[(int64_t)p.delta * p.nslices + run_slot] = make_double2(sn, 0.0);
+        }
+        dr = di = nn = 0.0;
+        run_slot = -1;
+    };
     // t = a psi - z of row `row` (a real: a*psi; a imaginary: i*a*psi), one FMA per part
     auto first_terms = [&](const V &ps, const V &zz, R &tr, R &ti) {
         if (HASZ) {
@@ -116,7 +134,7 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
         }
     };
     // y = beta (A x) + t, the dot terms, and the store
-    auto finish = [&](int64_t s, int64_t row, R ar, R ai, R tr, R ti) {
+    auto finish = [&](int64_t s, int64_t row, int inst, R ar, R ai, R tr, R ti) {
         V out;
         if (BM == B_ONE) { out.x = ar; out.y = ai; }
         else if (BM == B_REAL) { out.x = fma(beta, ar, tr); out.y = fma(beta, ai, ti); }
@@ -132,18 +150,18 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
             const double qr = (double)q.x, qi = (double)q.y;
             const double orr = (double)out.x, oi = (double)out.y;
             if (MULTI) {
-                const double sr = warp_sum(fma(qr, orr, qi * oi));
-                const double si = warp_sum(fma(qr, oi, -qi * orr));
-                if (lane == 0) p.partials[(int64_t)p.delta * p.nslices + s] = make_double2(sr, si);
-                if (p.norm_partials) {
-                    const double sn = warp_sum(fma(orr, orr, oi * oi));
-                    if (lane == 0) p.norm_partials[(int64_t)p.delta * p.nslices + s] = make_double2(sn, 0.0);
+                if (run_slot >= 0 && inst != run_inst) flush_run();
+                if (run_slot < 0) {
+                    run_slot = s;
+                    run_inst = inst;
+                } else if (lane == 0) {
+                    p.partials[(int64_t)p.delta * p.nslices + s] = make_double2(0.0, 0.0);
+                    if (p.norm_partials) p.norm_partials[(int64_t)p.delta * p.nslices + s] = make_double2(0.0, 0.0);
                 }
-            } else {
-                dr = fma(qr, orr, fma(qi, oi, dr));
-                di = fma(qr, oi, fma(-qi, orr, di));
-                if (p.norm_partials) nn = fma(orr, orr, fma(oi, oi, nn));
             }
+            dr = fma(qr, orr, fma(qi, oi, dr));
+            di = fma(qr, oi, fma(-qi, orr, di));
+            if (p.norm_partials) nn = fma(orr, orr, fma(oi, oi, nn));
         }
     };
     // one slice on its own (every operator; the tail of a group)
@@ -168,7 +186,7 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
         else { ar = d * xi.x; ai = d * xi.y; }
         if (OP == OP_SELL) sell_apply<R, REALV>(p, s, lane, x, ar, ai);
         else if (row < p.n) stencil_apply<R, OP>(p, row, x, ar, ai);
-        finish(s, row, ar, ai, tr, ti);
+        finish(s, row, cur_inst, ar, ai, tr, ti);
     };
 
     if constexpr (SPW == 1) {
@@ -211,6 +229,7 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
             d[q] = diag ? ldm<R>(diag + row) : (R)0;
         }
         R ar[SPW], ai[SPW], tr[SPW], ti[SPW], aq[SPW], bq[SPW];
+        int gq[SPW];
 #pragma unroll
         for (int q = 0; q < SPW; ++q) {
             if (MULTI) {
@@ -222,6 +241,7 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
             }
             aq[q] = a;
             bq[q] = beta;
+            gq[q] = cur_inst;
             first_terms(ps[q], zz[q], tr[q], ti[q]);
             if (BM == B_ONE) { ar[q] = fma(d[q], xi[q].x, tr[q]); ai[q] = fma(d[q], xi[q].y, ti[q]); }
             else { ar[q] = d[q] * xi[q].x; ai[q] = d[q] * xi[q].y; }
@@ -232,11 +252,13 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
         for (int q = 0; q < SPW; ++q) {
             a = aq[q];
             beta = bq[q];
-            finish(s0 + q, ((s0 + q) << 5) + lane, ar[q], ai[q], tr[q], ti[q]);
+            finish(s0 + q, ((s0 + q) << 5) + lane, gq[q], ar[q], ai[q], tr[q], ti[q]);
         }
     }
     }
-    if (FINAL && !MULTI && kF32) {
+    if (FINAL && MULTI) {
+        if (run_slot >= 0) flush_run();
+    } else if (FINAL && kF32) {
         // FP32 data: the block's sums in FP32 pairs, one conversion per value; the
         // block's first warp slot holds them, its other warp slots zero
         F2Sum sums[3] = {fr, fi, fn};
@@ -248,7 +270,7 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
             if (p.norm_partials)
                 p.norm_partials[(int64_t)p.delta * nwarps + warp] = make_double2(lead ? v[2] : 0.0, 0.0);
         }
-    } else if (FINAL && !MULTI) {
+    } else if (FINAL) {
         dr = warp_sum(dr);
         di = warp_sum(di);
         if (lane == 0) p.partials[(int64_t)p.delta * nwarps + warp] = make_double2(dr, di);

@@ -930,17 +930,20 @@ static int finish_create(tbpm_ctx *ctx, const tbpm_opts &o)
     return TBPM_OK;
 }
 
-// Autotuner (TBPM_F_AUTOTUNE): times middle sweeps of this context's operator
-// over launch shapes: block widths of 128, 256, 512 and 1024 threads, 1, 2 or
-// 4 consecutive 32-row slices per warp iteration (the shapes sweep_shape_built
-// accepts for this operator), and for each the grids of occupancy/2,
-// occupancy and twice the occupancy blocks per SM (all of 1 .. occupancy when
-// that is at most 4). Every candidate is timed over 3 sweeps after one
-// warm-up; the four fastest and the default shape (512 threads, one slice,
-// the occupancy grid) are timed again over 10 sweeps, and the fastest of
-// those is kept for the life of the context. The single-instance dot
-// partials are per warp of the chosen grid, which is then fixed, so results
-// stay reproducible from call to call. Runs once, before any graph is captured.
+// Autotuner (TBPM_F_AUTOTUNE): times whole time steps of this context's
+// operator (the K = 18 sweep sequence of x = pi: first, second, 14 middle and
+// the final sweep with its dot partials) over launch shapes: block widths of
+// 128, 256, 512 and 1024 threads, 1, 2 or 4 consecutive 32-row slices per warp
+// iteration (the shapes sweep_shape_built accepts for this operator), and for
+// each the grids of occupancy/2, occupancy and twice the occupancy blocks per
+// SM (all of 1 .. occupancy when that is at most 4). Every candidate is timed
+// over 2 steps after one warm-up step; the four fastest and the default shape
+// (512 threads, one slice, the occupancy grid) are timed again over 6 steps,
+// and the fastest of those is kept for the life of the context. The
+// single-instance dot partials are per warp of the chosen grid, which is then
+// fixed, so results stay reproducible from call to call. Runs once, before any
+// graph is captured; the sweeps run on zero coefficients and overwrite the
+// work vectors, which every call initialises.
 static int autotune(tbpm_ctx *ctx)
 {
     if (ctx->tuned) return TBPM_OK;
@@ -949,15 +952,6 @@ static int autotune(tbpm_ctx *ctx)
     CU(cudaMemsetAsync(ctx->d_coef, 0, sizeof(double2) * kMaxTerms * std::max(1, ctx->ninst), ctx->stream));
     ctx->K_cached = -1;
     ctx->dt_cached.clear();
-    SweepParams p;
-    fill_operator(ctx, p);
-    p.coef = ctx->d_coef;
-    p.psi = ctx->d_psi;
-    p.x = ctx->d_b0;
-    p.y = ctx->d_b1;
-    p.z = ctx->d_b1;
-    p.ia = 1; p.ib = -1; p.ic = -1; p.bscale = 1.0;
-    p.slice_inst = ctx->d_slice_inst;
     const bool multi = ctx->d_slice_inst != nullptr;
     struct Cand {
         int block, spw, grid;
@@ -966,6 +960,7 @@ static int autotune(tbpm_ctx *ctx)
     std::vector<Cand> cands;
     const SweepVariant base = variant(ctx, 1);
     const int def_grid = ctx->nblk;
+    int64_t max_warps = 0;
     for (int block : {128, 256, 512, 1024})
         for (int spw : {1, 2, 4}) {
             SweepVariant v = base;
@@ -980,31 +975,73 @@ static int autotune(tbpm_ctx *ctx)
             else
                 ks = {occ / 2, occ};
             ks.push_back(2 * occ);
-            for (int k : ks) cands.push_back({block, spw, k * ctx->num_sms, 0.0});
+            for (int k : ks) {
+                cands.push_back({block, spw, k * ctx->num_sms, 0.0});
+                max_warps = std::max<int64_t>(max_warps, (int64_t)k * ctx->num_sms * block / 32);
+            }
         }
     bool have_def = false;
     for (const Cand &c : cands) have_def |= c.block == kBlockB1 && c.spw == 1 && c.grid == def_grid;
     if (!have_def) cands.push_back({kBlockB1, 1, def_grid, 0.0});
-    cudaEvent_t e0, e1;
-    CU(cudaEventCreate(&e0));
-    CU(cudaEventCreate(&e1));
+    // the final sweep's per-warp partials (slot 0) of the widest candidate
+    double2 *part = ctx->d_partials;
+    double2 *own_part = nullptr;
+    if (!multi && (size_t)max_warps > ctx->partials_cap) {
+        CU(cudaMalloc(&own_part, sizeof(double2) * (size_t)max_warps));
+        part = own_part;
+    }
+    SweepParams p;
+    fill_operator(ctx, p);
+    p.coef = ctx->d_coef;
+    p.psi = ctx->d_psi;
+    p.psi0 = ctx->d_psi0;
+    p.partials = part;
+    p.delta = 0;
+    p.slice_inst = ctx->d_slice_inst;
+    void *Bv[2] = {ctx->d_b0, ctx->d_b1};
+    constexpr int Kt = 18;
+    auto step = [&](const SweepVariant &v, int grid) -> cudaError_t {
+        cudaError_t e;
+        p.x = ctx->d_psi; p.z = nullptr; p.y = Bv[0];
+        p.ia = Kt - 2; p.ib = -1; p.ic = Kt - 1; p.bscale = 1.0;
+        if ((e = launch_sweep(v, SW_FIRST, false, false, p, grid, ctx->stream)) != cudaSuccess) return e;
+        p.x = Bv[0]; p.y = Bv[1];
+        p.ia = Kt - 3; p.ib = Kt - 1; p.ic = -1;
+        if ((e = launch_sweep(v, SW_SECOND, true, false, p, grid, ctx->stream)) != cudaSuccess) return e;
+        for (int k = Kt - 4; k >= 1; --k) {
+            p.x = Bv[(Kt - 3 - k) & 1];
+            p.y = Bv[(Kt - 2 - k) & 1];
+            p.z = p.y;
+            p.ia = k; p.ib = -1; p.ic = -1;
+            if ((e = launch_sweep(v, SW_MID, (k & 1) != 0, true, p, grid, ctx->stream)) != cudaSuccess) return e;
+        }
+        p.x = Bv[(Kt - 3) & 1];
+        p.z = Bv[(Kt - 4) & 1];
+        p.y = ctx->d_psi;
+        p.ia = 0; p.ib = -1; p.ic = -1; p.bscale = 0.5;
+        return launch_sweep(v, SW_FINAL, false, true, p, grid, ctx->stream);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto time_us = [&](const Cand &c, int reps, double *us) -> int {
         SweepVariant v = base;
         v.block = c.block;
         v.spw = c.spw;
-        CU(launch_sweep(v, SW_MID, true, true, p, c.grid, ctx->stream));        // warm
+        CU(step(v, c.grid));                                                // warm
         CU(cudaEventRecord(e0, ctx->stream));
-        for (int r = 0; r < reps; ++r) CU(launch_sweep(v, SW_MID, true, true, p, c.grid, ctx->stream));
+        for (int r = 0; r < reps; ++r) CU(step(v, c.grid));
         CU(cudaEventRecord(e1, ctx->stream));
         CU(cudaEventSynchronize(e1));
         float ms = 0.f;
         CU(cudaEventElapsedTime(&ms, e0, e1));
-        *us = 1e3 * ms / reps;
+        *us = 1e3 * ms / reps / (Kt - 1);                                  // per sweep
         return TBPM_OK;
     };
-    for (Cand &c : cands)
-        if ((rc = time_us(c, 3, &c.us))) break;
     std::vector<Cand> fin;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = TBPM_ERR_CUDA;
+        ctx->last_error = "autotune: cudaEventCreate failed";
+    }
+    for (size_t i = 0; i < cands.size() && !rc; ++i) rc = time_us(cands[i], 2, &cands[i].us);
     if (!rc) {
         std::vector<Cand> sorted = cands;
         std::sort(sorted.begin(), sorted.end(), [](const Cand &a, const Cand &b) { return a.us < b.us; });
@@ -1012,11 +1049,14 @@ static int autotune(tbpm_ctx *ctx)
         bool def_in = false;
         for (const Cand &c : fin) def_in |= c.block == kBlockB1 && c.spw == 1 && c.grid == def_grid;
         if (!def_in) fin.push_back({kBlockB1, 1, def_grid, 0.0});
-        for (Cand &c : fin)
-            if ((rc = time_us(c, 10, &c.us))) break;
+        for (size_t i = 0; i < fin.size() && !rc; ++i) rc = time_us(fin[i], 6, &fin[i].us);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (own_part) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(own_part);
+    }
     if (rc) return rc;
     Cand best = fin[0];
     double def_us = 0.0;

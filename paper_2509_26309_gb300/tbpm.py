@@ -320,7 +320,7 @@ def tbpm_dos_corr_noalloc(n: int, row_ptr, col, val, rescale: float, psi0, dt: f
                "tbpm_dos_corr_noalloc")
 
 
-def tbpm_fp64_peak(device: int = -1, iters: int = 50000, reps: int = 3) -> tuple[float, float]:
+def tbpm_fp64_peak(device: int = -1, iters: int = 20000, reps: int = 3) -> tuple[float, float]:
     """(FP64 TFLOP/s, ms per launch) of an FMA-only kernel on the device: the
     measured ceiling of the FP64 sweeps."""
     tf, ms = C.c_double(), C.c_double()
