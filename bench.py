@@ -197,6 +197,11 @@ def run_ours(args, rank, world, local_rank):
     def count():
         launches[0] += tb.tbpm_get_info(ctx)["kernel_launches"]
 
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        from paper_2509_26309_gb300.replicas import average_over_ranks
+
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
@@ -206,9 +211,15 @@ def run_ours(args, rank, world, local_rank):
             ev[1].record(stream)
         tb.kpm_moments(ctx, dpsi, M_MOMENTS, out=dmu)
         count()
-        tb.tbpm_dos_from_corr(ctx, dcorr[0], DT)
+        c, m = dcorr[0], dmu[0]
+        if dist:
+            # the one exchange of the state-sharded path: the average of the
+            # ranks' correlations and moments over all states (one per rank)
+            c = average_over_ranks(dcorr[0].clone(), world)
+            m = average_over_ranks(dmu[0].clone(), world)
+        tb.tbpm_dos_from_corr(ctx, c, DT)
         count()
-        tb.kpm_dos_jackson(ctx, dmu[0], N_E)
+        tb.kpm_dos_jackson(ctx, m, N_E)
         count()
 
     for _ in range(args.warmup):
@@ -217,9 +228,7 @@ def run_ours(args, rank, world, local_rank):
     K = tb.tbpm_get_info(ctx)["num_terms"]
     torch.cuda.synchronize()
 
-    dist = world > 1
     if dist:
-        import torch.distributed as td
         td.barrier()
     launches[0] = 0
     dos_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -236,6 +245,7 @@ def run_ours(args, rank, world, local_rank):
         td.barrier()
     gpu_launches = launches[0]
     ms = start.elapsed_time(stop)
+    peak64 = measure_fp64_peak(tb, local_rank)
     dos_ms = sum(a.elapsed_time(b) for a, b in dos_ev) / args.steps
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if dist:
@@ -246,8 +256,9 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel family (the Clenshaw sweeps), measured
     # over the timed region: DOS part time / sweeps. ncu shows these FP64
-    # sweeps bound by the FP64 pipe (GB300 issues 2 FP64 FMA lanes per clock
-    # per SM), so the bound is the FP64 ALU; the HBM fraction is reported too.
+    # sweeps bound by the FP64 pipe, so the bound is the FP64 ALU, against the
+    # FMA-only kernel's rate measured in this run; the HBM fractions are
+    # reported too, on the kernel's own streams and on the survey's basis.
     info = tb.tbpm_get_info(ctx)
     sweeps = N_STEPS * (K - 1)
     sweep_s = dos_ms / 1e3 / sweeps
@@ -263,18 +274,30 @@ def run_ours(args, rank, world, local_rank):
     ops_step_row = 12 + 10 + (K - 4) * 10 + 16
     flops_per_sweep = 2.0 * n * ops_step_row / (K - 1)
     hbm, hbm_source = measured_hbm()
-    fp64_peak = FP64_PEAK_TFLOPS
     tflops = flops_per_sweep / sweep_s / 1e12
     gbs = bytes_per_sweep / sweep_s / 1e9
-    roofline = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(fp64_peak, 4),
-                "unit": "TFLOP/s", "frac": round(tflops / fp64_peak, 4), "traffic": profile_traffic(),
+    # the survey's per-orbital-term basis: complex128 hoppings (4 stored
+    # entries x (16 B value + 4 B column) + 4 B row pointer) and the forward
+    # recurrence's 5 vector streams of 16 B
+    survey_gbs = SURVEY_B_PER_TERM * n / sweep_s / 1e9
+    roofline = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(peak64["tflops"], 4),
+                "unit": "TFLOP/s", "frac": round(tflops / peak64["tflops"], 4), "traffic": profile_traffic(),
                 "kernel": "Clenshaw sweeps (sweep_b1, FP64, SELL, real hoppings)",
-                "peak_source": "FP64 pipe from unit counts and clock (no measured FP64 peak in "
-                               "MEASURED_PEAKS.json): 2 FMA lanes/clk/SM x 152 SMs x 2.07 GHz",
+                "peak_source": peak64["source"], "fp64_peak": peak64,
                 "flops_per_sweep": round(flops_per_sweep), "sweep_us": round(sweep_s * 1e6, 2),
                 "hbm": {"achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                         "frac": round(gbs / hbm, 4), "bytes_per_sweep": round(bytes_per_sweep),
-                        "peak_source": hbm_source}}
+                        "basis": "the kernel's own streams: real hoppings (int32 column + FP64 value), "
+                                 "FP64 diagonal, slice offsets; 4 vector streams per middle sweep "
+                                 "(Clenshaw), 2/3/5 in the first/second/final sweep",
+                        "peak_source": hbm_source},
+                "hbm_survey_basis": {"achieved": round(survey_gbs, 1), "peak": hbm, "unit": "GB/s",
+                                     "frac": round(survey_gbs / hbm, 4), "bytes_per_orbital_term": SURVEY_B_PER_TERM,
+                                     "why_above_1": "the basis counts complex128 hoppings (16 B) and the forward "
+                                                    "recurrence's 5 vector streams; the kernel stores real hoppings "
+                                                    "(8 B, every imaginary part is zero) and sums the series by "
+                                                    "Clenshaw's recurrence (4 streams), so it moves ~0.65 of these "
+                                                    "bytes for the same orbital-terms"}}
 
     # e2e: the same step through the public API with pinned host buffers,
     # H2D of psi0 and D2H of every result inside the timed region
@@ -288,7 +311,7 @@ def run_ours(args, rank, world, local_rank):
         tb.tbpm_dos_from_corr(ctx, hcorr[0], DT)
         tb.kpm_dos_jackson(ctx, hmu[0], N_E)
 
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = args.steps
     e2e_step()
     torch.cuda.synchronize()
     if dist:
@@ -331,10 +354,11 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def timed_calls(fn, reps, stream):
-    """Mean device time (ms) of fn() over reps calls, after one warm-up call."""
+def timed_calls(fn, reps, stream, warm=None):
+    """Mean device time (ms) of fn() over reps calls, after one warm-up call
+    (of warm() if given: a shorter call that builds the same graphs)."""
     import torch
-    fn()
+    (warm or fn)()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -353,6 +377,18 @@ def dos_l1(ctx, corr, ref, dt):
     _, d = tb.tbpm_dos_from_corr(ctx, np.asarray(corr), dt)
     _, r = tb.tbpm_dos_from_corr(ctx, np.asarray(ref), dt)
     return float(np.sum(np.abs(d - r)) / np.sum(np.abs(r)))
+
+
+def oracle_golden(name: str, state: int = 0):
+    """The oracle's stored C(t) of a full-size workload (tests/golden/, written
+    by tests/golden/make_oracle_golden.py from the oracle alone), or None."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_{name}_s{state}.txt")
+    try:
+        a = np.loadtxt(path, comments="#")
+    except OSError:
+        return None
+    return a[:, 0] + 1j * a[:, 1]
 
 
 def measured_hbm():
@@ -374,15 +410,43 @@ def hbm_roof(units_per_s, bytes_per_unit, basis):
             "bytes_per_unit": bytes_per_unit, "basis": basis}
 
 
-FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12   # 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2
+# algorithmic bytes per orbital-term of the survey's measurement basis (FP64
+# CSR): 4 stored entries x (16 B complex value + 4 B column) + 4 B row pointer,
+# plus 5 vector streams of 16 B (the forward recurrence)
+SURVEY_B_PER_TERM = 4 * (16 + 4) + 4 + 5 * 16
+
+# the FP64 peak of this run (measure_fp64_peak), shared by the roofline fields
+PEAK64 = {}
+
+
+def measure_fp64_peak(tb, device: int) -> dict:
+    """FP64 TFLOP/s of the library's FMA-only kernel on this GPU (the fastest
+    of 3 launches at each of its 3 shapes, ~50-100 ms each), the SM clocks
+    sampled while it ran, and the figure the unit counts give at the sampled
+    clock (2 FP64 FMA lanes per clock per SM x the device's SM count) for
+    comparison."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    with ClockSampler(device) as clk:
+        tf, ms = tb.tbpm_fp64_peak(device, 20000, 3)
+    c = clk.summary()
+    mhz = c["sm_mhz"] or c["sm_max_mhz"]
+    out = {"tflops": tf, "ms_per_launch": ms, "sms": sms, "clocks": c,
+           "source": "measured in this run: tbpm_fp64_peak, an FMA-only kernel (8 or 16 independent chains "
+                     "per thread, 1024 or 2048 threads per SM), the fastest launch"}
+    if mhz:
+        out["unit_count_tflops_at_clock"] = 2 * sms * mhz * 1e6 * 2 / 1e12
+    PEAK64.update(out)
+    return out
 
 
 def alu_roof(units_per_s, fp64_ops_per_unit):
     """FP64-pipe roofline of a variant: FP64 operations (FMA, MUL or ADD, one
-    issue slot each, 2 flops) per unit x units/s against the pipe's peak."""
+    issue slot each, 2 flops) per unit x units/s against the measured peak."""
     tf = units_per_s * fp64_ops_per_unit * 2 / 1e12
-    return {"bound": "alu", "achieved": round(tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-            "frac": round(tf / FP64_PEAK_TFLOPS, 4), "fp64_ops_per_unit": fp64_ops_per_unit}
+    pk = PEAK64["tflops"]
+    return {"bound": "alu", "achieved": round(tf, 4), "peak": round(pk, 4), "unit": "TFLOP/s",
+            "frac": round(tf / pk, 4), "fp64_ops_per_unit": fp64_ops_per_unit, "peak_source": PEAK64["source"]}
 
 
 # algorithmic bytes per orbital-term of a middle sweep (FP32, real hoppings):
@@ -402,24 +466,24 @@ def run_variants(args, dev, stream):
     device-resident inputs (not part of the headline value):
       - FP64 64x64 pristine graphene (N = 8192), 1024 steps: one cluster launch
         against one graph-launched kernel per sweep;
-      - FP64 uneven batch of 40 lattices in one context (autotuned grid),
-        dt_g = pi/rescale_g (K = 18 for every instance), 256 steps, against the
-        same instances one context at a time;
+      - FP64 uneven batch of 40 lattices in one context, dt_g = pi/rescale_g
+        (K = 18 for every instance), 1024 steps: autotuned launch shape against
+        the default shape, and against the same instances one context at a time;
       - FP32 single state, stored matrix: graphene 2048x2048, W = 1
-        (N = 8,388,608), 1024 steps, with and without renormalisation, DOS L1
-        error against the FP64 run of the same state;
+        (N = 8,388,608), 1024 steps, with and without renormalisation, C(t) and
+        DOS L1 errors against the oracle's stored FP64 C(t) of the same state;
       - FP32 block of 16 states vs FP64 single state on graphene 4096x4096,
         W = 1 (N = 33,554,432, the paper's benchmark lattice), stencil and
-        stored-matrix paths, 32 steps each (the speedup is a throughput ratio,
-        so the step count only sets the sample length); DOS L1 of state 0;
+        stored-matrix paths, 128 steps each (the speedup is a throughput ratio,
+        so the step count only sets the sample length); C(t) and DOS L1 errors
+        of state 0 against the oracle's stored C(t);
       - FP32 single state on that stencil and on an AB-bilayer stencil of as many
         orbitals, temporally blocked vs one launch per sweep, and 512 KPM moments
         blocked vs one launch per pass;
       - the AC current correlation on graphene 1024x1024 (W = 1) at 300 K;
       - on that lattice and operator, the time-dependent wave function, the
         quasi-eigenstates and the Haydock recursion (FP64).
-    The FP64 runs the errors are taken against are the path the parity tests
-    hold to 1e-10 of the oracle."""
+    The oracle's C(t) come from tests/golden/ (written by the oracle alone)."""
     import numpy as np
     import torch
     import tbpm_inputs as ti
@@ -439,20 +503,27 @@ def run_variants(args, dev, stream):
                      "states": 1, "n_steps": 1024}
         tb.tbpm_destroy(c1)
     # uneven batch of 40 lattices (monolayer / AB bilayer, N log-uniform
-    # 1e4..4e6, per-instance W and rescale), FP64, one block-diagonal operator
-    # with an autotuned grid, against the same 40 instances one context at a time
+    # 1e4..4e6, per-instance W and rescale), FP64, 1024 steps: one
+    # block-diagonal operator with the autotuned launch shape, the same at the
+    # default shape (512 threads, one slice per warp, the occupancy grid), and
+    # the 40 instances one context at a time
     insts = ti.batch_instances()
     n5 = sum(i.csr.n for i in insts)
-    steps5 = 256
+    steps5 = 1024
     dts = [math.pi / i.rescale for i in insts]
     psi5 = torch.from_numpy(np.concatenate([ti.random_phase_state(i.csr.n, k)
                                             for k, i in enumerate(insts)])).to(dev)
-    cb = tb.tbpm_create_batch([(i.csr, i.rescale) for i in insts],
-                              tb.make_opts(flags=tb.TBPM_F_AUTOTUNE, stream=so))
     ob = torch.empty((len(insts), steps5 + 1), dtype=torch.complex128, device=dev)
-    msb = timed_calls(lambda: tb.tbpm_batch_dos_corr(cb, psi5, dts, steps5, out=ob), 1, stream)
-    ib = tb.tbpm_get_info(cb)
-    tb.tbpm_destroy(cb)
+    ow = torch.empty((len(insts), 17), dtype=torch.complex128, device=dev)
+    units5 = steps5 * 17 * n5                          # K = 18 at dt * rescale = pi
+    batch = {}
+    for name, flags in (("tuned", tb.TBPM_F_AUTOTUNE), ("default_shape", 0)):
+        cb = tb.tbpm_create_batch([(i.csr, i.rescale) for i in insts], tb.make_opts(flags=flags, stream=so))
+        msb = timed_calls(lambda: tb.tbpm_batch_dos_corr(cb, psi5, dts, steps5, out=ob), 1, stream,
+                          warm=lambda: tb.tbpm_batch_dos_corr(cb, psi5, dts, 16, out=ow))
+        ib = tb.tbpm_get_info(cb)
+        batch[name] = {"ms": msb, "info": ib, "corr": ob.clone()}
+        tb.tbpm_destroy(cb)
     seq_ms = 0.0
     off = 0
     dev_max = 0.0
@@ -460,18 +531,26 @@ def run_variants(args, dev, stream):
         ci = tb.tbpm_create(i.csr.n, i.csr.row_ptr, i.csr.col, i.csr.val, i.rescale, tb.make_opts(stream=so))
         pi = psi5[off:off + i.csr.n].reshape(1, i.csr.n)
         oi = torch.empty((1, steps5 + 1), dtype=torch.complex128, device=dev)
-        seq_ms += timed_calls(lambda: tb.tbpm_dos_corr(ci, pi, dts[k], steps5, out=oi), 1, stream)
-        dev_max = max(dev_max, float((oi[0] - ob[k]).abs().max()))
+        seq_ms += timed_calls(lambda: tb.tbpm_dos_corr(ci, pi, dts[k], steps5, out=oi), 1, stream,
+                              warm=lambda: tb.tbpm_dos_corr(ci, pi, dts[k], 16, out=ow[k:k + 1]))
+        dev_max = max(dev_max, float((oi[0] - batch["tuned"]["corr"][k]).abs().max()))
         tb.tbpm_destroy(ci)
         off += i.csr.n
-    units5 = steps5 * 17 * n5                          # K = 18 at dt * rescale = pi
-    res["fp64_batch40_uneven"] = {"value": units5 / (msb / 1e3), "unit": UNIT, "ms_per_call": msb,
-                                  "instances": len(insts), "orbitals": n5, "n_steps": steps5,
-                                  "num_terms": ib["num_terms"], "grid_blocks": ib["grid_blocks"],
-                                  "tuned": bool(ib["tuned"]), "max_abs_dC_vs_sequential": dev_max}
+    ib = batch["tuned"]["info"]
+    res["fp64_batch40_uneven"] = {
+        "value": units5 / (batch["tuned"]["ms"] / 1e3), "unit": UNIT, "ms_per_call": batch["tuned"]["ms"],
+        "instances": len(insts), "orbitals": n5, "n_steps": steps5, "num_terms": ib["num_terms"],
+        "tuned_shape": {"grid_blocks": ib["grid_blocks"], "block_threads": ib["block_threads"],
+                        "slices_per_warp": ib["slices_per_warp"], "candidates": ib["tune_candidates"],
+                        "middle_sweep_us": ib["tune_best_us"], "default_middle_sweep_us": ib["tune_default_us"]},
+        "gain_vs_default_shape": batch["default_shape"]["ms"] / batch["tuned"]["ms"],
+        "max_abs_dC_vs_sequential": dev_max,
+        "max_abs_dC_vs_default_shape": float((batch["tuned"]["corr"] - batch["default_shape"]["corr"]).abs().max())}
+    res["fp64_batch40_default_shape"] = {"value": units5 / (batch["default_shape"]["ms"] / 1e3), "unit": UNIT,
+                                         "ms_per_call": batch["default_shape"]["ms"], "n_steps": steps5}
     res["fp64_batch40_sequential"] = {"value": units5 / (seq_ms / 1e3), "unit": UNIT, "ms_per_call": seq_ms,
                                       "instances": len(insts), "n_steps": steps5}
-    del insts, psi5
+    del insts, psi5, batch
     # graphene 2048x2048, W = 1: FP32 single state, SELL, against FP64 on the same state
     n3 = 2 * 2048 * 2048
     h3 = ti.graphene_csr(2048, 2048, onsite=ti.anderson_onsite(n3, W_DISORDER, 1))
@@ -480,6 +559,11 @@ def run_variants(args, dev, stream):
     ref3 = torch.empty((1, 1025), dtype=torch.complex128, device=dev)
     tb.tbpm_dos_corr(c64, psi, DT, 1024, out=ref3)
     ref3h = ref3[0].cpu().numpy()
+    orc3 = oracle_golden("graphene2048_dos1024")
+    res["fp64_sell_2048x2048_vs_oracle"] = {
+        "max_abs_dC": None if orc3 is None else float(np.max(np.abs(ref3h - orc3))),
+        "dos_l1": None if orc3 is None else dos_l1(c64, ref3h, orc3, DT),
+        "reference": "oracle C(t), 1024 steps (tests/golden/oracle_graphene2048_dos1024_s0.txt)"}
     out = torch.empty((1, 1025), dtype=torch.complex128, device=dev)
     for name, flags in (("fp32_sell_2048x2048", 0), ("fp32_sell_renorm_2048x2048", tb.TBPM_F_RENORM)):
         ctx = tb.tbpm_create(n3, h3.row_ptr, h3.col, h3.val, RESCALE,
@@ -490,8 +574,12 @@ def run_variants(args, dev, stream):
         res[name] = {"value": v3, "unit": UNIT, "ms_per_call": ms,
                      "states": 1, "n_steps": 1024,
                      "roofline": hbm_roof(v3, B_SELL32 + B_VEC32, "middle sweep, stored matrix + 4 vector streams"),
-                     "dos_l1_vs_fp64": dos_l1(c64, out[0].cpu().numpy(), ref3h, DT),
-                     "max_abs_dC_vs_fp64": float(np.max(np.abs(out[0].cpu().numpy() - ref3h)))}
+                     "dos_l1_vs_oracle": None if orc3 is None else dos_l1(c64, out[0].cpu().numpy(), orc3, DT),
+                     "max_abs_dC_vs_oracle": None if orc3 is None else float(np.max(np.abs(out[0].cpu().numpy() - orc3))),
+                     "dos_l1_reference": "the oracle's FP64 C(t) over the same 1024 steps "
+                                         "(tests/golden/oracle_graphene2048_dos1024_s0.txt); both DOS through the "
+                                         "library's Hann transform",
+                     "dos_l1_vs_gpu_fp64": dos_l1(c64, out[0].cpu().numpy(), ref3h, DT)}
         tb.tbpm_destroy(ctx)
     tb.tbpm_destroy(c64)
     del psi, h3
@@ -499,7 +587,8 @@ def run_variants(args, dev, stream):
     l4 = 4096
     n4 = 2 * l4 * l4
     eps = ti.anderson_onsite(n4, W_DISORDER, 1)
-    steps = 32
+    steps = 128
+    orc4 = oracle_golden("graphene4096_dos128")
     blk = torch.empty((16, n4), dtype=torch.complex128, device=dev)
     for j in range(16):
         blk[j].copy_(torch.from_numpy(ti.random_phase_state(n4, j)))
@@ -539,11 +628,18 @@ def run_variants(args, dev, stream):
             roof = hbm_roof(v32, 4 / 16 + B_VEC32, "middle sweep, on-site / 16 + 4 vector streams")
         else:
             roof = hbm_roof(v32, B_SELL32 / 16 + B_VEC32, "middle sweep, stored matrix / 16 + 4 vector streams")
-        res[f"fp32_x16_{path}_4096x4096"] = {"value": v32, "unit": "orbital-term-states/s", "ms_per_call": ms32,
-                                             "states": 16, "n_steps": steps,
-                                             "dos_l1_vs_fp64_state0": dos_l1(ctx64, s0, r, DT), "roofline": roof}
+        res[f"fp32_x16_{path}_4096x4096"] = {
+            "value": v32, "unit": "orbital-term-states/s", "ms_per_call": ms32, "states": 16, "n_steps": steps,
+            "dos_l1_vs_oracle_state0": None if orc4 is None else dos_l1(ctx64, s0, orc4, DT),
+            "max_abs_dC_vs_oracle_state0": None if orc4 is None else float(np.max(np.abs(s0 - orc4))),
+            "dos_l1_reference": "the oracle's FP64 C(t) of state 0 over the same 128 steps "
+                                "(tests/golden/oracle_graphene4096_dos128_s0.txt); both DOS through the library's "
+                                "Hann transform",
+            "roofline": roof}
         res[f"fp64_x1_{path}_4096x4096"] = {"value": v64, "unit": UNIT, "ms_per_call": ms64, "states": 1,
                                             "n_steps": steps,
+                                            "max_abs_dC_vs_oracle": None if orc4 is None else
+                                            float(np.max(np.abs(r - orc4))),
                                             "max_abs_dC_vs_stencil": float(np.max(np.abs(r - ref4)))}
         res[f"fp32_batched_speedup_vs_fp64_{path}"] = v32 / v64
         tb.tbpm_destroy(ctx64)
@@ -562,7 +658,8 @@ def run_variants(args, dev, stream):
                 else hbm_roof(v1s, 4 + B_VEC32, "middle sweep, on-site + 4 vector streams"))
         res[name] = {"value": v1s, "unit": UNIT, "ms_per_call": ms1s, "states": 1,
                      "n_steps": steps, "kernel_launches": tb.tbpm_get_info(c1s)["kernel_launches"],
-                     "max_abs_dC_vs_fp64": float(np.max(np.abs(o1[0].cpu().numpy() - ref4))), "roofline": roof}
+                     "max_abs_dC_vs_oracle": None if orc4 is None else
+                     float(np.max(np.abs(o1[0].cpu().numpy() - orc4))), "roofline": roof}
         tb.tbpm_destroy(c1s)
     res["fp32_tblock_speedup_vs_per_sweep"] = (res["fp32_x1_stencil_tblock_4096x4096"]["value"] /
                                                res["fp32_x1_stencil_per_sweep_4096x4096"]["value"])
@@ -642,6 +739,19 @@ def run_variants(args, dev, stream):
     return res
 
 
+# the sources of the sweep kernel whose DRAM traffic profiles/traffic.json records
+TRAFFIC_SOURCES = ("cheb_sweep.cu", "sweep_b1.cuh", "sweep_ops.cuh")
+
+
+def sources_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the sweep kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2509_26309_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profile_traffic():
     """DRAM bytes per sweep launch from the committed ncu summary, if it was
     taken on the current kernel source; otherwise None."""
@@ -650,11 +760,7 @@ def profile_traffic():
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    import hashlib
-    h = hashlib.sha256()
-    for f in ("cheb_sweep.cu", "sweep_ops.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2509_26309_gb300", "csrc", f), "rb").read())
-    if rec.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
+    if rec.get("kernel_sources_sha256_16") != sources_hash():
         return None
     return rec.get("sweep_traffic_bytes")
 

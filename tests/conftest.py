@@ -13,6 +13,19 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long CPU test")
 
 
+def golden_values(name: str, state: int = 0):
+    """Stored oracle results of a full-size workload (tests/golden/oracle_*.txt,
+    written by tests/golden/make_oracle_golden.py from the oracle alone)."""
+    import numpy as np
+    a = np.loadtxt(os.path.join(ROOT, "tests", "golden", f"oracle_{name}_s{state}.txt"), comments="#")
+    return a[:, 0] + 1j * a[:, 1]
+
+
+@pytest.fixture(scope="session")
+def golden():
+    return golden_values
+
+
 @pytest.fixture(scope="session")
 def orc():
     import oracle

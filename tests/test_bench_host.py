@@ -16,15 +16,21 @@ def test_workload_units():
     assert bench.workload_units(10, 3, n_steps=5, M=7) == 10 * (5 * 2 + 4)
 
 
-def test_roofline_fractions():
+def test_roofline_fractions(monkeypatch):
     peak = bench.measured_hbm()[0]
     r = bench.hbm_roof(1e9, 100.0, "basis")
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(100.0) and r["frac"] == pytest.approx(100.0 / peak, abs=1e-4)
+    monkeypatch.setattr(bench, "PEAK64", {"tflops": 1.25, "source": "test"})
     a = bench.alu_roof(1e10, 16)
-    # 16 FP64 operations of 2 flops each per unit
-    assert a["achieved"] == pytest.approx(0.32) and a["peak"] == pytest.approx(1.2586, abs=1e-4)
-    assert a["frac"] == pytest.approx(0.32 / bench.FP64_PEAK_TFLOPS, abs=1e-4)
+    # 16 FP64 operations of 2 flops each per unit, against the measured peak
+    assert a["achieved"] == pytest.approx(0.32) and a["peak"] == pytest.approx(1.25)
+    assert a["frac"] == pytest.approx(0.32 / 1.25, abs=1e-4)
+
+
+def test_survey_bytes_per_orbital_term():
+    # FP64 CSR: 4 entries x (16 B value + 4 B column) + 4 B row pointer + 5 vectors x 16 B
+    assert bench.SURVEY_B_PER_TERM == 164
 
 
 def test_traffic_record_follows_the_kernel_source(tmp_path, monkeypatch):
@@ -34,11 +40,11 @@ def test_traffic_record_follows_the_kernel_source(tmp_path, monkeypatch):
     (root / "profiles").mkdir(parents=True)
     csrc = root / "paper_2509_26309_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    for f in ("cheb_sweep.cu", "sweep_ops.cuh"):
+    for f in bench.TRAFFIC_SOURCES:
         shutil.copy(os.path.join(bench.ROOT, "paper_2509_26309_gb300", "csrc", f), csrc / f)
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), root / "profiles" / "traffic.json")
     monkeypatch.setattr(bench, "ROOT", str(root))
-    rec = json.load(open(root / "profiles" / "traffic.json"))
+    rec = {"kernel_sources_sha256_16": bench.sources_hash(), "sweep_traffic_bytes": 123456789}
+    json.dump(rec, open(root / "profiles" / "traffic.json", "w"))
     assert bench.profile_traffic() == rec["sweep_traffic_bytes"]
     with open(csrc / "sweep_ops.cuh", "a") as f:
         f.write("\n// edited\n")
