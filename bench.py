@@ -420,11 +420,12 @@ PEAK64 = {}
 
 
 def measure_fp64_peak(tb, device: int) -> dict:
-    """FP64 TFLOP/s of the library's FMA-only kernel on this GPU (the fastest
-    of 3 launches at each of its 3 shapes, ~50-100 ms each), the SM clocks
-    sampled while it ran, and the figure the unit counts give at the sampled
-    clock (2 FP64 FMA lanes per clock per SM x the device's SM count) for
-    comparison."""
+    """FP64 TFLOP/s of the library's FP64-only kernels on this GPU (FMA, MUL
+    and ADD forms, the fastest of 3 launches at each form and shape, ~50 ms
+    each; every FP64 instruction counted as 2 operations, as the sweeps'
+    roofline counts them), the SM clocks sampled while they ran, and the figure
+    the unit counts give at the sampled clock (2 FP64 lanes per clock per SM x
+    the device's SM count) for comparison."""
     import torch
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     with ClockSampler(device) as clk:
@@ -432,8 +433,8 @@ def measure_fp64_peak(tb, device: int) -> dict:
     c = clk.summary()
     mhz = c["sm_mhz"] or c["sm_max_mhz"]
     out = {"tflops": tf, "ms_per_launch": ms, "sms": sms, "clocks": c,
-           "source": "measured in this run: tbpm_fp64_peak, an FMA-only kernel (8 or 16 independent chains "
-                     "per thread, 1024 or 2048 threads per SM), the fastest launch"}
+           "source": "measured in this run: tbpm_fp64_peak, kernels of independent FP64 FMA, MUL or ADD chains "
+                     "(8 per thread, 1024 or 2048 threads per SM), the fastest launch"}
     if mhz:
         out["unit_count_tflops_at_clock"] = 2 * sms * mhz * 1e6 * 2 / 1e12
     PEAK64.update(out)
@@ -459,6 +460,10 @@ B_VEC32 = 4 * 8
 # b_{k+1}, b_{k+2}, on-site in (28 B), two b out; final block the same in plus
 # psi0 (8 B), psi out (8 B)
 B_TBLOCK_STEP = (12 + 16) + (28 + 16) + (28 + 8 + 8)
+# the same with the halo re-reads: every read covers the tile region, 1.31 x the
+# interior on the monolayer (a 96 x 32-cell region, interior 90 x 26)
+TB_REGION_MONO = (96 * 32) / (90 * 26)
+B_TBLOCK_STEP_HALO = (12 * TB_REGION_MONO + 16) + (28 * TB_REGION_MONO + 16) + (28 * TB_REGION_MONO + 8 + 8)
 
 
 def run_variants(args, dev, stream):
@@ -656,6 +661,9 @@ def run_variants(args, dev, stream):
         v1s = n4 * steps * (K - 1) / (ms1s / 1e3)
         roof = (hbm_roof(v1s, B_TBLOCK_STEP / (K - 1), "blocked time step, no halo re-reads, per sweep") if flags == 0
                 else hbm_roof(v1s, 4 + B_VEC32, "middle sweep, on-site + 4 vector streams"))
+        if flags == 0:
+            roof["halo_basis"] = hbm_roof(v1s, B_TBLOCK_STEP_HALO / (K - 1),
+                                          "blocked time step with the halo re-reads of the 1.31x tile region, per sweep")
         res[name] = {"value": v1s, "unit": UNIT, "ms_per_call": ms1s, "states": 1,
                      "n_steps": steps, "kernel_launches": tb.tbpm_get_info(c1s)["kernel_launches"],
                      "max_abs_dC_vs_oracle": None if orc4 is None else

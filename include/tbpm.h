@@ -408,15 +408,16 @@ typedef struct tbpm_info {
 int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info);
 
 /* tbpm_fp64_peak: a measurement helper with no counterpart in the paper. It
- * times `reps` launches (after one warm-up each) of a kernel that issues only
- * independent FP64 FMAs on every SM of `device` (-1 = the current device), at
- * three shapes (8 chains per thread with 1024 or 2048 threads per SM, 16 chains
- * with 1024; `iters` rounds per chain), and reports the fastest launch as FP64
- * TFLOP/s (2 per FMA) in *tflops and its duration in *ms_per_launch (may be
- * NULL): the measured ceiling of the FP64 sweeps, whose FP64 instructions
- * bound them on GB300. Allocates and frees a small device buffer; blocks the
- * host. 1 <= iters <= 2^26, reps >= 1, else TBPM_ERR_ARG; no GPU:
- * TBPM_ERR_NO_DEVICE. */
+ * times `reps` launches (after one warm-up each) of kernels that issue only
+ * independent FP64 instructions on every SM of `device` (-1 = the current
+ * device): FMA with parameter or register operands, MUL and ADD, 8 chains per
+ * thread of `iters` rounds, at 1024 and 2048 threads per SM, and reports the
+ * fastest launch as TFLOP/s, each FP64 instruction counted as 2 operations
+ * (one issue slot of the FP64 pipe), in *tflops, and its duration in
+ * *ms_per_launch (may be NULL): the measured ceiling of the FP64 sweeps, whose
+ * FP64 instructions bound them on GB300. Allocates and frees a small device
+ * buffer; blocks the host. 1 <= iters <= 2^26, reps >= 1, else TBPM_ERR_ARG;
+ * no GPU: TBPM_ERR_NO_DEVICE. */
 int tbpm_fp64_peak(int device, int iters, int reps, double *tflops, double *ms_per_launch);
 
 /* A static, human-readable name for a status code. */

@@ -10,15 +10,17 @@
 // floor the sparse product of Sec. 2.2.1 sits on, broken for the structured
 // lattices only.
 //
-// Layout on chip. A tile region is W1 rows (m1) by 32 cells (m2). Lane l of
-// every warp owns cell m2 = o2 + l; warp w owns kTbR consecutive rows. Each
-// thread keeps all PER orbitals of its cells in registers (A, B per layer):
-// psi, the on-site energies, b_{k+1} and b_{k+2}. The neighbours B(m - a2)
-// and A(m + a2) are one lane away (warp shuffles), B(m - a1) and A(m + a1) one
-// row away (the thread's own registers, or, across a warp boundary, a row that
-// each warp publishes in shared memory once per sweep), the dimer partner in
-// the same cell. Lanes at the region's left and right edges and rows at its
-// top and bottom read stand-in values: those cells are halo.
+// Layout on chip. A tile region is W1 rows (m1) by W2 = 32 C2 cells (m2).
+// Lane l of every warp owns the C2 consecutive cells m2 = o2 + C2 l + c; warp w
+// owns R consecutive rows. Each thread keeps all PER orbitals of its cells in
+// registers (A, B per layer): psi, the on-site energies, b_{k+1} and b_{k+2}.
+// The neighbours B(m - a2) and A(m + a2) are in the thread's own registers
+// between its cells, and one lane away (warp shuffles) at the ends of its run
+// of C2 cells; B(m - a1) and A(m + a1) are one row away (the thread's own
+// registers, or, across a warp boundary, a row that each warp publishes in
+// shared memory once per sweep), the dimer partner in the same cell. Lanes at
+// the region's left and right edges and rows at its top and bottom read
+// stand-in values: those cells are halo.
 //
 // A block of S sweeps loads psi(t_n), b_{k+1}, b_{k+2} and the on-site
 // energies for its region (cp.async into a per-thread staging area while the
@@ -38,30 +40,45 @@ namespace tbpm {
 namespace {
 
 constexpr int kTbH = (kTbS + 1) / 2;            // halo cells per side
-constexpr int kTbR = 3;                         // rows per warp
-constexpr int kTbW2 = 32;                       // region cells along m2 (one per lane)
-constexpr int kTbT2 = kTbW2 - 2 * kTbH;         // interior cells along m2
 
-// PER orbitals per cell: the monolayer runs 1024 threads (64 registers each),
-// the bilayer, with twice the state per cell, 512 (128 registers each); the
-// KPM kernel (KPM = true), which also keeps per-pass dot sums in registers,
-// runs 512 threads for both.
+// Tile configuration of each kernel. The monolayer time steps run 1024
+// threads of 3 rows x 1 cell (a 32 x 96-cell region, interior 26 x 90, 64
+// registers per thread); the bilayer, with twice the state per cell, and the
+// KPM passes, which also keep per-pass dot sums in registers, run 512 threads
+// of 3 rows x 1 cell (32 x 48 cells). Two cells per lane (in-thread
+// neighbours along m2, half the shuffles, a 64-cell-wide region) measured
+// slower on GB300 for the monolayer time steps: 4.2e11 orbital-terms/s at 512
+// threads x 3 rows and 4.1e11 at 768 x 2 rows, against 5.5e11 here (4096^2).
 template <int PER, bool KPM = false>
 struct TbCfg {
-    static constexpr int threads = (PER == 2 && !KPM) ? 1024 : 512;
+    static constexpr bool kMonoSteps = PER == 2 && !KPM;
+    static constexpr int C2 = 1;                // cells per lane along m2
+    static constexpr int R = 3;                 // rows per warp
+    static constexpr int threads = kMonoSteps ? 1024 : 512;
     static constexpr int warps = threads / 32;
-    static constexpr int W1 = warps * kTbR;     // region rows (m1)
+    static constexpr int W1 = warps * R;        // region rows (m1)
     static constexpr int T1 = W1 - 2 * kTbH;    // interior rows
+    static constexpr int W2 = 32 * C2;          // region cells along m2
+    static constexpr int T2 = W2 - 2 * kTbH;    // interior cells along m2
     static constexpr int V4 = PER / 2;          // float4 per cell
-    // shared memory: staging (per thread and row: psi, b_{k+1}, b_{k+2} as V4
+    static constexpr int NC = R * C2;           // cells per thread
+    static constexpr int N = PER * NC;          // orbitals per thread
+    // shared memory: staging (per thread and cell: psi, b_{k+1}, b_{k+2} as V4
     // float4 each, on-site as V4 float2), then the boundary rows each warp
-    // publishes per sweep (first row's A values, last row's B values, V4 of
-    // each per lane), double-buffered
-    static constexpr size_t stage = (size_t)threads * kTbR * V4 * (3 * sizeof(float4) + sizeof(float2));
-    static constexpr size_t exch = (size_t)2 * 2 * V4 * warps * 32 * sizeof(float2);
+    // publishes per sweep (first row's A values, last row's B values, V4 x C2
+    // of each per lane), double-buffered
+    static constexpr size_t stage = (size_t)threads * NC * V4 * (3 * sizeof(float4) + sizeof(float2));
+    static constexpr size_t exch = (size_t)2 * 2 * V4 * C2 * warps * 32 * sizeof(float2);
     static constexpr size_t smem = stage + exch;
     static_assert(smem <= 227 * 1024, "shared memory per block");
 };
+
+// Orbital o of cell c of row r in a thread's register arrays.
+template <int PER, int C2>
+__device__ __forceinline__ constexpr int tb_idx(int r, int c, int o)
+{
+    return (r * C2 + c) * PER + o;
+}
 
 // m mod L for m in [-L, 2L) by one compare (the usual case: regions no larger
 // than the lattice), by a division otherwise.
@@ -116,7 +133,7 @@ __device__ __forceinline__ double block_sum_f2(F2Sum *a, float2 *sm, int warp, i
     return out;
 }
 
-// This thread's staging slots: slot (r, v) at [(r * V4 + v) * threads].
+// This thread's staging slots: slot (cell j, v) at [(j * V4 + v) * threads].
 struct Stage {
     float4 *ps, *bx, *bz;
     float2 *on;
@@ -128,96 +145,145 @@ __device__ __forceinline__ void prefetch_tile(const TbParams &p, const Stage &st
 {
     typedef TbCfg<PER, KPM> C;
     const int t1 = tile / p.tiles2, t2 = tile - t1 * p.tiles2;
-    const int o1 = t1 * C::T1 - kTbH, o2 = t2 * kTbT2 - kTbH;
-    const int m2 = wrap(o2 + lane, p.L2);
+    const int o1 = t1 * C::T1 - kTbH, o2 = t2 * C::T2 - kTbH;
     const float4 *psi = reinterpret_cast<const float4 *>(p.psi);
     const float4 *bx = reinterpret_cast<const float4 *>(p.bx);
     const float4 *bz = reinterpret_cast<const float4 *>(p.bz);
     const float2 *on = reinterpret_cast<const float2 *>(p.onsite);
 #pragma unroll
-    for (int r = 0; r < kTbR; ++r) {
-        const int cell = wrap(o1 + r0 + r, p.L1) * p.L2 + m2;
+    for (int c = 0; c < C::C2; ++c) {
+        const int m2 = wrap(o2 + C::C2 * lane + c, p.L2);
 #pragma unroll
-        for (int v = 0; v < C::V4; ++v) {
-            const int g = cell * C::V4 + v;             // float4 index: orbitals 2v, 2v+1 of the cell
-            const int slot = (r * C::V4 + v) * C::threads;
-            if (!KPM) cp_async16(st.ps + slot, psi + g);
-            if (p.onsite) cp_async8(st.on + slot, on + g);
-            else st.on[slot] = make_float2(0.0f, 0.0f);
-            if (!first) {
-                cp_async16(st.bx + slot, bx + g);
-                cp_async16(st.bz + slot, bz + g);
+        for (int r = 0; r < C::R; ++r) {
+            const int cell = wrap(o1 + r0 + r, p.L1) * p.L2 + m2;
+#pragma unroll
+            for (int v = 0; v < C::V4; ++v) {
+                const int g = cell * C::V4 + v;         // float4 index: orbitals 2v, 2v+1 of the cell
+                const int slot = ((r * C::C2 + c) * C::V4 + v) * C::threads;
+                if (!KPM) cp_async16(st.ps + slot, psi + g);
+                if (p.onsite) cp_async8(st.on + slot, on + g);
+                else st.on[slot] = make_float2(0.0f, 0.0f);
+                if (!first) {
+                    cp_async16(st.bx + slot, bx + g);
+                    cp_async16(st.bz + slot, bz + g);
+                }
             }
         }
     }
     cp_async_commit();
 }
 
-// One sweep over this thread's kTbR cells (PER orbitals each, orbital o of
-// row r at index PER r + o: A_L = 2L, B_L = 2L + 1). x holds b_{k+1}, z holds
-// b_{k+2} on entry and the new b_k on exit. up[L] is the B_L value of the row
-// above this warp's first row, dn[L] the A_L value of the row below its last
-// row. FORM 0: a middle sweep with c_k real (out = a psi - z + A x); FORM 1:
-// c_k imaginary (i a psi); FORM 2: the general form
+// One sweep over this thread's R x C2 cells (PER orbitals each, at
+// tb_idx(r, c, o): A_L = 2L, B_L = 2L + 1). x holds b_{k+1}, z holds b_{k+2}
+// on entry and the new b_k on exit. up[c][L] is the B_L value of cell c of the
+// row above this warp's first row, dn[c][L] the A_L value of cell c of the row
+// below its last row. The three in-layer neighbours are summed unscaled and
+// enter through one FMA with t (the dimer partner of the bilayer through one
+// with t_perp).
+// FORM 0: a middle sweep with c_k real (out = a psi - z + A x); FORM 1: c_k
+// imaginary (i a psi); FORM 3: no psi term (out = A x - z, the KPM pass);
+// FORM 2: the general form
 //   out = alpha psi - hz z + beta (d x + t sum of the neighbours).
-template <int PER, int FORM>
-__device__ __forceinline__ void tb_rows(const float2 (&ps)[PER * kTbR], const float (&on)[PER * kTbR],
-                                        const float2 (&x)[PER * kTbR], float2 (&z)[PER * kTbR],
-                                        const float2 (&up)[PER / 2], const float2 (&dn)[PER / 2], float t,
-                                        float tp, const float *c)
+template <int PER, int R, int C2, int FORM>
+__device__ __forceinline__ void tb_rows(const float2 (&ps)[PER * R * C2], const float (&on)[PER * R * C2],
+                                        const float2 (&x)[PER * R * C2], float2 (&z)[PER * R * C2],
+                                        const float2 (&up)[C2][PER / 2], const float2 (&dn)[C2][PER / 2],
+                                        float t, float tp, const float *c)
 {
 #pragma unroll
-    for (int r = 0; r < kTbR; ++r) {
-        float2 sum[PER];                              // sum of each orbital's neighbours
+    for (int r = 0; r < R; ++r) {
+        float2 sum[C2][PER];                          // unscaled sum of each orbital's in-layer neighbours
 #pragma unroll
         for (int L = 0; L < PER / 2; ++L) {
-            const float2 xa = x[PER * r + 2 * L], xb = x[PER * r + 2 * L + 1];
-            // A(m): B(m), B(m - a1) (row above), B(m - a2) (lane to the left)
-            const float2 b1 = r > 0 ? x[PER * (r - 1) + 2 * L + 1] : up[L];
-            const float b2x = __shfl_up_sync(0xffffffffu, xb.x, 1);
-            const float b2y = __shfl_up_sync(0xffffffffu, xb.y, 1);
-            // B(m): A(m), A(m + a1) (row below), A(m + a2) (lane to the right)
-            const float2 a1 = r < kTbR - 1 ? x[PER * (r + 1) + 2 * L] : dn[L];
-            const float a2x = __shfl_down_sync(0xffffffffu, xa.x, 1);
-            const float a2y = __shfl_down_sync(0xffffffffu, xa.y, 1);
-            sum[2 * L] = make_float2(t * (xb.x + b1.x + b2x), t * (xb.y + b1.y + b2y));
-            sum[2 * L + 1] = make_float2(t * (xa.x + a1.x + a2x), t * (xa.y + a1.y + a2y));
-        }
-        if (PER == 4) {                               // the dimer A1(m) - B2(m)
-            const float2 a1v = x[PER * r], b2v = x[PER * r + 3];
-            sum[0].x = fmaf(tp, b2v.x, sum[0].x);
-            sum[0].y = fmaf(tp, b2v.y, sum[0].y);
-            sum[3].x = fmaf(tp, a1v.x, sum[3].x);
-            sum[3].y = fmaf(tp, a1v.y, sum[3].y);
+            // B of the last cell of the lane to the left, A of the first cell of the lane to the right
+            const float2 xbl = x[tb_idx<PER, C2>(r, C2 - 1, 2 * L + 1)];
+            const float2 xaf = x[tb_idx<PER, C2>(r, 0, 2 * L)];
+            const float2 bw = make_float2(__shfl_up_sync(0xffffffffu, xbl.x, 1),
+                                          __shfl_up_sync(0xffffffffu, xbl.y, 1));
+            const float2 ae = make_float2(__shfl_down_sync(0xffffffffu, xaf.x, 1),
+                                          __shfl_down_sync(0xffffffffu, xaf.y, 1));
+#pragma unroll
+            for (int cc = 0; cc < C2; ++cc) {
+                const float2 xa = x[tb_idx<PER, C2>(r, cc, 2 * L)], xb = x[tb_idx<PER, C2>(r, cc, 2 * L + 1)];
+                // A(m): B(m), B(m - a1) (row above), B(m - a2) (cell to the left)
+                const float2 b1 = r > 0 ? x[tb_idx<PER, C2>(r - 1, cc, 2 * L + 1)] : up[cc][L];
+                const float2 b2 = cc > 0 ? x[tb_idx<PER, C2>(r, cc - 1, 2 * L + 1)] : bw;
+                // B(m): A(m), A(m + a1) (row below), A(m + a2) (cell to the right)
+                const float2 a1 = r < R - 1 ? x[tb_idx<PER, C2>(r + 1, cc, 2 * L)] : dn[cc][L];
+                const float2 a2 = cc < C2 - 1 ? x[tb_idx<PER, C2>(r, cc + 1, 2 * L)] : ae;
+                sum[cc][2 * L] = make_float2(xb.x + b1.x + b2.x, xb.y + b1.y + b2.y);
+                sum[cc][2 * L + 1] = make_float2(xa.x + a1.x + a2.x, xa.y + a1.y + a2.y);
+            }
         }
 #pragma unroll
-        for (int o = 0; o < PER; ++o) {
-            const int i = PER * r + o;
-            const float2 xi = x[i], pv = ps[i], zz = z[i];
-            float2 out;
-            if (FORM == 0) {
-                out.x = sum[o].x + fmaf(on[i], xi.x, fmaf(c[0], pv.x, -zz.x));
-                out.y = sum[o].y + fmaf(on[i], xi.y, fmaf(c[0], pv.y, -zz.y));
-            } else if (FORM == 1) {
-                out.x = sum[o].x + fmaf(on[i], xi.x, fmaf(-c[1], pv.y, -zz.x));
-                out.y = sum[o].y + fmaf(on[i], xi.y, fmaf(c[1], pv.x, -zz.y));
-            } else {
-                const float tr = fmaf(-c[4], zz.x, fmaf(c[0], pv.x, -c[1] * pv.y));
-                const float ti = fmaf(-c[4], zz.y, fmaf(c[0], pv.y, c[1] * pv.x));
-                const float hr = fmaf(on[i], xi.x, sum[o].x), hi = fmaf(on[i], xi.y, sum[o].y);
-                out.x = fmaf(c[2], hr, fmaf(-c[3], hi, tr));
-                out.y = fmaf(c[2], hi, fmaf(c[3], hr, ti));
+        for (int cc = 0; cc < C2; ++cc) {
+#pragma unroll
+            for (int o = 0; o < PER; ++o) {
+                const int i = tb_idx<PER, C2>(r, cc, o);
+                const float2 xi = x[i], pv = ps[i], zz = z[i];
+                const bool dimer = PER == 4 && (o == 0 || o == 3);
+                const float2 pt = dimer ? x[tb_idx<PER, C2>(r, cc, 3 - o)] : make_float2(0.0f, 0.0f);
+                float2 out;
+                if (FORM != 2) {
+                    // the psi and z terms, then d x, the dimer partner, t times the neighbours
+                    float rx, ry;
+                    if (FORM == 0) { rx = fmaf(c[0], pv.x, -zz.x); ry = fmaf(c[0], pv.y, -zz.y); }
+                    else if (FORM == 1) { rx = fmaf(-c[1], pv.y, -zz.x); ry = fmaf(c[1], pv.x, -zz.y); }
+                    else { rx = -zz.x; ry = -zz.y; }
+                    rx = fmaf(on[i], xi.x, rx);
+                    ry = fmaf(on[i], xi.y, ry);
+                    if (dimer) { rx = fmaf(tp, pt.x, rx); ry = fmaf(tp, pt.y, ry); }
+                    out.x = fmaf(t, sum[cc][o].x, rx);
+                    out.y = fmaf(t, sum[cc][o].y, ry);
+                } else {
+                    const float tr = fmaf(-c[4], zz.x, fmaf(c[0], pv.x, -c[1] * pv.y));
+                    const float ti = fmaf(-c[4], zz.y, fmaf(c[0], pv.y, c[1] * pv.x));
+                    float dr = on[i] * xi.x, di = on[i] * xi.y;
+                    if (dimer) { dr = fmaf(tp, pt.x, dr); di = fmaf(tp, pt.y, di); }
+                    const float hr = fmaf(t, sum[cc][o].x, dr), hi = fmaf(t, sum[cc][o].y, di);
+                    out.x = fmaf(c[2], hr, fmaf(-c[3], hi, tr));
+                    out.y = fmaf(c[2], hi, fmaf(c[3], hr, ti));
+                }
+                z[i] = out;
             }
-            z[i] = out;
         }
     }
+}
+
+// Publishes this warp's boundary rows of x (the first row's A values, the last
+// row's B values) into exchange buffer ex and, after the block barrier, reads
+// the neighbouring warps' into up and dn (the region's first and last warps
+// read their own values: those rows are halo).
+// ex layout: [side][v][c][warp][lane] float2.
+template <int PER, int R, int C2, int WARPS>
+__device__ __forceinline__ void tb_exchange(float2 *ex, const float2 (&x)[PER * R * C2], float2 (&up)[C2][PER / 2],
+                                            float2 (&dn)[C2][PER / 2], int warp, int lane)
+{
+    constexpr int V4 = PER / 2;
+#pragma unroll
+    for (int v = 0; v < V4; ++v)
+#pragma unroll
+        for (int c = 0; c < C2; ++c) {
+            ex[((v * C2 + c) * WARPS + warp) * 32 + lane] = x[tb_idx<PER, C2>(0, c, 2 * v)];
+            ex[(((V4 + v) * C2 + c) * WARPS + warp) * 32 + lane] = x[tb_idx<PER, C2>(R - 1, c, 2 * v + 1)];
+        }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < V4; ++v)
+#pragma unroll
+        for (int c = 0; c < C2; ++c) {
+            up[c][v] = warp > 0 ? ex[(((V4 + v) * C2 + c) * WARPS + warp - 1) * 32 + lane]
+                                : x[tb_idx<PER, C2>(0, c, 2 * v + 1)];
+            dn[c][v] = warp < WARPS - 1 ? ex[((v * C2 + c) * WARPS + warp + 1) * 32 + lane]
+                                        : x[tb_idx<PER, C2>(R - 1, c, 2 * v)];
+        }
 }
 
 template <int PER>
 __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbParams p)
 {
     typedef TbCfg<PER> C;
-    constexpr int N = PER * kTbR;                 // orbitals per thread
+    constexpr int N = C::N;                       // orbitals per thread
     extern __shared__ __align__(16) unsigned char smem[];
     // FP32 coefficients of this launch's sweeps: alpha (re, im), beta (re, im), hz.
     // Formed once per block from the FP64 series: on GB300 an FP64 operation costs
@@ -228,15 +294,14 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
     Stage st;
     {
         float4 *base = reinterpret_cast<float4 *>(smem) + threadIdx.x;
-        const int span = kTbR * C::V4 * C::threads;
+        const int span = C::NC * C::V4 * C::threads;
         st.ps = base;
         st.bx = base + span;
         st.bz = base + 2 * span;
         st.on = reinterpret_cast<float2 *>(reinterpret_cast<float4 *>(smem) + 3 * span) + threadIdx.x;
     }
-    // exch[buf][side][v][w][lane]: side 0 = first row's A_v of warp w, side 1 = last row's B_v
     float2 *exch = reinterpret_cast<float2 *>(smem + C::stage);
-    const int r0 = warp * kTbR;                   // this warp's first region row
+    const int r0 = warp * C::R;                   // this warp's first region row
     const int K = p.K;
     const bool first = p.j0 == 0;
     const bool final = p.j0 + p.S == K - 1;
@@ -278,18 +343,19 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
     // sweeps run so far by this block: the exchange buffer alternates with it
     // (across tiles too), so a buffer is rewritten only two barriers after its reads
     int nsweep = 0;
+    constexpr int kExch = 2 * C::V4 * C::C2 * C::warps * 32;   // float2 per exchange buffer
     if ((int)blockIdx.x < ntiles) prefetch_tile<PER, false>(p, st, blockIdx.x, r0, lane, first);
     __syncthreads();                               // the coefficient table
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int t1 = tile / p.tiles2, t2 = tile - t1 * p.tiles2;
-        const int o1 = t1 * C::T1 - kTbH, o2 = t2 * kTbT2 - kTbH;
+        const int o1 = t1 * C::T1 - kTbH, o2 = t2 * C::T2 - kTbH;
         cp_async_wait_all();                      // this thread's own staging slots
 #pragma unroll
-        for (int r = 0; r < kTbR; ++r) {
+        for (int j = 0; j < C::NC; ++j) {
 #pragma unroll
             for (int v = 0; v < C::V4; ++v) {
-                const int slot = (r * C::V4 + v) * C::threads;
-                const int i = PER * r + 2 * v;
+                const int slot = (j * C::V4 + v) * C::threads;
+                const int i = PER * j + 2 * v;
                 const float4 q = st.ps[slot];
                 ps[i] = make_float2(q.x, q.y);
                 ps[i + 1] = make_float2(q.z, q.w);
@@ -317,58 +383,52 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
         for (int q = 0; q < p.S; ++q) {
             const float *c = cf[q];
             const int form = cform[q];
-            float2 *ex = exch + (nsweep++ & 1) * 2 * C::V4 * C::warps * 32;
-            const float2 *x = (q & 1) ? zo : xo;
-            float2 up[C::V4], dn[C::V4];
-#pragma unroll
-            for (int v = 0; v < C::V4; ++v) {
-                ex[(v * C::warps + warp) * 32 + lane] = x[2 * v];                                   // first row, A_v
-                ex[((C::V4 + v) * C::warps + warp) * 32 + lane] = x[PER * (kTbR - 1) + 2 * v + 1]; // last row, B_v
-            }
-            __syncthreads();
-#pragma unroll
-            for (int v = 0; v < C::V4; ++v) {
-                up[v] = warp > 0 ? ex[((C::V4 + v) * C::warps + warp - 1) * 32 + lane] : x[2 * v + 1];
-                dn[v] = warp < C::warps - 1 ? ex[(v * C::warps + warp + 1) * 32 + lane] : x[PER * (kTbR - 1) + 2 * v];
-            }
+            float2 *ex = exch + (nsweep++ & 1) * kExch;
+            float2 up[C::C2][C::V4], dn[C::C2][C::V4];
             if ((q & 1) == 0) {
-                if (form == 0) tb_rows<PER, 0>(ps, on, xo, zo, up, dn, t, tp, c);
-                else if (form == 1) tb_rows<PER, 1>(ps, on, xo, zo, up, dn, t, tp, c);
-                else tb_rows<PER, 2>(ps, on, xo, zo, up, dn, t, tp, c);
+                tb_exchange<PER, C::R, C::C2, C::warps>(ex, xo, up, dn, warp, lane);
+                if (form == 0) tb_rows<PER, C::R, C::C2, 0>(ps, on, xo, zo, up, dn, t, tp, c);
+                else if (form == 1) tb_rows<PER, C::R, C::C2, 1>(ps, on, xo, zo, up, dn, t, tp, c);
+                else tb_rows<PER, C::R, C::C2, 2>(ps, on, xo, zo, up, dn, t, tp, c);
             } else {
-                if (form == 0) tb_rows<PER, 0>(ps, on, zo, xo, up, dn, t, tp, c);
-                else if (form == 1) tb_rows<PER, 1>(ps, on, zo, xo, up, dn, t, tp, c);
-                else tb_rows<PER, 2>(ps, on, zo, xo, up, dn, t, tp, c);
+                tb_exchange<PER, C::R, C::C2, C::warps>(ex, zo, up, dn, warp, lane);
+                if (form == 0) tb_rows<PER, C::R, C::C2, 0>(ps, on, zo, xo, up, dn, t, tp, c);
+                else if (form == 1) tb_rows<PER, C::R, C::C2, 1>(ps, on, zo, xo, up, dn, t, tp, c);
+                else tb_rows<PER, C::R, C::C2, 2>(ps, on, zo, xo, up, dn, t, tp, c);
             }
         }
         // newest b (or psi(t_{n+1})) in zo after an odd number of sweeps, else in xo
         const bool odd = (p.S & 1) != 0;
-        const int m2 = o2 + lane;
-        const bool col_in = lane >= kTbH && lane < kTbH + kTbT2 && m2 < p.L2;
 #pragma unroll
-        for (int r = 0; r < kTbR; ++r) {
-            const int c1 = r0 + r;
-            const int m1 = o1 + c1;
-            if (!col_in || c1 < kTbH || c1 >= kTbH + C::T1 || m1 >= p.L1) continue;
-            const int cell = m1 * p.L2 + m2;
+        for (int cc = 0; cc < C::C2; ++cc) {
+            const int l2 = C::C2 * lane + cc;       // region column
+            const int m2 = o2 + l2;
+            if (l2 < kTbH || l2 >= kTbH + C::T2 || m2 >= p.L2) continue;
 #pragma unroll
-            for (int v = 0; v < C::V4; ++v) {
-                const int i = PER * r + 2 * v;
-                const int g = cell * C::V4 + v;
-                const float2 na = odd ? zo[i] : xo[i], nb = odd ? zo[i + 1] : xo[i + 1];
-                const float4 yn = make_float4(na.x, na.y, nb.x, nb.y);
-                if (final) {
-                    __stcs(reinterpret_cast<float4 *>(p.psi_out) + g, yn);
-                    const float4 q0 = __ldcs(reinterpret_cast<const float4 *>(p.psi0) + g);
-                    // conj(q0) y = (q0.x y.x + q0.y y.y) + i (q0.x y.y - q0.y y.x), two orbitals
-                    sr.add_dot(q0.x, yn.x, q0.y, yn.y);
-                    si.add_dot(q0.x, yn.y, -q0.y, yn.x);
-                    sr.add_dot(q0.z, yn.z, q0.w, yn.w);
-                    si.add_dot(q0.z, yn.w, -q0.w, yn.z);
-                } else {
-                    const float2 pa = odd ? xo[i] : zo[i], pb = odd ? xo[i + 1] : zo[i + 1];
-                    __stcs(reinterpret_cast<float4 *>(p.ox) + g, yn);
-                    __stcs(reinterpret_cast<float4 *>(p.oz) + g, make_float4(pa.x, pa.y, pb.x, pb.y));
+            for (int r = 0; r < C::R; ++r) {
+                const int c1 = r0 + r;
+                const int m1 = o1 + c1;
+                if (c1 < kTbH || c1 >= kTbH + C::T1 || m1 >= p.L1) continue;
+                const int cell = m1 * p.L2 + m2;
+#pragma unroll
+                for (int v = 0; v < C::V4; ++v) {
+                    const int i = tb_idx<PER, C::C2>(r, cc, 2 * v);
+                    const int g = cell * C::V4 + v;
+                    const float2 na = odd ? zo[i] : xo[i], nb = odd ? zo[i + 1] : xo[i + 1];
+                    const float4 yn = make_float4(na.x, na.y, nb.x, nb.y);
+                    if (final) {
+                        __stcs(reinterpret_cast<float4 *>(p.psi_out) + g, yn);
+                        const float4 q0 = __ldcs(reinterpret_cast<const float4 *>(p.psi0) + g);
+                        // conj(q0) y = (q0.x y.x + q0.y y.y) + i (q0.x y.y - q0.y y.x), two orbitals
+                        sr.add_dot(q0.x, yn.x, q0.y, yn.y);
+                        si.add_dot(q0.x, yn.y, -q0.y, yn.x);
+                        sr.add_dot(q0.z, yn.z, q0.w, yn.w);
+                        si.add_dot(q0.z, yn.w, -q0.w, yn.z);
+                    } else {
+                        const float2 pa = odd ? xo[i] : zo[i], pb = odd ? xo[i + 1] : zo[i + 1];
+                        __stcs(reinterpret_cast<float4 *>(p.ox) + g, yn);
+                        __stcs(reinterpret_cast<float4 *>(p.oz) + g, make_float4(pa.x, pa.y, pb.x, pb.y));
+                    }
                 }
             }
         }
@@ -396,20 +456,20 @@ template <int PER>
 __global__ void __launch_bounds__(TbCfg<PER, true>::threads, 1) tb_kpm_kernel(TbParams p)
 {
     typedef TbCfg<PER, true> C;
-    constexpr int N = PER * kTbR;
+    constexpr int N = C::N;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Stage st;
     {
         float4 *base = reinterpret_cast<float4 *>(smem) + threadIdx.x;
-        const int span = kTbR * C::V4 * C::threads;
+        const int span = C::NC * C::V4 * C::threads;
         st.ps = base;
         st.bx = base + span;
         st.bz = base + 2 * span;
         st.on = reinterpret_cast<float2 *>(reinterpret_cast<float4 *>(smem) + 3 * span) + threadIdx.x;
     }
     float2 *exch = reinterpret_cast<float2 *>(smem + C::stage);
-    const int r0 = warp * kTbR;
+    const int r0 = warp * C::R;
     const int ntiles = p.tiles1 * p.tiles2;
     const float t = p.t, tp = p.t_perp;
     // T_{m+1} = A T_m - T_{m-1}: the middle-sweep form with no psi term
@@ -422,17 +482,18 @@ __global__ void __launch_bounds__(TbCfg<PER, true>::threads, 1) tb_kpm_kernel(Tb
     float2 xo[N], zo[N];
     float on[N];
     int nsweep = 0;
+    constexpr int kExch = 2 * C::V4 * C::C2 * C::warps * 32;
     if ((int)blockIdx.x < ntiles) prefetch_tile<PER, true>(p, st, blockIdx.x, r0, lane, false);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int t1 = tile / p.tiles2, t2 = tile - t1 * p.tiles2;
-        const int o1 = t1 * C::T1 - kTbH, o2 = t2 * kTbT2 - kTbH;
+        const int o1 = t1 * C::T1 - kTbH, o2 = t2 * C::T2 - kTbH;
         cp_async_wait_all();
 #pragma unroll
-        for (int r = 0; r < kTbR; ++r) {
+        for (int j = 0; j < C::NC; ++j) {
 #pragma unroll
             for (int v = 0; v < C::V4; ++v) {
-                const int slot = (r * C::V4 + v) * C::threads;
-                const int i = PER * r + 2 * v;
+                const int slot = (j * C::V4 + v) * C::threads;
+                const int i = PER * j + 2 * v;
                 const float2 o = st.on[slot];
                 on[i] = o.x;
                 on[i + 1] = o.y;
@@ -444,46 +505,46 @@ __global__ void __launch_bounds__(TbCfg<PER, true>::threads, 1) tb_kpm_kernel(Tb
             }
         }
         if (tile + (int)gridDim.x < ntiles) prefetch_tile<PER, true>(p, st, tile + gridDim.x, r0, lane, false);
-        const int m2 = o2 + lane;
-        const bool col_in = lane >= kTbH && lane < kTbH + kTbT2 && m2 < p.L2;
-        bool row_in[kTbR];
+        bool cell_in[C::R][C::C2];
 #pragma unroll
-        for (int r = 0; r < kTbR; ++r) {
-            const int c1 = r0 + r;
-            row_in[r] = col_in && c1 >= kTbH && c1 < kTbH + C::T1 && o1 + c1 < p.L1;
+        for (int cc = 0; cc < C::C2; ++cc) {
+            const int l2 = C::C2 * lane + cc;
+            const bool col_in = l2 >= kTbH && l2 < kTbH + C::T2 && o2 + l2 < p.L2;
+#pragma unroll
+            for (int r = 0; r < C::R; ++r) {
+                const int c1 = r0 + r;
+                cell_in[r][cc] = col_in && c1 >= kTbH && c1 < kTbH + C::T1 && o1 + c1 < p.L1;
+            }
         }
 #pragma unroll
         for (int q = 0; q < kTbS; ++q) {
             if (q < p.S) {
-                float2 *ex = exch + (nsweep++ & 1) * 2 * C::V4 * C::warps * 32;
+                float2 *ex = exch + (nsweep++ & 1) * kExch;
                 float2 *x = (q & 1) ? zo : xo;
                 float2 *y = (q & 1) ? xo : zo;
-                float2 up[C::V4], dn[C::V4];
-#pragma unroll
-                for (int v = 0; v < C::V4; ++v) {
-                    ex[(v * C::warps + warp) * 32 + lane] = x[2 * v];
-                    ex[((C::V4 + v) * C::warps + warp) * 32 + lane] = x[PER * (kTbR - 1) + 2 * v + 1];
+                float2 up[C::C2][C::V4], dn[C::C2][C::V4];
+                if ((q & 1) == 0) {
+                    tb_exchange<PER, C::R, C::C2, C::warps>(ex, xo, up, dn, warp, lane);
+                    tb_rows<PER, C::R, C::C2, 3>(zero, on, xo, zo, up, dn, t, tp, cm);
+                } else {
+                    tb_exchange<PER, C::R, C::C2, C::warps>(ex, zo, up, dn, warp, lane);
+                    tb_rows<PER, C::R, C::C2, 3>(zero, on, zo, xo, up, dn, t, tp, cm);
                 }
-                __syncthreads();
-#pragma unroll
-                for (int v = 0; v < C::V4; ++v) {
-                    up[v] = warp > 0 ? ex[((C::V4 + v) * C::warps + warp - 1) * 32 + lane] : x[2 * v + 1];
-                    dn[v] = warp < C::warps - 1 ? ex[(v * C::warps + warp + 1) * 32 + lane]
-                                                : x[PER * (kTbR - 1) + 2 * v];
-                }
-                if ((q & 1) == 0) tb_rows<PER, 0>(zero, on, xo, zo, up, dn, t, tp, cm);
-                else tb_rows<PER, 0>(zero, on, zo, xo, up, dn, t, tp, cm);
                 // the dots of this pass: x = T_{m+q}, y = T_{m+q+1}
                 float nn = 0.0f, cr = 0.0f, ci = 0.0f;
 #pragma unroll
-                for (int r = 0; r < kTbR; ++r) {
-                    if (!row_in[r]) continue;
+                for (int r = 0; r < C::R; ++r) {
 #pragma unroll
-                    for (int o = 0; o < PER; ++o) {
-                        const float2 a = x[PER * r + o], b = y[PER * r + o];
-                        nn = fmaf(a.x, a.x, fmaf(a.y, a.y, nn));
-                        cr = fmaf(b.x, a.x, fmaf(b.y, a.y, cr));
-                        ci = fmaf(b.x, a.y, fmaf(-b.y, a.x, ci));
+                    for (int cc = 0; cc < C::C2; ++cc) {
+                        if (!cell_in[r][cc]) continue;
+#pragma unroll
+                        for (int o = 0; o < PER; ++o) {
+                            const int i = tb_idx<PER, C::C2>(r, cc, o);
+                            const float2 a = x[i], b = y[i];
+                            nn = fmaf(a.x, a.x, fmaf(a.y, a.y, nn));
+                            cr = fmaf(b.x, a.x, fmaf(b.y, a.y, cr));
+                            ci = fmaf(b.x, a.y, fmaf(-b.y, a.x, ci));
+                        }
                     }
                 }
                 acc[q][0].add(nn);
@@ -493,16 +554,20 @@ __global__ void __launch_bounds__(TbCfg<PER, true>::threads, 1) tb_kpm_kernel(Tb
         }
         const bool odd = (p.S & 1) != 0;
 #pragma unroll
-        for (int r = 0; r < kTbR; ++r) {
-            if (!row_in[r]) continue;
-            const int cell = (o1 + r0 + r) * p.L2 + m2;
+        for (int cc = 0; cc < C::C2; ++cc) {
+            const int m2 = o2 + C::C2 * lane + cc;
 #pragma unroll
-            for (int v = 0; v < C::V4; ++v) {
-                const int i = PER * r + 2 * v;
-                const float2 na = odd ? zo[i] : xo[i], nb = odd ? zo[i + 1] : xo[i + 1];
-                const float2 pa = odd ? xo[i] : zo[i], pb = odd ? xo[i + 1] : zo[i + 1];
-                __stcs(reinterpret_cast<float4 *>(p.ox) + cell * C::V4 + v, make_float4(na.x, na.y, nb.x, nb.y));
-                __stcs(reinterpret_cast<float4 *>(p.oz) + cell * C::V4 + v, make_float4(pa.x, pa.y, pb.x, pb.y));
+            for (int r = 0; r < C::R; ++r) {
+                if (!cell_in[r][cc]) continue;
+                const int cell = (o1 + r0 + r) * p.L2 + m2;
+#pragma unroll
+                for (int v = 0; v < C::V4; ++v) {
+                    const int i = tb_idx<PER, C::C2>(r, cc, 2 * v);
+                    const float2 na = odd ? zo[i] : xo[i], nb = odd ? zo[i + 1] : xo[i + 1];
+                    const float2 pa = odd ? xo[i] : zo[i], pb = odd ? xo[i + 1] : zo[i + 1];
+                    __stcs(reinterpret_cast<float4 *>(p.ox) + cell * C::V4 + v, make_float4(na.x, na.y, nb.x, nb.y));
+                    __stcs(reinterpret_cast<float4 *>(p.oz) + cell * C::V4 + v, make_float4(pa.x, pa.y, pb.x, pb.y));
+                }
             }
         }
     }
@@ -527,8 +592,9 @@ __global__ void __launch_bounds__(TbCfg<PER, true>::threads, 1) tb_kpm_kernel(Tb
 int tb_tiles(int per, int64_t l1, int64_t l2, int *tiles1, int *tiles2)
 {
     const int t1 = per == 2 ? TbCfg<2>::T1 : TbCfg<4>::T1;
+    const int t2 = per == 2 ? TbCfg<2>::T2 : TbCfg<4>::T2;
     *tiles1 = (int)((l1 + t1 - 1) / t1);
-    *tiles2 = (int)((l2 + kTbT2 - 1) / kTbT2);
+    *tiles2 = (int)((l2 + t2 - 1) / t2);
     return *tiles1 * *tiles2;
 }
 
@@ -544,8 +610,9 @@ cudaError_t tb_prepare(int per)
 int tb_kpm_tiles(int per, int64_t l1, int64_t l2, int *tiles1, int *tiles2)
 {
     const int t1 = per == 2 ? TbCfg<2, true>::T1 : TbCfg<4, true>::T1;
+    const int t2 = per == 2 ? TbCfg<2, true>::T2 : TbCfg<4, true>::T2;
     *tiles1 = (int)((l1 + t1 - 1) / t1);
-    *tiles2 = (int)((l2 + kTbT2 - 1) / kTbT2);
+    *tiles2 = (int)((l2 + t2 - 1) / t2);
     return *tiles1 * *tiles2;
 }
 
