@@ -1,4 +1,9 @@
-"""Haydock recursion and continued-fraction LDOS on the GPU against the oracle."""
+"""Haydock recursion and continued-fraction LDOS on the GPU against the oracle.
+
+Bars: FP64 chain coefficients, LDOS and correlations within 1e-10 of the oracle
+(measured on GB300: <= 1.2e-13 over 120 levels); FP32 coefficients within 1e-5
+(measured 4.8e-7: FP32 rounding of the stored vectors, 2^-24 per sweep, grows along
+the recursion), FP32 correlations within 3e-5 as in the FP32 tests."""
 import numpy as np
 import pytest
 
@@ -8,14 +13,14 @@ import paper_2509_26309_gb300 as tb
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec,tol", [(tb.TBPM_FP64, 1e-10), (tb.TBPM_FP32, 2e-4)])
+@pytest.mark.parametrize("prec,tol", [(tb.TBPM_FP64, 1e-10), (tb.TBPM_FP32, 1e-5)])
 def test_haydock_coefficients(orc, prec, tol):
     h = ti.graphene_csr(40, 30, onsite=ti.anderson_onsite(2400, 1.0, 3), bond_phases=[0.2, 0.5, -0.3])
     ctx = tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, 9.0, tb.make_opts(precision=prec))
     for psi0 in (ti.site_state(h.n, 77), ti.random_phase_state(h.n, 4)):
         a, b = tb.tbpm_haydock(ctx, psi0, 120)
         ra, rb = orc.haydock(h, psi0, 120)
-        assert np.max(np.abs(a - ra)) <= tol * 10 and np.max(np.abs(b - rb)) <= tol * 10
+        assert np.max(np.abs(a - ra)) <= tol and np.max(np.abs(b - rb)) <= tol
 
 
 def test_haydock_1024x1024_and_ldos(orc):
@@ -26,11 +31,11 @@ def test_haydock_1024x1024_and_ldos(orc):
     psi0 = ti.site_state(n, 123457)
     a, b = tb.tbpm_haydock(ctx, psi0, 60)
     ra, rb = orc.haydock(h, psi0, 60)
-    assert np.max(np.abs(a - ra)) <= 1e-9 and np.max(np.abs(b - rb)) <= 1e-9
+    assert np.max(np.abs(a - ra)) <= 1e-10 and np.max(np.abs(b - rb)) <= 1e-10
     E = np.linspace(-9, 9, 361)
     got = tb.tbpm_haydock_ldos(ctx, a, b, E, 0.1)
     ref = orc.haydock_ldos(ra, rb, E, 0.1)
-    assert np.max(np.abs(got - ref)) <= 1e-9
+    assert np.max(np.abs(got - ref)) <= 1e-10
 
 
 def test_haydock_stencil_and_chain_stop(orc):
@@ -70,7 +75,7 @@ def test_haydock_deterministic_and_launch_order_neutral(orc):
     for a, b in runs[1:]:
         assert np.array_equal(a, runs[0][0]) and np.array_equal(b, runs[0][1])
     ra, rb = orc.haydock(h, psi0, 200)
-    assert np.max(np.abs(runs[0][0] - ra)) <= 1e-9 and np.max(np.abs(runs[0][1] - rb)) <= 1e-9
+    assert np.max(np.abs(runs[0][0] - ra)) <= 1e-10 and np.max(np.abs(runs[0][1] - rb)) <= 1e-10
 
 
 @pytest.mark.parametrize("prec,tol", [(tb.TBPM_FP64, 1e-10), (tb.TBPM_FP32, 1e-5)])
@@ -86,7 +91,7 @@ def test_quasi_eigenstates(orc, prec, tol):
     assert np.max(np.abs(got - ref)) <= tol
     # the ordinary correlation call still works on the same context afterwards
     c = tb.tbpm_dos_corr(ctx, psi0, dt, 20)
-    assert np.max(np.abs(c - orc.dos_corr(h, 9.0, psi0, dt, 20))) <= max(tol, 1e-10) * 10
+    assert np.max(np.abs(c - orc.dos_corr(h, 9.0, psi0, dt, 20))) <= (1e-10 if prec == tb.TBPM_FP64 else 3e-5)
     # the graphs of the first call serve a call with other energies of the same
     # count (read from device memory at run time); another dt or count rebuilds them
     E2 = E + 0.35
