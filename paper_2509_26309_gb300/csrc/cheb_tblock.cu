@@ -279,7 +279,22 @@ __device__ __forceinline__ void tb_exchange(float2 *ex, const float2 (&x)[PER * 
         }
 }
 
-template <int PER>
+// Sweep forms of a launch, 3 bits per sweep position (0, 1: middle sweeps with
+// c_k real or imaginary; 2: the general form; 7: no sweep at this position).
+// PAT < 0: the forms are read from the block's coefficient table at run time.
+constexpr int kPatEnd = 7;
+constexpr int tb_pat(int f0, int f1, int f2, int f3, int f4, int f5)
+{
+    return f0 | (f1 << 3) | (f2 << 6) | (f3 << 9) | (f4 << 12) | (f5 << 15);
+}
+// The launches of a K = 18 time step (x = pi) and of odd-K steps of the same
+// partition: first (first, second and four middle sweeps), middle (six middle
+// sweeps), final (four middle sweeps and the final one), by parity of k.
+constexpr int kPatFirst0 = tb_pat(2, 2, 0, 1, 0, 1), kPatFirst1 = tb_pat(2, 2, 1, 0, 1, 0);
+constexpr int kPatMid0 = tb_pat(0, 1, 0, 1, 0, 1), kPatMid1 = tb_pat(1, 0, 1, 0, 1, 0);
+constexpr int kPatFinal0 = tb_pat(0, 1, 0, 1, 2, kPatEnd), kPatFinal1 = tb_pat(1, 0, 1, 0, 2, kPatEnd);
+
+template <int PER, int PAT>
 __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbParams p)
 {
     typedef TbCfg<PER> C;
@@ -384,9 +399,10 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
         // exchange buffer; 6.1e11 against 5.6e11 orbital-terms/s for the runtime loop)
 #pragma unroll
         for (int q = 0; q < kTbS; ++q) {
-            if (q >= p.S) break;
+            const int fq = PAT >= 0 ? ((PAT >> (3 * q)) & 7) : -1;   // compile-time after unrolling
+            if (PAT >= 0 ? fq == kPatEnd : q >= p.S) break;
             const float *c = cf[q];
-            const int form = cform[q];
+            const int form = PAT >= 0 ? fq : cform[q];
             float2 *ex = exch + (nsweep++ & 1) * kExch;
             float2 up[C::C2][C::V4], dn[C::C2][C::V4];
             if ((q & 1) == 0) {
@@ -602,13 +618,60 @@ int tb_tiles(int per, int64_t l1, int64_t l2, int *tiles1, int *tiles2)
     return *tiles1 * *tiles2;
 }
 
+namespace {
+
+// The specialised form patterns, then the run-time one.
+constexpr int kTbPats[7] = {kPatFirst0, kPatFirst1, kPatMid0, kPatMid1, kPatFinal0, kPatFinal1, -1};
+
+template <int PER, int I = 0>
+cudaError_t tb_prepare_all()
+{
+    if constexpr (I < 7) {
+        cudaError_t e = cudaFuncSetAttribute(tb_block_kernel<PER, kTbPats[I]>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TbCfg<PER>::smem);
+        if (e != cudaSuccess) return e;
+        return tb_prepare_all<PER, I + 1>();
+    }
+    return cudaSuccess;
+}
+
+template <int PER, int I = 0>
+cudaError_t tb_launch_pat(int pat, const TbParams &p, int grid, cudaStream_t s)
+{
+    if constexpr (I < 7) {
+        if (kTbPats[I] == pat || kTbPats[I] < 0) {
+            tb_block_kernel<PER, kTbPats[I]><<<grid, TbCfg<PER>::threads, TbCfg<PER>::smem, s>>>(p);
+            return cudaGetLastError();
+        }
+        return tb_launch_pat<PER, I + 1>(pat, p, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The form pattern of the launch of sweeps [j0, j0 + S) of a K-term step, as the
+// kernel's coefficient table forms it.
+int tb_launch_pattern(int K, int j0, int S)
+{
+    int pat = 0;
+    for (int q = 0; q < kTbS; ++q) {
+        int f = kPatEnd;
+        if (q < S) {
+            const int j = j0 + q;
+            const bool is_first = j == 0, is_final = j == K - 2;
+            const bool is_second = !is_first && !is_final && j == 1;
+            const int k = is_final ? 0 : K - 2 - j;
+            f = (is_first || is_second || is_final) ? 2 : (k & 1);
+        }
+        pat |= f << (3 * q);
+    }
+    return pat;
+}
+
+}  // namespace
+
 cudaError_t tb_prepare(int per)
 {
-    if (per == 2)
-        return cudaFuncSetAttribute(tb_block_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)TbCfg<2>::smem);
-    return cudaFuncSetAttribute(tb_block_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)TbCfg<4>::smem);
+    return per == 2 ? tb_prepare_all<2>() : tb_prepare_all<4>();
 }
 
 int tb_kpm_tiles(int per, int64_t l1, int64_t l2, int *tiles1, int *tiles2)
@@ -638,9 +701,10 @@ cudaError_t launch_tb_kpm(int per, const TbParams &p, int grid, cudaStream_t s)
 
 cudaError_t launch_tb_block(int per, const TbParams &p, int grid, cudaStream_t s)
 {
-    if (per == 2) tb_block_kernel<2><<<grid, TbCfg<2>::threads, TbCfg<2>::smem, s>>>(p);
-    else tb_block_kernel<4><<<grid, TbCfg<4>::threads, TbCfg<4>::smem, s>>>(p);
-    return cudaGetLastError();
+    // a launch whose sweep forms match a specialised pattern runs the kernel
+    // compiled for it (no form dispatch), any other the run-time form table
+    const int pat = tb_launch_pattern(p.K, p.j0, p.S);
+    return per == 2 ? tb_launch_pat<2>(pat, p, grid, s) : tb_launch_pat<4>(pat, p, grid, s);
 }
 
 }  // namespace tbpm
