@@ -46,9 +46,10 @@ constexpr int kTbH = (kTbS + 1) / 2;            // halo cells per side
 // registers per thread); the bilayer, with twice the state per cell, and the
 // KPM passes, which also keep per-pass dot sums in registers, run 512 threads
 // of 3 rows x 1 cell (32 x 48 cells). Two cells per lane (in-thread
-// neighbours along m2, half the shuffles, a 64-cell-wide region) measured
-// slower on GB300 for the monolayer time steps: 4.2e11 orbital-terms/s at 512
-// threads x 3 rows and 4.1e11 at 768 x 2 rows, against 5.5e11 here (4096^2).
+// neighbours along m2, half the shuffles, a 64-cell-wide region; the staging
+// loads stay coalesced) measured slower on GB300 for the monolayer time steps:
+// 4.2e11 orbital-terms/s at 512 threads x 3 rows, 4.1e11 at 768 x 2 rows and
+// 1024 x 1 row, against 6.1e11 here (4096^2).
 template <int PER, bool KPM = false>
 struct TbCfg {
     static constexpr bool kMonoSteps = PER == 2 && !KPM;
@@ -150,16 +151,21 @@ __device__ __forceinline__ void prefetch_tile(const TbParams &p, const Stage &st
     const float4 *bx = reinterpret_cast<const float4 *>(p.bx);
     const float4 *bz = reinterpret_cast<const float4 *>(p.bz);
     const float2 *on = reinterpret_cast<const float2 *>(p.onsite);
+    // lane l fetches region column j = 32 c + l (coalesced) into the staging
+    // slot of the column's owner, lane j / C2, cell j % C2 of the same warp (the
+    // warp synchronises before the owners read and before the slots are refilled)
 #pragma unroll
     for (int c = 0; c < C::C2; ++c) {
-        const int m2 = wrap(o2 + C::C2 * lane + c, p.L2);
+        const int j = 32 * c + lane;
+        const int own = j / C::C2 - lane, oc = j % C::C2;   // owner's lane offset, its cell
+        const int m2 = wrap(o2 + j, p.L2);
 #pragma unroll
         for (int r = 0; r < C::R; ++r) {
             const int cell = wrap(o1 + r0 + r, p.L1) * p.L2 + m2;
 #pragma unroll
             for (int v = 0; v < C::V4; ++v) {
                 const int g = cell * C::V4 + v;         // float4 index: orbitals 2v, 2v+1 of the cell
-                const int slot = ((r * C::C2 + c) * C::V4 + v) * C::threads;
+                const int slot = ((r * C::C2 + oc) * C::V4 + v) * C::threads + own;
                 if (!KPM) cp_async16(st.ps + slot, psi + g);
                 if (p.onsite) cp_async8(st.on + slot, on + g);
                 else st.on[slot] = make_float2(0.0f, 0.0f);
@@ -364,7 +370,8 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int t1 = tile / p.tiles2, t2 = tile - t1 * p.tiles2;
         const int o1 = t1 * C::T1 - kTbH, o2 = t2 * C::T2 - kTbH;
-        cp_async_wait_all();                      // this thread's own staging slots
+        cp_async_wait_all();                      // the staging slots this thread filled
+        if (C::C2 > 1) __syncwarp();              // and those its warp's other lanes filled
 #pragma unroll
         for (int j = 0; j < C::NC; ++j) {
 #pragma unroll
@@ -392,6 +399,7 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
             }
         }
         // the staging slots are free again: fetch the next tile during the sweeps
+        if (C::C2 > 1) __syncwarp();              // every lane has read its slots
         if (tile + (int)gridDim.x < ntiles) prefetch_tile<PER, false>(p, st, tile + gridDim.x, r0, lane, first);
         // the register arrays trade roles each sweep: even sweeps read b_{k+1} from
         // xo and overwrite zo with b_k, odd sweeps the reverse. The loop is unrolled
