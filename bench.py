@@ -475,8 +475,9 @@ def run_variants(args, dev, stream):
         (K = 18 for every instance), 1024 steps: autotuned launch shape against
         the default shape, and against the same instances one context at a time;
       - FP32 single state, stored matrix: graphene 2048x2048, W = 1
-        (N = 8,388,608), 1024 steps, with and without renormalisation, C(t) and
-        DOS L1 errors against the oracle's stored FP64 C(t) of the same state;
+        (N = 8,388,608), 1024 steps, with and without renormalisation and with
+        the autotuned launch shape, C(t) and DOS L1 errors against the oracle's
+        stored FP64 C(t) of the same state;
       - FP32 block of 16 states vs FP64 single state on graphene 4096x4096,
         W = 1 (N = 33,554,432, the paper's benchmark lattice), stencil and
         stored-matrix paths, 128 steps each (the speedup is a throughput ratio,
@@ -570,14 +571,18 @@ def run_variants(args, dev, stream):
         "dos_l1": None if orc3 is None else dos_l1(c64, ref3h, orc3, DT),
         "reference": "oracle C(t), 1024 steps (tests/golden/oracle_graphene2048_dos1024_s0.txt)"}
     out = torch.empty((1, 1025), dtype=torch.complex128, device=dev)
-    for name, flags in (("fp32_sell_2048x2048", 0), ("fp32_sell_renorm_2048x2048", tb.TBPM_F_RENORM)):
+    for name, flags in (("fp32_sell_2048x2048", 0), ("fp32_sell_renorm_2048x2048", tb.TBPM_F_RENORM),
+                        ("fp32_sell_autotuned_2048x2048", tb.TBPM_F_AUTOTUNE)):
         ctx = tb.tbpm_create(n3, h3.row_ptr, h3.col, h3.val, RESCALE,
                              tb.make_opts(precision=tb.TBPM_FP32, flags=flags, stream=so))
         ms = timed_calls(lambda: tb.tbpm_dos_corr(ctx, psi, DT, 1024, out=out), 1, stream)
         K = tb.tbpm_get_info(ctx)["num_terms"]
         v3 = n3 * 1024 * (K - 1) / (ms / 1e3)
+        i3 = tb.tbpm_get_info(ctx)
         res[name] = {"value": v3, "unit": UNIT, "ms_per_call": ms,
                      "states": 1, "n_steps": 1024,
+                     "shape": {"grid_blocks": i3["grid_blocks"], "block_threads": i3["block_threads"],
+                               "slices_per_warp": i3["slices_per_warp"], "tuned": bool(i3["tuned"])},
                      "roofline": hbm_roof(v3, B_SELL32 + B_VEC32, "middle sweep, stored matrix + 4 vector streams"),
                      "dos_l1_vs_oracle": None if orc3 is None else dos_l1(c64, out[0].cpu().numpy(), orc3, DT),
                      "max_abs_dC_vs_oracle": None if orc3 is None else float(np.max(np.abs(out[0].cpu().numpy() - orc3))),

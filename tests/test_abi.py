@@ -113,6 +113,10 @@ def test_rejects_small_rescale_and_bad_args():
     assert l.kpm_dos_jackson(None, None, 4, 4, None, None) == tb.TBPM_ERR_ARG
     assert l.tbpm_get_info(None, None) == tb.TBPM_ERR_ARG
     assert l.tbpm_default_opts(None) == tb.TBPM_ERR_ARG
+    tf = C.c_double()
+    assert l.tbpm_fp64_peak(0, 0, 1, C.byref(tf), None) == tb.TBPM_ERR_ARG
+    assert l.tbpm_fp64_peak(0, 100, 0, C.byref(tf), None) == tb.TBPM_ERR_ARG
+    assert l.tbpm_fp64_peak(0, 100, 1, None, None) == tb.TBPM_ERR_ARG
     l.tbpm_destroy(None)
 
 

@@ -264,6 +264,28 @@ def test_stencil_rejects_stored_matrix_shapes():
         assert e.value.status == tb.TBPM_ERR_UNSUPPORTED
 
 
+def test_fp64_peak_probe():
+    """The FP64 probe: its rate lies within a factor of two of the unit count
+    (2 FP64 lanes per clock per SM, 152 SMs, about 2 GHz on GB300) and above the
+    rate a middle sweep reaches, which it bounds."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tf, ms = tb.tbpm_fp64_peak(0, 2000, 1)
+    unit = 2 * sms * 2.0e9 * 2 / 1e12
+    assert 0.5 * unit < tf < 2.0 * unit and ms > 0
+    h = ti.graphene_csr(512, 512, onsite=ti.anderson_onsite(2 * 512 * 512, 1.0, 1))
+    ctx = create(h, flags=tb.TBPM_F_NO_CLUSTER)
+    psi0 = ti.random_phase_state(h.n, 0)
+    tb.tbpm_dos_corr(ctx, psi0, DT, 16)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    tb.tbpm_dos_corr(ctx, psi0, DT, 64)
+    b.record()
+    torch.cuda.synchronize()
+    sweep_tf = 2.0 * h.n * 64 * 178 / (a.elapsed_time(b) / 1e3) / 1e12     # 178 FP64 operations per row and step
+    assert sweep_tf < tf
+
+
 def test_dos_transforms(orc):
     h = ti.graphene_csr(16, 16, onsite=ti.anderson_onsite(512, 1.0, 1))
     psi0 = ti.random_phase_state(h.n, 0)
