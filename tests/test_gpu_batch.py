@@ -79,13 +79,17 @@ def test_batch_mixed_term_counts(orc):
     assert tb.tbpm_get_info(ctx)["num_terms"] == max(orc.cheb_num_terms(d * r) for d, r in zip(dts, rs))
 
 
-def test_batch_fp32_renorm(orc):
+@pytest.mark.parametrize("bt,spw", [(512, 1), (256, 2)])
+def test_batch_fp32_renorm(orc, bt, spw):
+    """FP32 batch with and without renormalisation (the final sweep's norm
+    partials per instance run), at the default and a two-slice shape."""
     insts = ti.batch_instances(count=5, scale_n=0.003)
     psi = concat_states(insts, 10)
     dts = [math.pi / i.rescale for i in insts]
     for flags in (0, tb.TBPM_F_RENORM):
         ctx = tb.tbpm_create_batch([(i.csr, i.rescale) for i in insts],
-                                   tb.make_opts(precision=tb.TBPM_FP32, flags=flags))
+                                   tb.make_opts(precision=tb.TBPM_FP32, flags=flags, block_threads=bt,
+                                                slices_per_warp=spw))
         c = tb.tbpm_batch_dos_corr(ctx, psi, dts, 128)
         for g, (i, p) in enumerate(zip(insts, split(psi, insts))):
             ref = orc.dos_corr(i.csr, i.rescale, p, dts[g], 128)
