@@ -454,6 +454,8 @@ def alu_roof(units_per_s, fp64_ops_per_unit):
 # three stored hoppings (int32 column + FP32 value), FP32 diagonal, slice
 # offset; four vector streams (gathered operand, psi, b_{k+2}, output) of 8 B
 B_SELL32 = 3 * (4 + 4) + 4 + 0.25
+# the same entries packed: 16-bit column offset + 8-bit value index per entry
+B_SELL32_PACKED = 3 * (2 + 1) + 4 + 0.25
 B_VEC32 = 4 * 8
 # the blocked stencil over one time step of 17 sweeps, without halo re-reads:
 # first block psi + on-site in (12 B), two b out (16 B); middle block psi,
@@ -572,7 +574,8 @@ def run_variants(args, dev, stream):
         "reference": "oracle C(t), 1024 steps (tests/golden/oracle_graphene2048_dos1024_s0.txt)"}
     out = torch.empty((1, 1025), dtype=torch.complex128, device=dev)
     for name, flags in (("fp32_sell_2048x2048", 0), ("fp32_sell_renorm_2048x2048", tb.TBPM_F_RENORM),
-                        ("fp32_sell_autotuned_2048x2048", tb.TBPM_F_AUTOTUNE)):
+                        ("fp32_sell_autotuned_2048x2048", tb.TBPM_F_AUTOTUNE),
+                        ("fp32_sell_plain_2048x2048", tb.TBPM_F_PLAIN_SELL)):
         ctx = tb.tbpm_create(n3, h3.row_ptr, h3.col, h3.val, RESCALE,
                              tb.make_opts(precision=tb.TBPM_FP32, flags=flags, stream=so))
         ms = timed_calls(lambda: tb.tbpm_dos_corr(ctx, psi, DT, 1024, out=out), 1, stream)
@@ -583,7 +586,11 @@ def run_variants(args, dev, stream):
                      "states": 1, "n_steps": 1024,
                      "shape": {"grid_blocks": i3["grid_blocks"], "block_threads": i3["block_threads"],
                                "slices_per_warp": i3["slices_per_warp"], "tuned": bool(i3["tuned"])},
-                     "roofline": hbm_roof(v3, B_SELL32 + B_VEC32, "middle sweep, stored matrix + 4 vector streams"),
+                     "packed": bool(i3["packed"]),
+                     "roofline": (hbm_roof(v3, B_SELL32_PACKED + B_VEC32,
+                                           "middle sweep, packed stored matrix + 4 vector streams")
+                                  if i3["packed"] else
+                                  hbm_roof(v3, B_SELL32 + B_VEC32, "middle sweep, stored matrix + 4 vector streams")),
                      "dos_l1_vs_oracle": None if orc3 is None else dos_l1(c64, out[0].cpu().numpy(), orc3, DT),
                      "max_abs_dC_vs_oracle": None if orc3 is None else float(np.max(np.abs(out[0].cpu().numpy() - orc3))),
                      "dos_l1_reference": "the oracle's FP64 C(t) over the same 1024 steps "

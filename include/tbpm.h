@@ -91,6 +91,16 @@ extern "C" {
                                           last blocks run and wait in hardware for
                                           that sweep to complete before touching
                                           any vector; results are identical      */
+#define TBPM_F_PLAIN_SELL         0x80u /* FP32 stored matrices with real values
+                                          are by default also kept packed, when
+                                          every entry's column lies within 32767
+                                          rows of its own (modulo the padded row
+                                          count) and at most 256 distinct values
+                                          occur: a 16-bit column offset and an
+                                          8-bit value index per entry (3 B instead
+                                          of 8), which the single-state sweeps and
+                                          KPM passes read; this flag keeps only the
+                                          plain form. Results are identical      */
 
 typedef struct tbpm_opts {
     int precision;       /* TBPM_FP64 | TBPM_FP32                                  */
@@ -101,11 +111,13 @@ typedef struct tbpm_opts {
                             default stream of the device                           */
     double bessel_tol;   /* Chebyshev cutoff |J_k| < tol; 0 selects 1e-12          */
     int block_threads;   /* launch shape of the single-state sweeps: threads per
-                            block, 128 | 256 | 512 | 1024; 0 selects 512. 1024 and
+                            block, 128 | 256 | 512 | 1024; 0 selects 512 (128 for
+                            a packed stored matrix, see TBPM_F_PLAIN_SELL). 1024 and
                             slices_per_warp > 1 are built for the stored-matrix
                             path only (TBPM_ERR_UNSUPPORTED on a stencil)         */
     int slices_per_warp; /* 32-row slices a warp works on at once: 1 | 2 | 4 (2
-                            and 4 with at most 512 threads); 0 selects 1. The
+                            and 4 with at most 512 threads); 0 selects 1 (4 for
+                            a packed stored matrix). The
                             grid is whole waves of the shape's occupancy.
                             TBPM_F_AUTOTUNE replaces both with the tuned shape    */
 } tbpm_opts;
@@ -400,8 +412,10 @@ typedef struct tbpm_info {
     int slices_per_warp;       /* 32-row slices a warp works on at once         */
     int tune_candidates;       /* launch shapes the autotuner timed (0: none)   */
     double tune_default_us;    /* autotuner: us per sweep (average over a time
-                                  step) at the default shape                    */
+                                  step) at the context's shape before tuning    */
     double tune_best_us;       /* autotuner: the same at the chosen shape       */
+    int packed;                /* 1 when the stored matrix is also kept packed
+                                  (TBPM_F_PLAIN_SELL)                            */
 } tbpm_info;
 
 /* Fills *info with the context's layout and the counters of its last call. */

@@ -14,6 +14,6 @@ from .tbpm import (  # noqa: F401
     TBPM_OK, TBPM_ERR_ARG, TBPM_ERR_CSR, TBPM_ERR_NOT_HERMITIAN, TBPM_ERR_RESCALE,
     TBPM_ERR_OOM, TBPM_ERR_CUDA, TBPM_ERR_TIMEOUT, TBPM_ERR_NO_DEVICE, TBPM_ERR_UNSUPPORTED,
     TBPM_FP64, TBPM_FP32, TBPM_PATH_AUTO, TBPM_PATH_SELL, TBPM_PATH_STENCIL,
-    TBPM_F_NO_HERMITIAN_CHECK, TBPM_F_FORCE_RESCALE, TBPM_F_RENORM, TBPM_F_NO_CLUSTER, TBPM_F_AUTOTUNE, TBPM_F_NO_TBLOCK, TBPM_F_NO_PDL,
+    TBPM_F_NO_HERMITIAN_CHECK, TBPM_F_FORCE_RESCALE, TBPM_F_RENORM, TBPM_F_NO_CLUSTER, TBPM_F_AUTOTUNE, TBPM_F_NO_TBLOCK, TBPM_F_NO_PDL, TBPM_F_PLAIN_SELL,
     TBPM_LATTICE_GRAPHENE, TBPM_LATTICE_AB_BILAYER,
 )

@@ -35,7 +35,7 @@ namespace {
 // <y|x> = <psi0|T_{m+1}(H~) T_m(H~)|psi0> is real for Hermitian H (a real
 // polynomial of H~ between the same state), so its imaginary part is stored
 // as zero instead of costing two more FP64 operations per row.
-template <typename R, int OP, bool REALV, bool FIRST>
+template <typename R, int OP, int VM, bool FIRST>
 __global__ void __launch_bounds__(kBlockB1, sizeof(R) == 4 ? 3 : 2) kpm_b1(KpmParams p)
 {
     typedef typename V2<R>::T V;
@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(kBlockB1, sizeof(R) == 4 ? 3 : 2) kpm_b1(KpmPa
     SweepParams sp;                     // operator fields for the shared helpers
     sp.n = p.n; sp.nslices = p.nslices; sp.slice_off = p.slice_off; sp.cols = p.cols; sp.vals = p.vals;
     sp.diag = p.diag; sp.l1 = p.l1; sp.l2 = p.l2; sp.t = p.t; sp.t_perp = p.t_perp;
+    sp.cdelta = p.cdelta; sp.vidx = p.vidx; sp.vtab = p.vtab; sp.npad = p.npad;
     const V *__restrict__ x = reinterpret_cast<const V *>(p.x);
     V *y = reinterpret_cast<V *>(p.y);
     const R *diag = reinterpret_cast<const R *>(p.diag);
@@ -60,13 +61,13 @@ __global__ void __launch_bounds__(kBlockB1, sizeof(R) == 4 ? 3 : 2) kpm_b1(KpmPa
         V out;
         if (FIRST) {
             ar = d * xi.x; ai = d * xi.y;
-            if (OP == OP_SELL) sell_apply<R, REALV>(sp, s, lane, x, ar, ai);
+            if (OP == OP_SELL) sell_apply<R, VM>(sp, s, lane, x, ar, ai);
             else if (row < p.n) stencil_apply<R, OP>(sp, row, x, ar, ai);
             out.x = sc * ar; out.y = sc * ai;
         } else {
             const V zz = y[row];
             ar = fma(d, xi.x, -zz.x); ai = fma(d, xi.y, -zz.y);
-            if (OP == OP_SELL) sell_apply<R, REALV>(sp, s, lane, x, ar, ai);
+            if (OP == OP_SELL) sell_apply<R, VM>(sp, s, lane, x, ar, ai);
             else if (row < p.n) stencil_apply<R, OP>(sp, row, x, ar, ai);
             out.x = ar; out.y = ai;
         }
@@ -102,11 +103,11 @@ __global__ void __launch_bounds__(kBlockB1, sizeof(R) == 4 ? 3 : 2) kpm_b1(KpmPa
     }
 }
 
-template <typename R, int OP, bool REALV>
+template <typename R, int OP, int VM>
 cudaError_t kpm_dispatch(const KpmParams &p, int grid, bool pdl, cudaStream_t s)
 {
-    return p.first ? launch_pdl(kpm_b1<R, OP, REALV, true>, grid, kBlockB1, pdl, s, p)
-                   : launch_pdl(kpm_b1<R, OP, REALV, false>, grid, kBlockB1, pdl, s, p);
+    return p.first ? launch_pdl(kpm_b1<R, OP, VM, true>, grid, kBlockB1, pdl, s, p)
+                   : launch_pdl(kpm_b1<R, OP, VM, false>, grid, kBlockB1, pdl, s, p);
 }
 
 }  // namespace
@@ -177,8 +178,9 @@ cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cuda
         return kpm_dispatch<double, OP_STENCIL_BI, true>(p, grid, v.pdl, s);
     }
     if (v.op == OP_SELL)
-        return v.real_values ? kpm_dispatch<float, OP_SELL, true>(p, grid, v.pdl, s)
-                             : kpm_dispatch<float, OP_SELL, false>(p, grid, v.pdl, s);
+        return v.packed ? kpm_dispatch<float, OP_SELL, VM_PACKED>(p, grid, v.pdl, s)
+               : v.real_values ? kpm_dispatch<float, OP_SELL, true>(p, grid, v.pdl, s)
+                               : kpm_dispatch<float, OP_SELL, false>(p, grid, v.pdl, s);
     if (v.op == OP_STENCIL_MONO) return kpm_dispatch<float, OP_STENCIL_MONO, true>(p, grid, v.pdl, s);
     return kpm_dispatch<float, OP_STENCIL_BI, true>(p, grid, v.pdl, s);
 }

@@ -43,19 +43,18 @@ __device__ __forceinline__ void sweep_coeffs(const SweepParams &p, int inst, R &
 // G slices of uniform SELL width N: every column and value load of the G rows
 // is issued first, then every gather, then the FMAs of each row in entry
 // order (the same order as sell_apply, so results do not depend on G).
-template <typename R, bool REALV, int N, int G>
-__device__ __forceinline__ void sell_group(const SweepParams &p, const int64_t (&off)[G], int lane,
+template <typename R, int VM, int N, int G>
+__device__ __forceinline__ void sell_group(const SweepParams &p, const int64_t (&off)[G], int64_t s0, int lane,
                                            const typename V2<R>::T *__restrict__ x, R (&ar)[G], R (&ai)[G])
 {
     typedef typename V2<R>::T V;
-    SellEntry<R, REALV> e[G][N];
+    SellEntry<R, VM> e[G][N];
 #pragma unroll
     for (int q = 0; q < G; ++q) {
-        const int32_t *cp = p.cols + off[q] + lane;
-        const void *vp = REALV ? (const void *)(reinterpret_cast<const R *>(p.vals) + off[q] + lane)
-                               : (const void *)(reinterpret_cast<const V *>(p.vals) + off[q] + lane);
+        SellRow<R, VM> rr;
+        rr.init(p, off[q], lane, ((s0 + q) << 5) + lane);
 #pragma unroll
-        for (int j = 0; j < N; ++j) e[q][j].load(cp, vp, 32 * (int64_t)j);
+        for (int j = 0; j < N; ++j) rr.load(e[q][j], j);
     }
     V xv[G][N];
 #pragma unroll
@@ -85,7 +84,7 @@ __device__ __forceinline__ void sell_group(const SweepParams &p, const int64_t (
 // others), one butterfly per run instead of one per slice.
 // Each row's arithmetic is the same for every shape; only the grouping of the
 // dot partials follows the grid.
-template <typename R, int OP, bool REALV, int BM, bool AIMAG, bool HASZ, bool FINAL, bool MULTI, int SPW, int LB>
+template <typename R, int OP, int VM, int BM, bool AIMAG, bool HASZ, bool FINAL, bool MULTI, int SPW, int LB>
 __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
 {
     typedef typename V2<R>::T V;
@@ -184,7 +183,7 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
         R ar, ai;
         if (BM == B_ONE) { ar = fma(d, xi.x, tr); ai = fma(d, xi.y, ti); }
         else { ar = d * xi.x; ai = d * xi.y; }
-        if (OP == OP_SELL) sell_apply<R, REALV>(p, s, lane, x, ar, ai);
+        if (OP == OP_SELL) sell_apply<R, VM>(p, s, lane, x, ar, ai);
         else if (row < p.n) stencil_apply<R, OP>(p, row, x, ar, ai);
         finish(s, row, cur_inst, ar, ai, tr, ti);
     };
@@ -246,8 +245,8 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
             if (BM == B_ONE) { ar[q] = fma(d[q], xi[q].x, tr[q]); ai[q] = fma(d[q], xi[q].y, ti[q]); }
             else { ar[q] = d[q] * xi[q].x; ai[q] = d[q] * xi[q].y; }
         }
-        if (w0 == 3) sell_group<R, REALV, 3, SPW>(p, off, lane, x, ar, ai);
-        else sell_group<R, REALV, 4, SPW>(p, off, lane, x, ar, ai);
+        if (w0 == 3) sell_group<R, VM, 3, SPW>(p, off, s0, lane, x, ar, ai);
+        else sell_group<R, VM, 4, SPW>(p, off, s0, lane, x, ar, ai);
 #pragma unroll
         for (int q = 0; q < SPW; ++q) {
             a = aq[q];
@@ -283,34 +282,34 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
 
 // Launches one sweep kind of one operator variant at shape (SPW, LB) with
 // `block` threads per block (block <= LB, a multiple of 32).
-template <typename R, int OP, bool REALV, bool MULTI, int SPW, int LB>
+template <typename R, int OP, int VM, bool MULTI, int SPW, int LB>
 cudaError_t sweep_dispatch(SweepKind kind, bool a_imag, bool has_z, const SweepParams &p,
                            int grid, int block, bool pdl, cudaStream_t s)
 {
     switch (kind) {
     case SW_FIRST:
-        return a_imag ? launch_pdl(sweep_b1<R, OP, REALV, B_REAL, true, false, false, MULTI, SPW, LB>, grid, block, pdl, s, p)
-                      : launch_pdl(sweep_b1<R, OP, REALV, B_IMAG, false, false, false, MULTI, SPW, LB>, grid, block, pdl, s, p);
+        return a_imag ? launch_pdl(sweep_b1<R, OP, VM, B_REAL, true, false, false, MULTI, SPW, LB>, grid, block, pdl, s, p)
+                      : launch_pdl(sweep_b1<R, OP, VM, B_IMAG, false, false, false, MULTI, SPW, LB>, grid, block, pdl, s, p);
     case SW_SECOND:
-        return a_imag ? launch_pdl(sweep_b1<R, OP, REALV, B_ONE, true, false, false, MULTI, SPW, LB>, grid, block, pdl, s, p)
-                      : launch_pdl(sweep_b1<R, OP, REALV, B_ONE, false, false, false, MULTI, SPW, LB>, grid, block, pdl, s, p);
+        return a_imag ? launch_pdl(sweep_b1<R, OP, VM, B_ONE, true, false, false, MULTI, SPW, LB>, grid, block, pdl, s, p)
+                      : launch_pdl(sweep_b1<R, OP, VM, B_ONE, false, false, false, MULTI, SPW, LB>, grid, block, pdl, s, p);
     case SW_MID:
-        return a_imag ? launch_pdl(sweep_b1<R, OP, REALV, B_ONE, true, true, false, MULTI, SPW, LB>, grid, block, pdl, s, p)
-                      : launch_pdl(sweep_b1<R, OP, REALV, B_ONE, false, true, false, MULTI, SPW, LB>, grid, block, pdl, s, p);
+        return a_imag ? launch_pdl(sweep_b1<R, OP, VM, B_ONE, true, true, false, MULTI, SPW, LB>, grid, block, pdl, s, p)
+                      : launch_pdl(sweep_b1<R, OP, VM, B_ONE, false, true, false, MULTI, SPW, LB>, grid, block, pdl, s, p);
     case SW_FINAL:
-        return has_z ? launch_pdl(sweep_b1<R, OP, REALV, B_REAL, false, true, true, MULTI, SPW, LB>, grid, block, pdl, s, p)
-                     : launch_pdl(sweep_b1<R, OP, REALV, B_REAL, false, false, true, MULTI, SPW, LB>, grid, block, pdl, s, p);
+        return has_z ? launch_pdl(sweep_b1<R, OP, VM, B_REAL, false, true, true, MULTI, SPW, LB>, grid, block, pdl, s, p)
+                     : launch_pdl(sweep_b1<R, OP, VM, B_REAL, false, false, true, MULTI, SPW, LB>, grid, block, pdl, s, p);
     }
     return cudaErrorInvalidValue;
 }
 
 // Resident blocks per SM of the middle sweep at this shape.
-template <typename R, int OP, bool REALV, bool MULTI, int SPW, int LB>
+template <typename R, int OP, int VM, bool MULTI, int SPW, int LB>
 int sweep_occupancy_of(int block)
 {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, sweep_b1<R, OP, REALV, B_ONE, false, true, false, MULTI, SPW, LB>, block, 0) != cudaSuccess)
+            &per_sm, sweep_b1<R, OP, VM, B_ONE, false, true, false, MULTI, SPW, LB>, block, 0) != cudaSuccess)
         return 0;
     return per_sm;
 }
@@ -333,6 +332,8 @@ cudaError_t sell_shape_launch(const SweepVariant &v, SweepKind kind, bool a_imag
     if (multi)
         return v.real_values ? sweep_dispatch<float, OP_SELL, true, true, SPW, LB>(kind, a_imag, has_z, p, grid, v.block, v.pdl, s)
                              : sweep_dispatch<float, OP_SELL, false, true, SPW, LB>(kind, a_imag, has_z, p, grid, v.block, v.pdl, s);
+    if (v.packed)           // the packed form: FP32 real values of a single instance
+        return sweep_dispatch<float, OP_SELL, VM_PACKED, false, SPW, LB>(kind, a_imag, has_z, p, grid, v.block, v.pdl, s);
     return v.real_values ? sweep_dispatch<float, OP_SELL, true, false, SPW, LB>(kind, a_imag, has_z, p, grid, v.block, v.pdl, s)
                          : sweep_dispatch<float, OP_SELL, false, false, SPW, LB>(kind, a_imag, has_z, p, grid, v.block, v.pdl, s);
 }
@@ -350,6 +351,7 @@ int sell_shape_occupancy(const SweepVariant &v, bool multi)
     if (multi)
         return v.real_values ? sweep_occupancy_of<float, OP_SELL, true, true, SPW, LB>(v.block)
                              : sweep_occupancy_of<float, OP_SELL, false, true, SPW, LB>(v.block);
+    if (v.packed) return sweep_occupancy_of<float, OP_SELL, VM_PACKED, false, SPW, LB>(v.block);
     return v.real_values ? sweep_occupancy_of<float, OP_SELL, true, false, SPW, LB>(v.block)
                          : sweep_occupancy_of<float, OP_SELL, false, false, SPW, LB>(v.block);
 }

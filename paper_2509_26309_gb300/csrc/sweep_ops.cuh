@@ -22,19 +22,21 @@ __device__ __forceinline__ T ldm(const T *p)
     return __ldg(p);
 }
 
+// How a SELL operator's entries are stored (the VM template argument):
+// VM_COMPLEX and VM_REAL: int32 columns and complex or real values; VM_PACKED
+// (real values, FP32): for each entry a 16-bit column offset from its row,
+// taken modulo the padded row count, and an 8-bit index into a table of at
+// most 256 distinct values (3 B per entry instead of 8 for lattice-like
+// matrices, whose neighbours sit at a few fixed offsets and whose hoppings take
+// a few values). The entries, and so the products, are the same in every form.
+enum ValueMode { VM_COMPLEX = 0, VM_REAL = 1, VM_PACKED = 2 };
+
 // One stored entry: acc += v x[c] (real v) or v x[c] (complex v).
-template <typename R, bool REALV>
-struct SellEntry;
-template <typename R>
-struct SellEntry<R, true> {
+template <typename R, int VM>
+struct SellEntry {
     typedef typename V2<R>::T V;
     int c;
     R v;
-    __device__ __forceinline__ void load(const int32_t *cp, const void *vp, int64_t e)
-    {
-        c = ldm<R>(cp + e);
-        v = ldm<R>(reinterpret_cast<const R *>(vp) + e);
-    }
     __device__ __forceinline__ void apply(const V &xv, R &ar, R &ai) const
     {
         ar = fma(v, xv.x, ar);
@@ -42,15 +44,10 @@ struct SellEntry<R, true> {
     }
 };
 template <typename R>
-struct SellEntry<R, false> {
+struct SellEntry<R, VM_COMPLEX> {
     typedef typename V2<R>::T V;
     int c;
     V v;
-    __device__ __forceinline__ void load(const int32_t *cp, const void *vp, int64_t e)
-    {
-        c = ldm<R>(cp + e);
-        v = ldm<R>(reinterpret_cast<const V *>(vp) + e);
-    }
     __device__ __forceinline__ void apply(const V &xv, R &ar, R &ai) const
     {
         ar = fma(v.x, xv.x, fma(-v.y, xv.y, ar));
@@ -58,15 +55,58 @@ struct SellEntry<R, false> {
     }
 };
 
+// The entries of one lane's row in a slice starting at entry `off`: entry j at
+// off + 32 j + lane.
+template <typename R, int VM>
+struct SellRow {
+    typedef typename V2<R>::T V;
+    const int32_t *cp;
+    const void *vp;
+    __device__ __forceinline__ void init(const SweepParams &p, int64_t off, int lane, int64_t)
+    {
+        cp = p.cols + off + lane;
+        vp = VM == VM_REAL ? (const void *)(reinterpret_cast<const R *>(p.vals) + off + lane)
+                           : (const void *)(reinterpret_cast<const V *>(p.vals) + off + lane);
+    }
+    __device__ __forceinline__ void load(SellEntry<R, VM> &e, int j) const
+    {
+        e.c = ldm<R>(cp + 32 * (int64_t)j);
+        if constexpr (VM == VM_REAL) e.v = ldm<R>(reinterpret_cast<const R *>(vp) + 32 * (int64_t)j);
+        else e.v = ldm<R>(reinterpret_cast<const V *>(vp) + 32 * (int64_t)j);
+    }
+};
+template <typename R>
+struct SellRow<R, VM_PACKED> {
+    const int16_t *dp;
+    const uint8_t *ip;
+    const R *tab;
+    int row, npad;
+    __device__ __forceinline__ void init(const SweepParams &p, int64_t off, int lane, int64_t r)
+    {
+        dp = p.cdelta + off + lane;
+        ip = p.vidx + off + lane;
+        tab = reinterpret_cast<const R *>(p.vtab);
+        row = (int)r;
+        npad = (int)p.npad;
+    }
+    __device__ __forceinline__ void load(SellEntry<R, VM_PACKED> &e, int j) const
+    {
+        int c = row + (int)ldm<R>(dp + 32 * (int64_t)j);
+        c = c < 0 ? c + npad : c;
+        e.c = c >= npad ? c - npad : c;
+        e.v = __ldg(tab + ldm<R>(ip + 32 * (int64_t)j));
+    }
+};
+
 // N entries j0 .. j0+N-1 of the lane's row: all loads first, then the FMAs.
-template <typename R, bool REALV, int N>
-__device__ __forceinline__ void sell_entries(const int32_t *cp, const void *vp, int j0,
+template <typename R, int VM, int N>
+__device__ __forceinline__ void sell_entries(const SellRow<R, VM> &rr, int j0,
                                              const typename V2<R>::T *__restrict__ x, R &ar, R &ai)
 {
     typedef typename V2<R>::T V;
-    SellEntry<R, REALV> e[N];
+    SellEntry<R, VM> e[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) e[q].load(cp, vp, 32 * (int64_t)(j0 + q));
+    for (int q = 0; q < N; ++q) rr.load(e[q], j0 + q);
     V xv[N];
 #pragma unroll
     for (int q = 0; q < N; ++q) xv[q] = __ldg(x + e[q].c);
@@ -80,25 +120,24 @@ __device__ __forceinline__ void sell_entries(const int32_t *cp, const void *vp, 
 // other widths as groups of 4 and a plain remainder loop. No code path issues
 // instructions for entries past w: a predicated-off FP64 instruction still
 // takes its slot in GB300's narrow FP64 pipe.
-template <typename R, bool REALV>
+template <typename R, int VM>
 __device__ __forceinline__ void sell_apply(const SweepParams &p, int64_t s, int lane,
                                            const typename V2<R>::T *__restrict__ x,
                                            R &ar, R &ai)
 {
     const int64_t off = ldm<R>(p.slice_off + s);
     const int w = (int)((ldm<R>(p.slice_off + s + 1) - off) >> 5);
-    const int32_t *cp = p.cols + off + lane;
-    const void *vp = REALV ? (const void *)(reinterpret_cast<const R *>(p.vals) + off + lane)
-                           : (const void *)(reinterpret_cast<const typename V2<R>::T *>(p.vals) + off + lane);
+    SellRow<R, VM> rr;
+    rr.init(p, off, lane, (s << 5) + lane);
     if (w == 3) {
-        sell_entries<R, REALV, 3>(cp, vp, 0, x, ar, ai);
+        sell_entries<R, VM, 3>(rr, 0, x, ar, ai);
     } else if (w == 4) {
-        sell_entries<R, REALV, 4>(cp, vp, 0, x, ar, ai);
+        sell_entries<R, VM, 4>(rr, 0, x, ar, ai);
     } else {
         int j = 0;
-        for (; j + 4 <= w; j += 4) sell_entries<R, REALV, 4>(cp, vp, j, x, ar, ai);
+        for (; j + 4 <= w; j += 4) sell_entries<R, VM, 4>(rr, j, x, ar, ai);
 #pragma unroll 1
-        for (; j < w; ++j) sell_entries<R, REALV, 1>(cp, vp, j, x, ar, ai);
+        for (; j < w; ++j) sell_entries<R, VM, 1>(rr, j, x, ar, ai);
     }
 }
 

@@ -247,6 +247,42 @@ void to_sell(const HostMatrix &m, int64_t n_pad, const std::vector<double> &row_
     }
 }
 
+// The packed form of FP32 real SELL entries: for entry e of row r, the column
+// offset (cols[e] - r) taken modulo n_pad into [-n_pad/2, n_pad/2), stored in
+// 16 bits, and the index of vals[e] in a table of the distinct values (their
+// bits), at most 256 (padding entries: offset 0, value 0). False, and nothing
+// is kept, when an offset does not fit 16 bits or more than 256 values occur.
+bool pack_sell(const std::vector<int32_t> &cols, const std::vector<float> &vals, const std::vector<int64_t> &off,
+               int64_t n_pad, std::vector<int16_t> &cdelta, std::vector<uint8_t> &vidx, std::vector<float> &vtab)
+{
+    const int64_t nent = off.back();
+    cdelta.assign(nent, 0);
+    vidx.assign(nent, 0);
+    vtab.clear();
+    std::map<uint32_t, int> index;
+    const int64_t nslices = (int64_t)off.size() - 1;
+    for (int64_t sl = 0; sl < nslices; ++sl)
+        for (int64_t e = off[sl]; e < off[sl + 1]; ++e) {
+            const int64_t r = sl * kSlice + (e - off[sl]) % kSlice;
+            int64_t d = ((int64_t)cols[e] - r) % n_pad;
+            if (d >= (n_pad + 1) / 2) d -= n_pad;
+            else if (d < -(n_pad / 2)) d += n_pad;
+            if (d < INT16_MIN || d > INT16_MAX) return false;
+            cdelta[e] = (int16_t)d;
+            uint32_t bits;
+            std::memcpy(&bits, &vals[e], sizeof(bits));
+            auto it = index.find(bits);
+            if (it == index.end()) {
+                if (vtab.size() == 256) return false;
+                it = index.emplace(bits, (int)vtab.size()).first;
+                vtab.push_back(vals[e]);
+            }
+            vidx[e] = (uint8_t)it->second;
+        }
+    vtab.resize(256, 0.0f);
+    return true;
+}
+
 template <typename T>
 int upload(tbpm_ctx *ctx, void **dst, const std::vector<T> &src)
 {
@@ -259,6 +295,7 @@ int upload(tbpm_ctx *ctx, void **dst, const std::vector<T> &src)
 // Stores A = 2 H / rescale (per row: 2 / rescale of the row's instance).
 int setup_sell(tbpm_ctx *ctx, const HostMatrix &m, const std::vector<double> *row_scale = nullptr)
 {
+    const bool row_scale_given = row_scale != nullptr;          // a batch of instances
     std::vector<double> uniform;
     if (!row_scale) {
         uniform.assign(m.n, 2.0 / ctx->rescale);
@@ -279,6 +316,17 @@ int setup_sell(tbpm_ctx *ctx, const HostMatrix &m, const std::vector<double> *ro
         to_sell<float>(m, ctx->n_pad, s, m.real_values, off, cols, vals, diag, ctx->sell.max_width);
         if ((rc = upload(ctx, (void **)&ctx->sell.vals, vals))) return rc;
         if ((rc = upload(ctx, (void **)&ctx->sell.diag, diag))) return rc;
+        // the packed form, for a single instance with real values
+        std::vector<int16_t> cdelta;
+        std::vector<uint8_t> vidx;
+        std::vector<float> vtab;
+        if (!row_scale_given && m.real_values && !(ctx->flags & TBPM_F_PLAIN_SELL) &&
+            pack_sell(cols, vals, off, ctx->n_pad, cdelta, vidx, vtab)) {
+            if ((rc = upload(ctx, (void **)&ctx->sell.cdelta, cdelta))) return rc;
+            if ((rc = upload(ctx, (void **)&ctx->sell.vidx, vidx))) return rc;
+            if ((rc = upload(ctx, (void **)&ctx->sell.vtab, vtab))) return rc;
+            ctx->sell.packed = true;
+        }
     }
     ctx->sell.nslices = ctx->n_pad / kSlice;
     ctx->sell.nent = off.back();
@@ -295,6 +343,7 @@ SweepVariant variant(const tbpm_ctx *ctx, int states)
     v.precision = ctx->precision;
     v.op = ctx->op;
     v.real_values = ctx->op == OP_SELL ? ctx->sell.real_values : true;
+    v.packed = ctx->op == OP_SELL && ctx->sell.packed && ctx->precision == TBPM_FP32 && ctx->ninst == 0;
     v.states = states;
     v.pdl = !(ctx->flags & TBPM_F_NO_PDL);
     v.block = ctx->sw_block;
@@ -316,6 +365,10 @@ void fill_operator(const tbpm_ctx *ctx, SweepParams &p)
         p.cols = ctx->sell.cols;
         p.vals = ctx->sell.vals;
         p.diag = ctx->sell.diag;
+        p.cdelta = ctx->sell.cdelta;
+        p.vidx = ctx->sell.vidx;
+        p.vtab = ctx->sell.vtab;
+        p.npad = ctx->n_pad;
     } else {
         p.diag = ctx->sten.onsite;
         p.l1 = ctx->sten.l1;
@@ -490,6 +543,7 @@ int enqueue_kpm_chunk(tbpm_ctx *ctx, int len, cudaStream_t s, int64_t *launches)
     memset(&p, 0, sizeof(p));
     p.n = op.n; p.nslices = op.nslices; p.slice_off = op.slice_off; p.cols = op.cols;
     p.vals = op.vals; p.diag = op.diag; p.l1 = op.l1; p.l2 = op.l2; p.t = op.t; p.t_perp = op.t_perp;
+    p.cdelta = op.cdelta; p.vidx = op.vidx; p.vtab = op.vtab; p.npad = op.npad;
     p.partials = ctx->d_partials;
     p.nblk = ctx->nblk_kpm;
     p.scale = 1.0;
@@ -890,27 +944,34 @@ static int check_opts(const tbpm_opts *in, tbpm_opts *o)
     if (o->precision != TBPM_FP64 && o->precision != TBPM_FP32) return TBPM_ERR_ARG;
     if (o->path < TBPM_PATH_AUTO || o->path > TBPM_PATH_STENCIL) return TBPM_ERR_ARG;
     if (o->flags & ~(unsigned)(TBPM_F_NO_HERMITIAN_CHECK | TBPM_F_FORCE_RESCALE | TBPM_F_RENORM |
-                               TBPM_F_NO_CLUSTER | TBPM_F_AUTOTUNE | TBPM_F_NO_TBLOCK | TBPM_F_NO_PDL))
+                               TBPM_F_NO_CLUSTER | TBPM_F_AUTOTUNE | TBPM_F_NO_TBLOCK | TBPM_F_NO_PDL |
+                               TBPM_F_PLAIN_SELL))
         return TBPM_ERR_ARG;
     if (o->bessel_tol == 0.0) o->bessel_tol = 1e-12;
     if (!(o->bessel_tol > 0.0 && o->bessel_tol < 1e-2)) return TBPM_ERR_ARG;
-    if (o->block_threads == 0) o->block_threads = kBlockB1;
-    if (o->slices_per_warp == 0) o->slices_per_warp = 1;
-    if (o->block_threads != 128 && o->block_threads != 256 && o->block_threads != 512 && o->block_threads != 1024)
+    // 0 leaves the shape to the operator (apply_shape)
+    if (o->block_threads != 0 && o->block_threads != 128 && o->block_threads != 256 && o->block_threads != 512 &&
+        o->block_threads != 1024)
         return TBPM_ERR_ARG;
-    if (o->slices_per_warp != 1 && o->slices_per_warp != 2 && o->slices_per_warp != 4) return TBPM_ERR_ARG;
+    if (o->slices_per_warp != 0 && o->slices_per_warp != 1 && o->slices_per_warp != 2 && o->slices_per_warp != 4)
+        return TBPM_ERR_ARG;
     return TBPM_OK;
 }
 
 // Applies the requested launch shape of the single-state sweeps once the
 // operator is known: TBPM_ERR_UNSUPPORTED if it is not built for this operator;
-// the grid is whole waves of the shape's middle-sweep occupancy.
+// the grid is whole waves of the shape's middle-sweep occupancy. Unset fields
+// (0) take the operator's default: 512 threads and one slice per warp, or, for
+// a packed stored matrix, whose smaller entries leave its sweeps waiting on
+// their dependent loads, 128 threads and four slices per warp (measured on
+// GB300 at 2048^2: 69.6 against 84.3 us per sweep at 512 x 1).
 static int apply_shape(tbpm_ctx *ctx, const tbpm_opts &o)
 {
-    if (o.block_threads == kBlockB1 && o.slices_per_warp == 1) return TBPM_OK;
     SweepVariant v = variant(ctx, 1);
-    v.block = o.block_threads;
-    v.spw = o.slices_per_warp;
+    const bool packed = v.packed;
+    v.block = o.block_threads ? o.block_threads : (packed ? 128 : kBlockB1);
+    v.spw = o.slices_per_warp ? o.slices_per_warp : (packed ? 4 : 1);
+    if (v.block == kBlockB1 && v.spw == 1) return TBPM_OK;
     if (!sweep_shape_built(v)) return TBPM_ERR_UNSUPPORTED;
     const int occ = sweep_shape_occupancy(v, ctx->d_slice_inst != nullptr);
     if (occ < 1) return TBPM_ERR_UNSUPPORTED;
@@ -937,8 +998,8 @@ static int finish_create(tbpm_ctx *ctx, const tbpm_opts &o)
 // iteration (the shapes sweep_shape_built accepts for this operator), and for
 // each the grids of occupancy/2, occupancy and twice the occupancy blocks per
 // SM (all of 1 .. occupancy when that is at most 4). Every candidate is timed
-// over 2 steps after one warm-up step; the four fastest and the default shape
-// (512 threads, one slice, the occupancy grid) are timed again over 6 steps,
+// over 2 steps after one warm-up step; the four fastest and the context's shape
+// before tuning (its default) are timed again over 6 steps,
 // and the fastest of those is kept for the life of the context. The
 // single-instance dot partials are per warp of the chosen grid, which is then
 // fixed, so results stay reproducible from call to call. Runs once, before any
@@ -959,7 +1020,8 @@ static int autotune(tbpm_ctx *ctx)
     };
     std::vector<Cand> cands;
     const SweepVariant base = variant(ctx, 1);
-    const int def_grid = ctx->nblk;
+    // the context's shape before tuning: the default, or the packed default
+    const int def_grid = ctx->nblk, def_block = ctx->sw_block, def_spw = ctx->sw_spw;
     int64_t max_warps = 0;
     for (int block : {128, 256, 512, 1024})
         for (int spw : {1, 2, 4}) {
@@ -981,8 +1043,8 @@ static int autotune(tbpm_ctx *ctx)
             }
         }
     bool have_def = false;
-    for (const Cand &c : cands) have_def |= c.block == kBlockB1 && c.spw == 1 && c.grid == def_grid;
-    if (!have_def) cands.push_back({kBlockB1, 1, def_grid, 0.0});
+    for (const Cand &c : cands) have_def |= c.block == def_block && c.spw == def_spw && c.grid == def_grid;
+    if (!have_def) cands.push_back({def_block, def_spw, def_grid, 0.0});
     // the final sweep's per-warp partials (slot 0) of the widest candidate
     double2 *part = ctx->d_partials;
     double2 *own_part = nullptr;
@@ -1047,8 +1109,8 @@ static int autotune(tbpm_ctx *ctx)
         std::sort(sorted.begin(), sorted.end(), [](const Cand &a, const Cand &b) { return a.us < b.us; });
         for (size_t i = 0; i < sorted.size() && i < 4; ++i) fin.push_back(sorted[i]);
         bool def_in = false;
-        for (const Cand &c : fin) def_in |= c.block == kBlockB1 && c.spw == 1 && c.grid == def_grid;
-        if (!def_in) fin.push_back({kBlockB1, 1, def_grid, 0.0});
+        for (const Cand &c : fin) def_in |= c.block == def_block && c.spw == def_spw && c.grid == def_grid;
+        if (!def_in) fin.push_back({def_block, def_spw, def_grid, 0.0});
         for (size_t i = 0; i < fin.size() && !rc; ++i) rc = time_us(fin[i], 6, &fin[i].us);
     }
     if (e0) cudaEventDestroy(e0);
@@ -1062,7 +1124,7 @@ static int autotune(tbpm_ctx *ctx)
     double def_us = 0.0;
     for (const Cand &c : fin) {
         if (c.us < best.us) best = c;
-        if (c.block == kBlockB1 && c.spw == 1 && c.grid == def_grid) def_us = c.us;
+        if (c.block == def_block && c.spw == def_spw && c.grid == def_grid) def_us = c.us;
     }
     // work buffers and graphs depend on the shape: rebuild them for the new one
     destroy_graphs(ctx);
@@ -1201,6 +1263,7 @@ void tbpm_destroy(tbpm_ctx *ctx)
     destroy_graphs(ctx);
     cudaFree(ctx->sell.slice_off); cudaFree(ctx->sell.cols); cudaFree(ctx->sell.vals);
     cudaFree(ctx->sell.diag); cudaFree(ctx->sten.onsite);
+    cudaFree(ctx->sell.cdelta); cudaFree(ctx->sell.vidx); cudaFree(ctx->sell.vtab);
     cudaFree(ctx->d_coef); cudaFree(ctx->d_K); cudaFree(ctx->d_counter);
     cudaFree(ctx->d_psi); cudaFree(ctx->d_b0); cudaFree(ctx->d_b1); cudaFree(ctx->d_psi0);
     cudaFree(ctx->d_partials); cudaFree(ctx->d_out); cudaFree(ctx->d_stage); cudaFree(ctx->d_misc);
@@ -1417,6 +1480,7 @@ int kpm_moments(tbpm_ctx *ctx, const double *psi0, int nstates, int M, double *m
         memset(&p, 0, sizeof(p));
         p.n = op.n; p.nslices = op.nslices; p.slice_off = op.slice_off; p.cols = op.cols;
         p.vals = op.vals; p.diag = op.diag; p.l1 = op.l1; p.l2 = op.l2; p.t = op.t; p.t_perp = op.t_perp;
+        p.cdelta = op.cdelta; p.vidx = op.vidx; p.vtab = op.vtab; p.npad = op.npad;
         p.x = ctx->d_psi; p.y = ctx->d_b0; p.scale = 0.5; p.first = true;
         p.partials = ctx->d_partials; p.delta = 0; p.nblk = ctx->nblk_kpm;
         CU(launch_kpm(v, p, ctx->nblk_kpm, ctx->stream));
@@ -2074,6 +2138,7 @@ int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info)
     info->tune_candidates = ctx->tune_candidates;
     info->tune_default_us = ctx->tune_default_us;
     info->tune_best_us = ctx->tune_best_us;
+    info->packed = ctx->op == OP_SELL && ctx->sell.packed ? 1 : 0;
     return TBPM_OK;
 }
 

@@ -75,6 +75,13 @@ struct Sell {
     void *diag = nullptr;         // R[n_pad]
     bool real_values = true;
     int max_width = 0;
+    // the packed form of the same entries (FP32, real values, when every
+    // column offset fits 16 bits modulo n_pad and at most 256 values occur):
+    // entry e is column (row + cdelta[e]) mod n_pad, value vtab[vidx[e]]
+    bool packed = false;
+    int16_t *cdelta = nullptr;    // int16[nent]
+    uint8_t *vidx = nullptr;      // uint8[nent]
+    void *vtab = nullptr;         // R[256]
 };
 
 // Periodic graphene / AB-bilayer stencil (matrix-free H v).
@@ -94,6 +101,10 @@ struct SweepParams {
     const int32_t *cols;
     const void *vals;
     const void *diag;
+    const int16_t *cdelta;        // the packed form (VM_PACKED kernels): column offsets,
+    const uint8_t *vidx;          // value indices and the value table, offsets taken
+    const void *vtab;             // modulo npad
+    int64_t npad;
     int64_t l1, l2;               // stencil geometry
     double t, t_perp;
     // vectors (all padded to n_pad rows, B states interleaved per row)
@@ -173,6 +184,10 @@ struct KpmParams {
     const int32_t *cols;
     const void *vals;
     const void *diag;
+    const int16_t *cdelta;        // the packed form, as in SweepParams
+    const uint8_t *vidx;
+    const void *vtab;
+    int64_t npad;
     int64_t l1, l2;
     double t, t_perp;
     const void *x;                // T_m
@@ -191,6 +206,7 @@ struct SweepVariant {
     int precision;                // TBPM_FP64 | TBPM_FP32
     int op;                       // OpKind
     bool real_values;
+    bool packed = false;          // the operator's packed form is used (FP32 SELL, real values)
     int states;                   // B: 1 or 16
     bool pdl;                     // B = 1 sweeps as programmatic dependent launches
     int block = kBlockB1;         // B = 1 sweeps: threads per block (32 .. 1024)

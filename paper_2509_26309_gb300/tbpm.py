@@ -39,6 +39,7 @@ TBPM_F_NO_CLUSTER = 0x8
 TBPM_F_AUTOTUNE = 0x10
 TBPM_F_NO_TBLOCK = 0x20
 TBPM_F_NO_PDL = 0x40
+TBPM_F_PLAIN_SELL = 0x80
 TBPM_LATTICE_GRAPHENE = 0
 TBPM_LATTICE_AB_BILAYER = 1
 
@@ -60,7 +61,7 @@ class tbpm_info(C.Structure):
                 ("kernel_launches", C.c_int64), ("gershgorin", C.c_double), ("rescale", C.c_double),
                 ("grid_blocks", C.c_int), ("tuned", C.c_int), ("fermi_terms", C.c_int),
                 ("block_threads", C.c_int), ("slices_per_warp", C.c_int), ("tune_candidates", C.c_int),
-                ("tune_default_us", C.c_double), ("tune_best_us", C.c_double)]
+                ("tune_default_us", C.c_double), ("tune_best_us", C.c_double), ("packed", C.c_int)]
 
 
 class TbpmError(RuntimeError):

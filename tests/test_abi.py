@@ -91,10 +91,10 @@ def test_rejects_small_rescale_and_bad_args():
     assert _create(h, rescale=float("nan")) == tb.TBPM_ERR_ARG
     assert _create(h, opts=tb.make_opts(precision=7)) == tb.TBPM_ERR_ARG
     assert _create(h, opts=tb.make_opts(path=tb.TBPM_PATH_STENCIL)) == tb.TBPM_ERR_ARG
-    assert _create(h, opts=tb.make_opts(flags=0x100)) == tb.TBPM_ERR_ARG
-    assert _create(h, opts=tb.make_opts(flags=0x80)) == tb.TBPM_ERR_ARG     # the first undefined bit
+    assert _create(h, opts=tb.make_opts(flags=0x200)) == tb.TBPM_ERR_ARG
+    assert _create(h, opts=tb.make_opts(flags=0x100)) == tb.TBPM_ERR_ARG    # the first undefined bit
     every = (tb.TBPM_F_NO_HERMITIAN_CHECK | tb.TBPM_F_FORCE_RESCALE | tb.TBPM_F_RENORM | tb.TBPM_F_NO_CLUSTER
-             | tb.TBPM_F_AUTOTUNE | tb.TBPM_F_NO_TBLOCK | tb.TBPM_F_NO_PDL)
+             | tb.TBPM_F_AUTOTUNE | tb.TBPM_F_NO_TBLOCK | tb.TBPM_F_NO_PDL | tb.TBPM_F_PLAIN_SELL)
     assert _create(h, opts=tb.make_opts(flags=every)) != tb.TBPM_ERR_ARG
     val = h.val.copy(); val[2] = np.nan
     assert _create(h, val=val) == tb.TBPM_ERR_ARG

@@ -148,3 +148,59 @@ def test_fp32_16_states_4096_full_size(orc, golden):
         for c in (c_st[j], c_sell[j]):
             assert np.max(np.abs(c - ref)) <= C_TOL
             assert dos_l1(orc, c, ref, DT) <= 1e-4
+
+
+@pytest.mark.parametrize("case", ["graphene", "bilayer", "graphene_wide"])
+def test_packed_sell_matches_plain_and_oracle(orc, case):
+    """FP32 stored matrices kept packed (16-bit column offsets modulo the padded
+    row count, 8-bit value indices): the same entries, so C(t) and the KPM
+    moments equal the plain form's bit for bit at the same launch shape (one and
+    two slices per warp), and the packed default shape (128 threads, four
+    slices) stays within the FP32 bars of the oracle."""
+    if case == "graphene":
+        h = ti.graphene_csr(60, 44, onsite=ti.anderson_onsite(5280, 1.0, 3))
+    elif case == "bilayer":
+        h = ti.bilayer_csr(23, 19, onsite=ti.anderson_onsite(4 * 23 * 19, 0.8, 4))
+    else:                                   # periodic wrap offsets beyond 2^15 before the modulus
+        h = ti.graphene_csr(256, 80, onsite=ti.anderson_onsite(40960, 1.0, 5))
+    rescale = max(9.0, 1.02 * ti.gershgorin_bound(h))
+    dt = math.pi / rescale
+    psi0 = ti.random_phase_state(h.n, 6)
+    ref = orc.dos_corr(h, rescale, psi0, dt, 128)
+    ref_mu = orc.kpm_moments(h, rescale, psi0, 256)
+    out = {}
+    for name, flags, bt, spw in (("packed", 0, 512, 1), ("plain", tb.TBPM_F_PLAIN_SELL, 512, 1),
+                                 ("packed_s2", 0, 256, 2), ("plain_s2", tb.TBPM_F_PLAIN_SELL, 256, 2),
+                                 ("packed_default", 0, 0, 0)):
+        ctx = tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, rescale,
+                             tb.make_opts(precision=tb.TBPM_FP32, flags=flags | tb.TBPM_F_NO_CLUSTER,
+                                          block_threads=bt, slices_per_warp=spw))
+        info = tb.tbpm_get_info(ctx)
+        assert info["packed"] == (0 if name.startswith("plain") else 1)
+        if name == "packed_default":
+            assert (info["block_threads"], info["slices_per_warp"]) == (128, 4)
+        out[name] = (tb.tbpm_dos_corr(ctx, psi0, dt, 128), tb.kpm_moments(ctx, psi0, 256))
+    for a, b in (("packed", "plain"), ("packed_s2", "plain_s2")):
+        assert np.array_equal(out[a][0], out[b][0]), a
+        assert np.array_equal(out[a][1], out[b][1]), a
+    assert np.max(np.abs(out["packed_default"][0] - ref)) <= C_TOL
+    assert np.max(np.abs(out["packed_default"][1] - ref_mu)) <= 1e-4
+
+
+def test_what_is_not_packed(orc):
+    """Complex values, FP64 contexts and column offsets beyond 16 bits keep the
+    plain form only; the latter still matches the oracle."""
+    h = ti.graphene_csr(20, 20, onsite=ti.anderson_onsite(800, 1.0, 3), bond_phases=[0.3, 0.1, 0.2])
+    ctx = tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, 9.0, tb.make_opts(precision=tb.TBPM_FP32))
+    assert tb.tbpm_get_info(ctx)["packed"] == 0
+    ctx = tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, 9.0)                      # FP64
+    assert tb.tbpm_get_info(ctx)["packed"] == 0
+    r = ti.random_hermitian_csr(70000, 2, seed=3, scale=1.0)
+    r.val = np.ascontiguousarray(r.val.real.astype(np.complex128))       # real symmetric, random columns
+    rescale = 1.05 * ti.gershgorin_bound(r)
+    ctx = tb.tbpm_create(r.n, r.row_ptr, r.col, r.val, rescale, tb.make_opts(precision=tb.TBPM_FP32))
+    assert tb.tbpm_get_info(ctx)["packed"] == 0
+    psi0 = ti.random_phase_state(r.n, 1)
+    c = tb.tbpm_dos_corr(ctx, psi0, 2.0 / rescale, 20)
+    assert np.max(np.abs(c - orc.dos_corr(r, rescale, psi0, 2.0 / rescale, 20))) <= C_TOL
+
