@@ -456,6 +456,8 @@ def alu_roof(units_per_s, fp64_ops_per_unit):
 B_SELL32 = 3 * (4 + 4) + 4 + 0.25
 # the same entries packed: 16-bit column offset + 8-bit value index per entry
 B_SELL32_PACKED = 3 * (2 + 1) + 4 + 0.25
+# packed per row (every slice of width 3): one 64-bit word and the diagonal
+B_SELL32_ROWS = 8 + 4
 B_VEC32 = 4 * 8
 # the blocked stencil over one time step of 17 sweeps, without halo re-reads:
 # first block psi + on-site in (12 B), two b out (16 B); middle block psi,
@@ -586,10 +588,13 @@ def run_variants(args, dev, stream):
                      "states": 1, "n_steps": 1024,
                      "shape": {"grid_blocks": i3["grid_blocks"], "block_threads": i3["block_threads"],
                                "slices_per_warp": i3["slices_per_warp"], "tuned": bool(i3["tuned"])},
-                     "packed": bool(i3["packed"]),
-                     "roofline": (hbm_roof(v3, B_SELL32_PACKED + B_VEC32,
-                                           "middle sweep, packed stored matrix + 4 vector streams")
-                                  if i3["packed"] else
+                     "packed": ("no", "per entry", "per row")[i3["packed"]],
+                     "roofline": (hbm_roof(v3, B_SELL32_ROWS + B_VEC32,
+                                           "middle sweep, stored matrix packed per row + 4 vector streams")
+                                  if i3["packed"] == 2 else
+                                  hbm_roof(v3, B_SELL32_PACKED + B_VEC32,
+                                           "middle sweep, stored matrix packed per entry + 4 vector streams")
+                                  if i3["packed"] == 1 else
                                   hbm_roof(v3, B_SELL32 + B_VEC32, "middle sweep, stored matrix + 4 vector streams")),
                      "dos_l1_vs_oracle": None if orc3 is None else dos_l1(c64, out[0].cpu().numpy(), orc3, DT),
                      "max_abs_dC_vs_oracle": None if orc3 is None else float(np.max(np.abs(out[0].cpu().numpy() - orc3))),

@@ -99,8 +99,13 @@ extern "C" {
                                           occur: a 16-bit column offset and an
                                           8-bit value index per entry (3 B instead
                                           of 8), which the single-state sweeps and
-                                          KPM passes read; this flag keeps only the
-                                          plain form. Results are identical      */
+                                          KPM passes read; when moreover every
+                                          32-row slice holds 3 entries per row and
+                                          at most 32 values occur, one 64-bit word
+                                          per row instead (three offsets and
+                                          three 5-bit indices). This flag keeps
+                                          only the plain form. Results are
+                                          identical                              */
 
 typedef struct tbpm_opts {
     int precision;       /* TBPM_FP64 | TBPM_FP32                                  */
@@ -112,12 +117,13 @@ typedef struct tbpm_opts {
     double bessel_tol;   /* Chebyshev cutoff |J_k| < tol; 0 selects 1e-12          */
     int block_threads;   /* launch shape of the single-state sweeps: threads per
                             block, 128 | 256 | 512 | 1024; 0 selects 512 (128 for
-                            a packed stored matrix, see TBPM_F_PLAIN_SELL). 1024 and
+                            a stored matrix packed per entry, 256 packed per row,
+                            see TBPM_F_PLAIN_SELL). 1024 and
                             slices_per_warp > 1 are built for the stored-matrix
                             path only (TBPM_ERR_UNSUPPORTED on a stencil)         */
     int slices_per_warp; /* 32-row slices a warp works on at once: 1 | 2 | 4 (2
                             and 4 with at most 512 threads); 0 selects 1 (4 for
-                            a packed stored matrix). The
+                            a stored matrix packed per entry, 2 per row). The
                             grid is whole waves of the shape's occupancy.
                             TBPM_F_AUTOTUNE replaces both with the tuned shape    */
 } tbpm_opts;
@@ -414,7 +420,8 @@ typedef struct tbpm_info {
     double tune_default_us;    /* autotuner: us per sweep (average over a time
                                   step) at the context's shape before tuning    */
     double tune_best_us;       /* autotuner: the same at the chosen shape       */
-    int packed;                /* 1 when the stored matrix is also kept packed
+    int packed;                /* the stored matrix is also kept packed: 0 no,
+                                  1 per entry, 2 one word per row
                                   (TBPM_F_PLAIN_SELL)                            */
 } tbpm_info;
 

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kBlockB1, sizeof(R) == 4 ? 3 : 2) kpm_b1(KpmPa
     SweepParams sp;                     // operator fields for the shared helpers
     sp.n = p.n; sp.nslices = p.nslices; sp.slice_off = p.slice_off; sp.cols = p.cols; sp.vals = p.vals;
     sp.diag = p.diag; sp.l1 = p.l1; sp.l2 = p.l2; sp.t = p.t; sp.t_perp = p.t_perp;
-    sp.cdelta = p.cdelta; sp.vidx = p.vidx; sp.vtab = p.vtab; sp.npad = p.npad;
+    sp.cdelta = p.cdelta; sp.vidx = p.vidx; sp.vtab = p.vtab; sp.rowpack = p.rowpack; sp.npad = p.npad;
     const V *__restrict__ x = reinterpret_cast<const V *>(p.x);
     V *y = reinterpret_cast<V *>(p.y);
     const R *diag = reinterpret_cast<const R *>(p.diag);
@@ -178,7 +178,8 @@ cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cuda
         return kpm_dispatch<double, OP_STENCIL_BI, true>(p, grid, v.pdl, s);
     }
     if (v.op == OP_SELL)
-        return v.packed ? kpm_dispatch<float, OP_SELL, VM_PACKED>(p, grid, v.pdl, s)
+        return v.packed == 2 ? kpm_dispatch<float, OP_SELL, VM_ROWS>(p, grid, v.pdl, s)
+               : v.packed == 1 ? kpm_dispatch<float, OP_SELL, VM_PACKED>(p, grid, v.pdl, s)
                : v.real_values ? kpm_dispatch<float, OP_SELL, true>(p, grid, v.pdl, s)
                                : kpm_dispatch<float, OP_SELL, false>(p, grid, v.pdl, s);
     if (v.op == OP_STENCIL_MONO) return kpm_dispatch<float, OP_STENCIL_MONO, true>(p, grid, v.pdl, s);

@@ -197,10 +197,11 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
             continue;
         }
         // a full group of SPW slices: the row operands and slice extents first
-        int64_t off[SPW];
-        int w0 = 0;
+        int64_t off[SPW] = {};
+        int w0 = 3;
         bool same = true;
-        {
+        if constexpr (VM != VM_ROWS) {      // VM_ROWS: every slice has width 3
+            w0 = 0;
             int64_t lo = ldm<R>(p.slice_off + s0);
 #pragma unroll
             for (int q = 0; q < SPW; ++q) {
@@ -332,7 +333,9 @@ cudaError_t sell_shape_launch(const SweepVariant &v, SweepKind kind, bool a_imag
     if (multi)
         return v.real_values ? sweep_dispatch<float, OP_SELL, true, true, SPW, LB>(kind, a_imag, has_z, p, grid, v.block, v.pdl, s)
                              : sweep_dispatch<float, OP_SELL, false, true, SPW, LB>(kind, a_imag, has_z, p, grid, v.block, v.pdl, s);
-    if (v.packed)           // the packed form: FP32 real values of a single instance
+    if (v.packed == 2)      // the packed forms: FP32 real values of a single instance
+        return sweep_dispatch<float, OP_SELL, VM_ROWS, false, SPW, LB>(kind, a_imag, has_z, p, grid, v.block, v.pdl, s);
+    if (v.packed == 1)
         return sweep_dispatch<float, OP_SELL, VM_PACKED, false, SPW, LB>(kind, a_imag, has_z, p, grid, v.block, v.pdl, s);
     return v.real_values ? sweep_dispatch<float, OP_SELL, true, false, SPW, LB>(kind, a_imag, has_z, p, grid, v.block, v.pdl, s)
                          : sweep_dispatch<float, OP_SELL, false, false, SPW, LB>(kind, a_imag, has_z, p, grid, v.block, v.pdl, s);
@@ -351,7 +354,8 @@ int sell_shape_occupancy(const SweepVariant &v, bool multi)
     if (multi)
         return v.real_values ? sweep_occupancy_of<float, OP_SELL, true, true, SPW, LB>(v.block)
                              : sweep_occupancy_of<float, OP_SELL, false, true, SPW, LB>(v.block);
-    if (v.packed) return sweep_occupancy_of<float, OP_SELL, VM_PACKED, false, SPW, LB>(v.block);
+    if (v.packed == 2) return sweep_occupancy_of<float, OP_SELL, VM_ROWS, false, SPW, LB>(v.block);
+    if (v.packed == 1) return sweep_occupancy_of<float, OP_SELL, VM_PACKED, false, SPW, LB>(v.block);
     return v.real_values ? sweep_occupancy_of<float, OP_SELL, true, false, SPW, LB>(v.block)
                          : sweep_occupancy_of<float, OP_SELL, false, false, SPW, LB>(v.block);
 }

@@ -28,8 +28,12 @@ __device__ __forceinline__ T ldm(const T *p)
 // taken modulo the padded row count, and an 8-bit index into a table of at
 // most 256 distinct values (3 B per entry instead of 8 for lattice-like
 // matrices, whose neighbours sit at a few fixed offsets and whose hoppings take
-// a few values). The entries, and so the products, are the same in every form.
-enum ValueMode { VM_COMPLEX = 0, VM_REAL = 1, VM_PACKED = 2 };
+// a few values). VM_ROWS (real values, FP32, every slice of width 3, at most
+// 32 values): one 64-bit word per row holding the row's three 16-bit column
+// offsets (bits 0-47) and three 5-bit value indices (bits 48-62), so that a row
+// costs one load and no slice extents are read. The entries, and so the
+// products, are the same in every form.
+enum ValueMode { VM_COMPLEX = 0, VM_REAL = 1, VM_PACKED = 2, VM_ROWS = 3 };
 
 // One stored entry: acc += v x[c] (real v) or v x[c] (complex v).
 template <typename R, int VM>
@@ -98,6 +102,27 @@ struct SellRow<R, VM_PACKED> {
     }
 };
 
+template <typename R>
+struct SellRow<R, VM_ROWS> {
+    uint64_t word;
+    const R *tab;
+    int row, npad;
+    __device__ __forceinline__ void init(const SweepParams &p, int64_t, int, int64_t r)
+    {
+        word = ldm<R>(p.rowpack + r);
+        tab = reinterpret_cast<const R *>(p.vtab);
+        row = (int)r;
+        npad = (int)p.npad;
+    }
+    __device__ __forceinline__ void load(SellEntry<R, VM_ROWS> &e, int j) const
+    {
+        int c = row + (int)(int16_t)(uint16_t)(word >> (16 * j));
+        c = c < 0 ? c + npad : c;
+        e.c = c >= npad ? c - npad : c;
+        e.v = __ldg(tab + (int)((word >> (48 + 5 * j)) & 31u));
+    }
+};
+
 // N entries j0 .. j0+N-1 of the lane's row: all loads first, then the FMAs.
 template <typename R, int VM, int N>
 __device__ __forceinline__ void sell_entries(const SellRow<R, VM> &rr, int j0,
@@ -125,6 +150,12 @@ __device__ __forceinline__ void sell_apply(const SweepParams &p, int64_t s, int 
                                            const typename V2<R>::T *__restrict__ x,
                                            R &ar, R &ai)
 {
+    if constexpr (VM == VM_ROWS) {          // every slice has width 3: no extents to read
+        SellRow<R, VM_ROWS> rr;
+        rr.init(p, 0, lane, (s << 5) + lane);
+        sell_entries<R, VM_ROWS, 3>(rr, 0, x, ar, ai);
+        return;
+    }
     const int64_t off = ldm<R>(p.slice_off + s);
     const int w = (int)((ldm<R>(p.slice_off + s + 1) - off) >> 5);
     SellRow<R, VM> rr;

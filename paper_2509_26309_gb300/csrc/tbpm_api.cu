@@ -283,6 +283,32 @@ bool pack_sell(const std::vector<int32_t> &cols, const std::vector<float> &vals,
     return true;
 }
 
+// The per-row packed form of a packed matrix whose slices all have width 3 and
+// whose entries take at most 32 values: row r's word holds the 16-bit offsets
+// of its entries j = 0, 1, 2 in bits 16 j .. 16 j + 15 and their 5-bit value
+// indices in bits 48 + 5 j .. 52 + 5 j. False when the matrix does not qualify.
+bool pack_rows(const std::vector<int16_t> &cdelta, const std::vector<uint8_t> &vidx,
+               const std::vector<int64_t> &off, std::vector<uint64_t> &rowpack)
+{
+    const int64_t nslices = (int64_t)off.size() - 1;
+    for (int64_t sl = 0; sl < nslices; ++sl)
+        if (off[sl + 1] - off[sl] != 3 * kSlice) return false;
+    for (uint8_t k : vidx)
+        if (k >= 32) return false;
+    rowpack.assign(nslices * kSlice, 0);
+    for (int64_t sl = 0; sl < nslices; ++sl)
+        for (int lane = 0; lane < kSlice; ++lane) {
+            uint64_t w = 0;
+            for (int j = 0; j < 3; ++j) {
+                const int64_t e = off[sl] + (int64_t)j * kSlice + lane;
+                w |= (uint64_t)(uint16_t)cdelta[e] << (16 * j);
+                w |= (uint64_t)vidx[e] << (48 + 5 * j);
+            }
+            rowpack[sl * kSlice + lane] = w;
+        }
+    return true;
+}
+
 template <typename T>
 int upload(tbpm_ctx *ctx, void **dst, const std::vector<T> &src)
 {
@@ -316,16 +342,23 @@ int setup_sell(tbpm_ctx *ctx, const HostMatrix &m, const std::vector<double> *ro
         to_sell<float>(m, ctx->n_pad, s, m.real_values, off, cols, vals, diag, ctx->sell.max_width);
         if ((rc = upload(ctx, (void **)&ctx->sell.vals, vals))) return rc;
         if ((rc = upload(ctx, (void **)&ctx->sell.diag, diag))) return rc;
-        // the packed form, for a single instance with real values
+        // a packed form, for a single instance with real values: one word per
+        // row where the matrix allows it, else the per-entry form
         std::vector<int16_t> cdelta;
         std::vector<uint8_t> vidx;
         std::vector<float> vtab;
+        std::vector<uint64_t> rowpack;
         if (!row_scale_given && m.real_values && !(ctx->flags & TBPM_F_PLAIN_SELL) &&
             pack_sell(cols, vals, off, ctx->n_pad, cdelta, vidx, vtab)) {
-            if ((rc = upload(ctx, (void **)&ctx->sell.cdelta, cdelta))) return rc;
-            if ((rc = upload(ctx, (void **)&ctx->sell.vidx, vidx))) return rc;
             if ((rc = upload(ctx, (void **)&ctx->sell.vtab, vtab))) return rc;
-            ctx->sell.packed = true;
+            if (pack_rows(cdelta, vidx, off, rowpack)) {
+                if ((rc = upload(ctx, (void **)&ctx->sell.rowpack, rowpack))) return rc;
+                ctx->sell.packed = 2;
+            } else {
+                if ((rc = upload(ctx, (void **)&ctx->sell.cdelta, cdelta))) return rc;
+                if ((rc = upload(ctx, (void **)&ctx->sell.vidx, vidx))) return rc;
+                ctx->sell.packed = 1;
+            }
         }
     }
     ctx->sell.nslices = ctx->n_pad / kSlice;
@@ -343,7 +376,7 @@ SweepVariant variant(const tbpm_ctx *ctx, int states)
     v.precision = ctx->precision;
     v.op = ctx->op;
     v.real_values = ctx->op == OP_SELL ? ctx->sell.real_values : true;
-    v.packed = ctx->op == OP_SELL && ctx->sell.packed && ctx->precision == TBPM_FP32 && ctx->ninst == 0;
+    v.packed = ctx->op == OP_SELL && ctx->precision == TBPM_FP32 && ctx->ninst == 0 ? ctx->sell.packed : 0;
     v.states = states;
     v.pdl = !(ctx->flags & TBPM_F_NO_PDL);
     v.block = ctx->sw_block;
@@ -368,6 +401,7 @@ void fill_operator(const tbpm_ctx *ctx, SweepParams &p)
         p.cdelta = ctx->sell.cdelta;
         p.vidx = ctx->sell.vidx;
         p.vtab = ctx->sell.vtab;
+        p.rowpack = ctx->sell.rowpack;
         p.npad = ctx->n_pad;
     } else {
         p.diag = ctx->sten.onsite;
@@ -543,7 +577,7 @@ int enqueue_kpm_chunk(tbpm_ctx *ctx, int len, cudaStream_t s, int64_t *launches)
     memset(&p, 0, sizeof(p));
     p.n = op.n; p.nslices = op.nslices; p.slice_off = op.slice_off; p.cols = op.cols;
     p.vals = op.vals; p.diag = op.diag; p.l1 = op.l1; p.l2 = op.l2; p.t = op.t; p.t_perp = op.t_perp;
-    p.cdelta = op.cdelta; p.vidx = op.vidx; p.vtab = op.vtab; p.npad = op.npad;
+    p.cdelta = op.cdelta; p.vidx = op.vidx; p.vtab = op.vtab; p.rowpack = op.rowpack; p.npad = op.npad;
     p.partials = ctx->d_partials;
     p.nblk = ctx->nblk_kpm;
     p.scale = 1.0;
@@ -961,16 +995,17 @@ static int check_opts(const tbpm_opts *in, tbpm_opts *o)
 // Applies the requested launch shape of the single-state sweeps once the
 // operator is known: TBPM_ERR_UNSUPPORTED if it is not built for this operator;
 // the grid is whole waves of the shape's middle-sweep occupancy. Unset fields
-// (0) take the operator's default: 512 threads and one slice per warp, or, for
-// a packed stored matrix, whose smaller entries leave its sweeps waiting on
-// their dependent loads, 128 threads and four slices per warp (measured on
-// GB300 at 2048^2: 69.6 against 84.3 us per sweep at 512 x 1).
+// (0) take the operator's default: 512 threads and one slice per warp; for a
+// stored matrix packed per entry, whose smaller entries leave its sweeps
+// waiting on their dependent loads, 128 threads and four slices per warp
+// (measured on GB300 for graphene 2048^2: 69.6 against 84.3 us per sweep at
+// 512 x 1); packed per row, 256 threads and two slices (58.4 us, against 60.1
+// at 128 x 4 and 61.0 at 512 x 1).
 static int apply_shape(tbpm_ctx *ctx, const tbpm_opts &o)
 {
     SweepVariant v = variant(ctx, 1);
-    const bool packed = v.packed;
-    v.block = o.block_threads ? o.block_threads : (packed ? 128 : kBlockB1);
-    v.spw = o.slices_per_warp ? o.slices_per_warp : (packed ? 4 : 1);
+    v.block = o.block_threads ? o.block_threads : v.packed == 2 ? 256 : v.packed == 1 ? 128 : kBlockB1;
+    v.spw = o.slices_per_warp ? o.slices_per_warp : v.packed == 2 ? 2 : v.packed == 1 ? 4 : 1;
     if (v.block == kBlockB1 && v.spw == 1) return TBPM_OK;
     if (!sweep_shape_built(v)) return TBPM_ERR_UNSUPPORTED;
     const int occ = sweep_shape_occupancy(v, ctx->d_slice_inst != nullptr);
@@ -1263,7 +1298,7 @@ void tbpm_destroy(tbpm_ctx *ctx)
     destroy_graphs(ctx);
     cudaFree(ctx->sell.slice_off); cudaFree(ctx->sell.cols); cudaFree(ctx->sell.vals);
     cudaFree(ctx->sell.diag); cudaFree(ctx->sten.onsite);
-    cudaFree(ctx->sell.cdelta); cudaFree(ctx->sell.vidx); cudaFree(ctx->sell.vtab);
+    cudaFree(ctx->sell.cdelta); cudaFree(ctx->sell.vidx); cudaFree(ctx->sell.vtab); cudaFree(ctx->sell.rowpack);
     cudaFree(ctx->d_coef); cudaFree(ctx->d_K); cudaFree(ctx->d_counter);
     cudaFree(ctx->d_psi); cudaFree(ctx->d_b0); cudaFree(ctx->d_b1); cudaFree(ctx->d_psi0);
     cudaFree(ctx->d_partials); cudaFree(ctx->d_out); cudaFree(ctx->d_stage); cudaFree(ctx->d_misc);
@@ -1480,7 +1515,7 @@ int kpm_moments(tbpm_ctx *ctx, const double *psi0, int nstates, int M, double *m
         memset(&p, 0, sizeof(p));
         p.n = op.n; p.nslices = op.nslices; p.slice_off = op.slice_off; p.cols = op.cols;
         p.vals = op.vals; p.diag = op.diag; p.l1 = op.l1; p.l2 = op.l2; p.t = op.t; p.t_perp = op.t_perp;
-        p.cdelta = op.cdelta; p.vidx = op.vidx; p.vtab = op.vtab; p.npad = op.npad;
+        p.cdelta = op.cdelta; p.vidx = op.vidx; p.vtab = op.vtab; p.rowpack = op.rowpack; p.npad = op.npad;
         p.x = ctx->d_psi; p.y = ctx->d_b0; p.scale = 0.5; p.first = true;
         p.partials = ctx->d_partials; p.delta = 0; p.nblk = ctx->nblk_kpm;
         CU(launch_kpm(v, p, ctx->nblk_kpm, ctx->stream));
@@ -2138,7 +2173,7 @@ int tbpm_get_info(const tbpm_ctx *ctx, tbpm_info *info)
     info->tune_candidates = ctx->tune_candidates;
     info->tune_default_us = ctx->tune_default_us;
     info->tune_best_us = ctx->tune_best_us;
-    info->packed = ctx->op == OP_SELL && ctx->sell.packed ? 1 : 0;
+    info->packed = ctx->op == OP_SELL ? ctx->sell.packed : 0;
     return TBPM_OK;
 }
 

@@ -75,12 +75,16 @@ struct Sell {
     void *diag = nullptr;         // R[n_pad]
     bool real_values = true;
     int max_width = 0;
-    // the packed form of the same entries (FP32, real values, when every
+    // a packed form of the same entries (FP32, real values, when every
     // column offset fits 16 bits modulo n_pad and at most 256 values occur):
-    // entry e is column (row + cdelta[e]) mod n_pad, value vtab[vidx[e]]
-    bool packed = false;
-    int16_t *cdelta = nullptr;    // int16[nent]
-    uint8_t *vidx = nullptr;      // uint8[nent]
+    // entry e is column (row + cdelta[e]) mod n_pad, value vtab[vidx[e]]; when
+    // besides every slice has width 3 and at most 32 values occur, one word
+    // per row instead (rowpack[r]: offset j in bits 16j..16j+15, value index j
+    // in bits 48+5j..52+5j)
+    int packed = 0;               // 0: plain only; 1: also per entry; 2: also per row
+    int16_t *cdelta = nullptr;    // per entry (packed 1): int16[nent]
+    uint8_t *vidx = nullptr;      // per entry (packed 1): uint8[nent]
+    uint64_t *rowpack = nullptr;  // per row (packed 2, every slice of width 3): uint64[n_pad]
     void *vtab = nullptr;         // R[256]
 };
 
@@ -104,6 +108,7 @@ struct SweepParams {
     const int16_t *cdelta;        // the packed form (VM_PACKED kernels): column offsets,
     const uint8_t *vidx;          // value indices and the value table, offsets taken
     const void *vtab;             // modulo npad
+    const uint64_t *rowpack;      // the per-row packed form (VM_ROWS kernels)
     int64_t npad;
     int64_t l1, l2;               // stencil geometry
     double t, t_perp;
@@ -184,9 +189,10 @@ struct KpmParams {
     const int32_t *cols;
     const void *vals;
     const void *diag;
-    const int16_t *cdelta;        // the packed form, as in SweepParams
+    const int16_t *cdelta;        // the packed forms, as in SweepParams
     const uint8_t *vidx;
     const void *vtab;
+    const uint64_t *rowpack;
     int64_t npad;
     int64_t l1, l2;
     double t, t_perp;
@@ -206,7 +212,8 @@ struct SweepVariant {
     int precision;                // TBPM_FP64 | TBPM_FP32
     int op;                       // OpKind
     bool real_values;
-    bool packed = false;          // the operator's packed form is used (FP32 SELL, real values)
+    int packed = 0;               // the operator's packed form used (FP32 SELL, real values):
+                                  // 0 none, 1 per entry (VM_PACKED), 2 per row (VM_ROWS)
     int states;                   // B: 1 or 16
     bool pdl;                     // B = 1 sweeps as programmatic dependent launches
     int block = kBlockB1;         // B = 1 sweeps: threads per block (32 .. 1024)
