@@ -304,15 +304,18 @@ cudaError_t sweep_dispatch(SweepKind kind, bool a_imag, bool has_z, const SweepP
     return cudaErrorInvalidValue;
 }
 
-// Resident blocks per SM of the middle sweep at this shape.
+// Resident blocks per SM of the middle sweep at this shape, or of the final
+// sweep (with b_2, the form of every final sweep but K = 3's).
 template <typename R, int OP, int VM, bool MULTI, int SPW, int LB>
-int sweep_occupancy_of(int block)
+int sweep_occupancy_of(int block, bool fin = false)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, sweep_b1<R, OP, VM, B_ONE, false, true, false, MULTI, SPW, LB>, block, 0) != cudaSuccess)
-        return 0;
-    return per_sm;
+    const cudaError_t e =
+        fin ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &per_sm, sweep_b1<R, OP, VM, B_REAL, false, true, true, MULTI, SPW, LB>, block, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &per_sm, sweep_b1<R, OP, VM, B_ONE, false, true, false, MULTI, SPW, LB>, block, 0);
+    return e == cudaSuccess ? per_sm : 0;
 }
 
 // The stored-matrix sweeps of one shape, for every precision, value kind and
@@ -342,22 +345,22 @@ cudaError_t sell_shape_launch(const SweepVariant &v, SweepKind kind, bool a_imag
 }
 
 template <int SPW, int LB>
-int sell_shape_occupancy(const SweepVariant &v, bool multi)
+int sell_shape_occupancy(const SweepVariant &v, bool multi, bool fin)
 {
     if (v.precision == TBPM_FP64) {
         if (multi)
-            return v.real_values ? sweep_occupancy_of<double, OP_SELL, true, true, SPW, LB>(v.block)
-                                 : sweep_occupancy_of<double, OP_SELL, false, true, SPW, LB>(v.block);
-        return v.real_values ? sweep_occupancy_of<double, OP_SELL, true, false, SPW, LB>(v.block)
-                             : sweep_occupancy_of<double, OP_SELL, false, false, SPW, LB>(v.block);
+            return v.real_values ? sweep_occupancy_of<double, OP_SELL, true, true, SPW, LB>(v.block, fin)
+                                 : sweep_occupancy_of<double, OP_SELL, false, true, SPW, LB>(v.block, fin);
+        return v.real_values ? sweep_occupancy_of<double, OP_SELL, true, false, SPW, LB>(v.block, fin)
+                             : sweep_occupancy_of<double, OP_SELL, false, false, SPW, LB>(v.block, fin);
     }
     if (multi)
-        return v.real_values ? sweep_occupancy_of<float, OP_SELL, true, true, SPW, LB>(v.block)
-                             : sweep_occupancy_of<float, OP_SELL, false, true, SPW, LB>(v.block);
-    if (v.packed == 2) return sweep_occupancy_of<float, OP_SELL, VM_ROWS, false, SPW, LB>(v.block);
-    if (v.packed == 1) return sweep_occupancy_of<float, OP_SELL, VM_PACKED, false, SPW, LB>(v.block);
-    return v.real_values ? sweep_occupancy_of<float, OP_SELL, true, false, SPW, LB>(v.block)
-                         : sweep_occupancy_of<float, OP_SELL, false, false, SPW, LB>(v.block);
+        return v.real_values ? sweep_occupancy_of<float, OP_SELL, true, true, SPW, LB>(v.block, fin)
+                             : sweep_occupancy_of<float, OP_SELL, false, true, SPW, LB>(v.block, fin);
+    if (v.packed == 2) return sweep_occupancy_of<float, OP_SELL, VM_ROWS, false, SPW, LB>(v.block, fin);
+    if (v.packed == 1) return sweep_occupancy_of<float, OP_SELL, VM_PACKED, false, SPW, LB>(v.block, fin);
+    return v.real_values ? sweep_occupancy_of<float, OP_SELL, true, false, SPW, LB>(v.block, fin)
+                         : sweep_occupancy_of<float, OP_SELL, false, false, SPW, LB>(v.block, fin);
 }
 
 }  // namespace

@@ -384,9 +384,20 @@ SweepVariant variant(const tbpm_ctx *ctx, int states)
     return v;
 }
 
-// Warps of the single-state sweep grid: the number of per-warp dot partials a
-// final sweep of one instance writes per slot.
-int64_t sweep_warps(const tbpm_ctx *ctx) { return (int64_t)ctx->nblk * ctx->sw_block / 32; }
+// Warps of the single-state final sweep's grid: the number of per-warp dot
+// partials a final sweep of one instance writes per slot.
+int64_t sweep_warps(const tbpm_ctx *ctx) { return (int64_t)ctx->nblk_fin * ctx->sw_block / 32; }
+
+// The final sweep's grid: one wave of its own occupancy at the context's shape,
+// at most the other sweeps' grid. It holds more registers than a middle sweep
+// (the FP64 <psi0|psi> and the norm), so the middle sweeps' grid of whole waves
+// of their occupancy (FP64: three blocks of 512 threads per SM) would run it as
+// one and a half waves (two blocks per SM), the last half wave on half the SM.
+void set_final_grid(tbpm_ctx *ctx)
+{
+    const int occ = sweep_shape_occupancy(variant(ctx, 1), ctx->d_slice_inst != nullptr, true);
+    ctx->nblk_fin = occ > 0 ? std::min(ctx->nblk, occ * ctx->num_sms) : ctx->nblk;
+}
 
 void fill_operator(const tbpm_ctx *ctx, SweepParams &p)
 {
@@ -493,7 +504,7 @@ int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, int B, int64_t ld, cudaStre
 {
     const SweepVariant v = variant(ctx, B);
     auto sweep = [&](SweepKind kind, bool a_imag, bool has_z, const SweepParams &p) {
-        return B == 1 ? launch_sweep(v, kind, a_imag, has_z, p, ctx->nblk, s)
+        return B == 1 ? launch_sweep(v, kind, a_imag, has_z, p, kind == SW_FINAL ? ctx->nblk_fin : ctx->nblk, s)
                       : launch_sweep_b16(v, kind, a_imag, has_z, p, ctx->nblk16, s);
     };
     SweepParams p;
@@ -663,7 +674,7 @@ int enqueue_series(tbpm_ctx *ctx, const double2 *coef, int K, bool alt, void *in
     p.y = out;
     p.ia = 0; p.ib = K == 3 ? 2 : -1; p.ic = -1; p.bscale = 0.5;
     p.delta = slot;
-    CU(launch_sweep(v, SW_FINAL, false, K >= 4, p, ctx->nblk, s));
+    CU(launch_sweep(v, SW_FINAL, false, K >= 4, p, ctx->nblk_fin, s));
     *launches += K - 1;
     return TBPM_OK;
 }
@@ -1006,13 +1017,15 @@ static int apply_shape(tbpm_ctx *ctx, const tbpm_opts &o)
     SweepVariant v = variant(ctx, 1);
     v.block = o.block_threads ? o.block_threads : v.packed == 2 ? 256 : v.packed == 1 ? 128 : kBlockB1;
     v.spw = o.slices_per_warp ? o.slices_per_warp : v.packed == 2 ? 2 : v.packed == 1 ? 4 : 1;
-    if (v.block == kBlockB1 && v.spw == 1) return TBPM_OK;
-    if (!sweep_shape_built(v)) return TBPM_ERR_UNSUPPORTED;
-    const int occ = sweep_shape_occupancy(v, ctx->d_slice_inst != nullptr);
-    if (occ < 1) return TBPM_ERR_UNSUPPORTED;
-    ctx->sw_block = v.block;
-    ctx->sw_spw = v.spw;
-    ctx->nblk = occ * ctx->num_sms;
+    if (v.block != kBlockB1 || v.spw != 1) {
+        if (!sweep_shape_built(v)) return TBPM_ERR_UNSUPPORTED;
+        const int occ = sweep_shape_occupancy(v, ctx->d_slice_inst != nullptr);
+        if (occ < 1) return TBPM_ERR_UNSUPPORTED;
+        ctx->sw_block = v.block;
+        ctx->sw_spw = v.spw;
+        ctx->nblk = occ * ctx->num_sms;
+    }
+    set_final_grid(ctx);
     return TBPM_OK;
 }
 
@@ -1116,7 +1129,9 @@ static int autotune(tbpm_ctx *ctx)
         p.z = Bv[(Kt - 4) & 1];
         p.y = ctx->d_psi;
         p.ia = 0; p.ib = -1; p.ic = -1; p.bscale = 0.5;
-        return launch_sweep(v, SW_FINAL, false, true, p, grid, ctx->stream);
+        const int occ_fin = sweep_shape_occupancy(v, multi, true);         // as set_final_grid
+        const int grid_fin = occ_fin > 0 ? std::min(grid, occ_fin * ctx->num_sms) : grid;
+        return launch_sweep(v, SW_FINAL, false, true, p, grid_fin, ctx->stream);
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto time_us = [&](const Cand &c, int reps, double *us) -> int {
@@ -1166,6 +1181,7 @@ static int autotune(tbpm_ctx *ctx)
     ctx->nblk = best.grid;
     ctx->sw_block = best.block;
     ctx->sw_spw = best.spw;
+    set_final_grid(ctx);
     ctx->cap_states = 0;
     ctx->tuned = true;
     ctx->tune_candidates = (int)cands.size();
