@@ -151,20 +151,20 @@ cudaError_t launch_sweep(const SweepVariant &v, SweepKind kind, bool a_imag, boo
     return launch_sell_s4_b512(v, kind, a_imag, has_z, p, grid, s);
 }
 
-int sweep_shape_occupancy(const SweepVariant &v, bool multi, bool fin)
+int sweep_shape_occupancy(const SweepVariant &v, bool multi, int kind)
 {
     if (!sweep_shape_built(v)) return 0;
     if (v.spw == 1 && v.block <= kBlockB1) {
-        if (v.op == OP_SELL) return sell_shape_occupancy<1, kBlockB1>(v, multi, fin);
+        if (v.op == OP_SELL) return sell_shape_occupancy<1, kBlockB1>(v, multi, kind);
         if (v.precision == TBPM_FP64)
-            return v.op == OP_STENCIL_MONO ? sweep_occupancy_of<double, OP_STENCIL_MONO, true, false, 1, kBlockB1>(v.block, fin)
-                                           : sweep_occupancy_of<double, OP_STENCIL_BI, true, false, 1, kBlockB1>(v.block, fin);
-        return v.op == OP_STENCIL_MONO ? sweep_occupancy_of<float, OP_STENCIL_MONO, true, false, 1, kBlockB1>(v.block, fin)
-                                       : sweep_occupancy_of<float, OP_STENCIL_BI, true, false, 1, kBlockB1>(v.block, fin);
+            return v.op == OP_STENCIL_MONO ? sweep_occupancy_of<double, OP_STENCIL_MONO, true, false, 1, kBlockB1>(v.block, kind)
+                                           : sweep_occupancy_of<double, OP_STENCIL_BI, true, false, 1, kBlockB1>(v.block, kind);
+        return v.op == OP_STENCIL_MONO ? sweep_occupancy_of<float, OP_STENCIL_MONO, true, false, 1, kBlockB1>(v.block, kind)
+                                       : sweep_occupancy_of<float, OP_STENCIL_BI, true, false, 1, kBlockB1>(v.block, kind);
     }
-    if (v.spw == 1) return occupancy_sell_s1_b1024(v, multi, fin);
-    if (v.spw == 2) return occupancy_sell_s2_b512(v, multi, fin);
-    return occupancy_sell_s4_b512(v, multi, fin);
+    if (v.spw == 1) return occupancy_sell_s1_b1024(v, multi, kind);
+    if (v.spw == 2) return occupancy_sell_s2_b512(v, multi, kind);
+    return occupancy_sell_s4_b512(v, multi, kind);
 }
 
 cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cudaStream_t s)

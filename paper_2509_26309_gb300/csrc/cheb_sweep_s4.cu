@@ -13,10 +13,10 @@ cudaError_t launch_sell_s4_b512(const SweepVariant &v, SweepKind kind, bool a_im
     return sell_shape_launch<4, 512>(v, kind, a_imag, has_z, p, grid, s);
 }
 
-int occupancy_sell_s4_b512(const SweepVariant &v, bool multi, bool fin)
+int occupancy_sell_s4_b512(const SweepVariant &v, bool multi, int kind)
 {
     if (v.op != OP_SELL || v.block > 512) return 0;
-    return sell_shape_occupancy<4, 512>(v, multi, fin);
+    return sell_shape_occupancy<4, 512>(v, multi, kind);
 }
 
 }  // namespace tbpm

@@ -304,18 +304,28 @@ cudaError_t sweep_dispatch(SweepKind kind, bool a_imag, bool has_z, const SweepP
     return cudaErrorInvalidValue;
 }
 
-// Resident blocks per SM of the middle sweep at this shape, or of the final
-// sweep (with b_2, the form of every final sweep but K = 3's).
+// Resident blocks per SM of one sweep kind at this shape (the fewest over the
+// kind's forms: c_k real or imaginary; the final sweep with b_2, the form of
+// every final sweep but K = 3's).
 template <typename R, int OP, int VM, bool MULTI, int SPW, int LB>
-int sweep_occupancy_of(int block, bool fin = false)
+int sweep_occupancy_of(int block, int kind = SW_MID)
 {
-    int per_sm = 0;
-    const cudaError_t e =
-        fin ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                  &per_sm, sweep_b1<R, OP, VM, B_REAL, false, true, true, MULTI, SPW, LB>, block, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                  &per_sm, sweep_b1<R, OP, VM, B_ONE, false, true, false, MULTI, SPW, LB>, block, 0);
-    return e == cudaSuccess ? per_sm : 0;
+    auto occ = [block](auto kernel) {
+        int per_sm = 0;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) == cudaSuccess ? per_sm : 0;
+    };
+    switch (kind) {
+    case SW_FIRST:
+        return std::min(occ(sweep_b1<R, OP, VM, B_REAL, true, false, false, MULTI, SPW, LB>),
+                        occ(sweep_b1<R, OP, VM, B_IMAG, false, false, false, MULTI, SPW, LB>));
+    case SW_SECOND:
+        return std::min(occ(sweep_b1<R, OP, VM, B_ONE, true, false, false, MULTI, SPW, LB>),
+                        occ(sweep_b1<R, OP, VM, B_ONE, false, false, false, MULTI, SPW, LB>));
+    case SW_FINAL:
+        return occ(sweep_b1<R, OP, VM, B_REAL, false, true, true, MULTI, SPW, LB>);
+    default:
+        return occ(sweep_b1<R, OP, VM, B_ONE, false, true, false, MULTI, SPW, LB>);
+    }
 }
 
 // The stored-matrix sweeps of one shape, for every precision, value kind and
@@ -345,22 +355,22 @@ cudaError_t sell_shape_launch(const SweepVariant &v, SweepKind kind, bool a_imag
 }
 
 template <int SPW, int LB>
-int sell_shape_occupancy(const SweepVariant &v, bool multi, bool fin)
+int sell_shape_occupancy(const SweepVariant &v, bool multi, int kind)
 {
     if (v.precision == TBPM_FP64) {
         if (multi)
-            return v.real_values ? sweep_occupancy_of<double, OP_SELL, true, true, SPW, LB>(v.block, fin)
-                                 : sweep_occupancy_of<double, OP_SELL, false, true, SPW, LB>(v.block, fin);
-        return v.real_values ? sweep_occupancy_of<double, OP_SELL, true, false, SPW, LB>(v.block, fin)
-                             : sweep_occupancy_of<double, OP_SELL, false, false, SPW, LB>(v.block, fin);
+            return v.real_values ? sweep_occupancy_of<double, OP_SELL, true, true, SPW, LB>(v.block, kind)
+                                 : sweep_occupancy_of<double, OP_SELL, false, true, SPW, LB>(v.block, kind);
+        return v.real_values ? sweep_occupancy_of<double, OP_SELL, true, false, SPW, LB>(v.block, kind)
+                             : sweep_occupancy_of<double, OP_SELL, false, false, SPW, LB>(v.block, kind);
     }
     if (multi)
-        return v.real_values ? sweep_occupancy_of<float, OP_SELL, true, true, SPW, LB>(v.block, fin)
-                             : sweep_occupancy_of<float, OP_SELL, false, true, SPW, LB>(v.block, fin);
-    if (v.packed == 2) return sweep_occupancy_of<float, OP_SELL, VM_ROWS, false, SPW, LB>(v.block, fin);
-    if (v.packed == 1) return sweep_occupancy_of<float, OP_SELL, VM_PACKED, false, SPW, LB>(v.block, fin);
-    return v.real_values ? sweep_occupancy_of<float, OP_SELL, true, false, SPW, LB>(v.block, fin)
-                         : sweep_occupancy_of<float, OP_SELL, false, false, SPW, LB>(v.block, fin);
+        return v.real_values ? sweep_occupancy_of<float, OP_SELL, true, true, SPW, LB>(v.block, kind)
+                             : sweep_occupancy_of<float, OP_SELL, false, true, SPW, LB>(v.block, kind);
+    if (v.packed == 2) return sweep_occupancy_of<float, OP_SELL, VM_ROWS, false, SPW, LB>(v.block, kind);
+    if (v.packed == 1) return sweep_occupancy_of<float, OP_SELL, VM_PACKED, false, SPW, LB>(v.block, kind);
+    return v.real_values ? sweep_occupancy_of<float, OP_SELL, true, false, SPW, LB>(v.block, kind)
+                         : sweep_occupancy_of<float, OP_SELL, false, false, SPW, LB>(v.block, kind);
 }
 
 }  // namespace

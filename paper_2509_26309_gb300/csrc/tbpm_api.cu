@@ -388,15 +388,33 @@ SweepVariant variant(const tbpm_ctx *ctx, int states)
 // partials a final sweep of one instance writes per slot.
 int64_t sweep_warps(const tbpm_ctx *ctx) { return (int64_t)ctx->nblk_fin * ctx->sw_block / 32; }
 
-// The final sweep's grid: one wave of its own occupancy at the context's shape,
-// at most the other sweeps' grid. It holds more registers than a middle sweep
-// (the FP64 <psi0|psi> and the norm), so the middle sweeps' grid of whole waves
-// of their occupancy (FP64: three blocks of 512 threads per SM) would run it as
-// one and a half waves (two blocks per SM), the last half wave on half the SM.
-void set_final_grid(tbpm_ctx *ctx)
+// The grids of the first, second and final sweeps: one wave of each one's own
+// occupancy at the context's block shape. Their register counts differ from a
+// middle sweep's: the final sweep holds more (the FP64 <psi0|psi> and the
+// norm), so the middle sweeps' grid of whole waves of their occupancy (FP64:
+// three blocks of 512 threads per SM) would run it as one and a half waves,
+// the last half wave on half the SM; the first and second sweeps of the FP32
+// stored matrix hold fewer, and more resident blocks keep more of their
+// dependent loads in flight. The middle sweeps keep the context's grid.
+int kind_grid(const tbpm_ctx *ctx, const SweepVariant &v, SweepKind kind)
 {
-    const int occ = sweep_shape_occupancy(variant(ctx, 1), ctx->d_slice_inst != nullptr, true);
-    ctx->nblk_fin = occ > 0 ? std::min(ctx->nblk, occ * ctx->num_sms) : ctx->nblk;
+    const int occ = sweep_shape_occupancy(v, ctx->d_slice_inst != nullptr, kind);
+    return occ > 0 ? occ * ctx->num_sms : ctx->nblk;
+}
+
+void set_kind_grids(tbpm_ctx *ctx)
+{
+    const SweepVariant v = variant(ctx, 1);
+    ctx->nblk_first = kind_grid(ctx, v, SW_FIRST);
+    ctx->nblk_second = kind_grid(ctx, v, SW_SECOND);
+    ctx->nblk_fin = kind_grid(ctx, v, SW_FINAL);
+}
+
+// The grid of one single-state sweep kind.
+int sweep_kind_grid(const tbpm_ctx *ctx, SweepKind kind)
+{
+    return kind == SW_FIRST ? ctx->nblk_first : kind == SW_SECOND ? ctx->nblk_second
+           : kind == SW_FINAL ? ctx->nblk_fin : ctx->nblk;
 }
 
 void fill_operator(const tbpm_ctx *ctx, SweepParams &p)
@@ -504,7 +522,7 @@ int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, int B, int64_t ld, cudaStre
 {
     const SweepVariant v = variant(ctx, B);
     auto sweep = [&](SweepKind kind, bool a_imag, bool has_z, const SweepParams &p) {
-        return B == 1 ? launch_sweep(v, kind, a_imag, has_z, p, kind == SW_FINAL ? ctx->nblk_fin : ctx->nblk, s)
+        return B == 1 ? launch_sweep(v, kind, a_imag, has_z, p, sweep_kind_grid(ctx, kind), s)
                       : launch_sweep_b16(v, kind, a_imag, has_z, p, ctx->nblk16, s);
     };
     SweepParams p;
@@ -656,11 +674,11 @@ int enqueue_series(tbpm_ctx *ctx, const double2 *coef, int K, bool alt, void *in
     auto im = [alt](int k) { return alt && (k & 1) != 0; };
     p.x = in; p.z = nullptr; p.y = Bv[0];
     p.ia = K - 2; p.ib = -1; p.ic = K - 1; p.bscale = 1.0;
-    CU(launch_sweep(v, SW_FIRST, im(K - 2), false, p, ctx->nblk, s));
+    CU(launch_sweep(v, SW_FIRST, im(K - 2), false, p, ctx->nblk_first, s));
     if (K >= 4) {
         p.x = Bv[0]; p.z = nullptr; p.y = Bv[1];
         p.ia = K - 3; p.ib = K - 1; p.ic = -1;
-        CU(launch_sweep(v, SW_SECOND, im(K - 3), false, p, ctx->nblk, s));
+        CU(launch_sweep(v, SW_SECOND, im(K - 3), false, p, ctx->nblk_second, s));
     }
     for (int k = K - 4; k >= 1; --k) {
         p.x = Bv[(K - 3 - k) & 1];
@@ -1025,7 +1043,7 @@ static int apply_shape(tbpm_ctx *ctx, const tbpm_opts &o)
         ctx->sw_spw = v.spw;
         ctx->nblk = occ * ctx->num_sms;
     }
-    set_final_grid(ctx);
+    set_kind_grids(ctx);
     return TBPM_OK;
 }
 
@@ -1085,15 +1103,14 @@ static int autotune(tbpm_ctx *ctx)
             else
                 ks = {occ / 2, occ};
             ks.push_back(2 * occ);
-            for (int k : ks) {
-                cands.push_back({block, spw, k * ctx->num_sms, 0.0});
-                max_warps = std::max<int64_t>(max_warps, (int64_t)k * ctx->num_sms * block / 32);
-            }
+            for (int k : ks) cands.push_back({block, spw, k * ctx->num_sms, 0.0});
+            // the final sweep's partials, per warp of its own grid
+            max_warps = std::max<int64_t>(max_warps, (int64_t)kind_grid(ctx, v, SW_FINAL) * block / 32);
         }
     bool have_def = false;
     for (const Cand &c : cands) have_def |= c.block == def_block && c.spw == def_spw && c.grid == def_grid;
     if (!have_def) cands.push_back({def_block, def_spw, def_grid, 0.0});
-    // the final sweep's per-warp partials (slot 0) of the widest candidate
+    // the final sweep's per-warp partials (slot 0) of the widest candidate shape
     double2 *part = ctx->d_partials;
     double2 *own_part = nullptr;
     if (!multi && (size_t)max_warps > ctx->partials_cap) {
@@ -1114,10 +1131,12 @@ static int autotune(tbpm_ctx *ctx)
         cudaError_t e;
         p.x = ctx->d_psi; p.z = nullptr; p.y = Bv[0];
         p.ia = Kt - 2; p.ib = -1; p.ic = Kt - 1; p.bscale = 1.0;
-        if ((e = launch_sweep(v, SW_FIRST, false, false, p, grid, ctx->stream)) != cudaSuccess) return e;
+        if ((e = launch_sweep(v, SW_FIRST, false, false, p, kind_grid(ctx, v, SW_FIRST), ctx->stream)) != cudaSuccess)
+            return e;
         p.x = Bv[0]; p.y = Bv[1];
         p.ia = Kt - 3; p.ib = Kt - 1; p.ic = -1;
-        if ((e = launch_sweep(v, SW_SECOND, true, false, p, grid, ctx->stream)) != cudaSuccess) return e;
+        if ((e = launch_sweep(v, SW_SECOND, true, false, p, kind_grid(ctx, v, SW_SECOND), ctx->stream)) != cudaSuccess)
+            return e;
         for (int k = Kt - 4; k >= 1; --k) {
             p.x = Bv[(Kt - 3 - k) & 1];
             p.y = Bv[(Kt - 2 - k) & 1];
@@ -1129,9 +1148,7 @@ static int autotune(tbpm_ctx *ctx)
         p.z = Bv[(Kt - 4) & 1];
         p.y = ctx->d_psi;
         p.ia = 0; p.ib = -1; p.ic = -1; p.bscale = 0.5;
-        const int occ_fin = sweep_shape_occupancy(v, multi, true);         // as set_final_grid
-        const int grid_fin = occ_fin > 0 ? std::min(grid, occ_fin * ctx->num_sms) : grid;
-        return launch_sweep(v, SW_FINAL, false, true, p, grid_fin, ctx->stream);
+        return launch_sweep(v, SW_FINAL, false, true, p, kind_grid(ctx, v, SW_FINAL), ctx->stream);
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto time_us = [&](const Cand &c, int reps, double *us) -> int {
@@ -1181,7 +1198,7 @@ static int autotune(tbpm_ctx *ctx)
     ctx->nblk = best.grid;
     ctx->sw_block = best.block;
     ctx->sw_spw = best.spw;
-    set_final_grid(ctx);
+    set_kind_grids(ctx);
     ctx->cap_states = 0;
     ctx->tuned = true;
     ctx->tune_candidates = (int)cands.size();

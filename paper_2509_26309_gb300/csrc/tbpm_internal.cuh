@@ -242,7 +242,9 @@ struct tbpm_ctx {
     int64_t nnz = 0;
     // sweep grids (fixed per context so the dot partials are deterministic)
     int nblk = 0;                    // single-state kernels
-    int nblk_fin = 0;                // the single-state final sweep: one wave of its own occupancy
+    int nblk_first = 0;              // the single-state first, second and final sweeps:
+    int nblk_second = 0;             // one wave of each one's own occupancy at the
+    int nblk_fin = 0;                // context's block shape
     int nblk_kpm = 0;                // the single-state KPM kernel
     int nblk16 = 0;                  // 16-state kernels
     // coefficients
@@ -331,8 +333,9 @@ cudaError_t launch_bessel(double x, double tol, double2 *d_coef, int *d_K, cudaS
 enum SweepKind { SW_FIRST = 0, SW_SECOND = 1, SW_MID = 2, SW_FINAL = 3 };
 cudaError_t launch_sweep(const SweepVariant &v, SweepKind kind, bool a_imag, bool has_z,
                          const SweepParams &p, int grid, cudaStream_t s);
-// Resident blocks per SM of the middle sweep at v's shape (0: shape not built).
-int sweep_shape_occupancy(const SweepVariant &v, bool multi, bool fin = false);
+// Resident blocks per SM of one sweep kind (a SweepKind) at v's shape (0:
+// shape not built).
+int sweep_shape_occupancy(const SweepVariant &v, bool multi, int kind = SW_MID);
 bool sweep_shape_built(const SweepVariant &v);
 // The stored-matrix shapes built in their own translation units.
 cudaError_t launch_sell_s1_b1024(const SweepVariant &v, SweepKind kind, bool a_imag, bool has_z,
@@ -341,9 +344,9 @@ cudaError_t launch_sell_s2_b512(const SweepVariant &v, SweepKind kind, bool a_im
                                 const SweepParams &p, int grid, cudaStream_t s);
 cudaError_t launch_sell_s4_b512(const SweepVariant &v, SweepKind kind, bool a_imag, bool has_z,
                                 const SweepParams &p, int grid, cudaStream_t s);
-int occupancy_sell_s1_b1024(const SweepVariant &v, bool multi, bool fin);
-int occupancy_sell_s2_b512(const SweepVariant &v, bool multi, bool fin);
-int occupancy_sell_s4_b512(const SweepVariant &v, bool multi, bool fin);
+int occupancy_sell_s1_b1024(const SweepVariant &v, bool multi, int kind);
+int occupancy_sell_s2_b512(const SweepVariant &v, bool multi, int kind);
+int occupancy_sell_s4_b512(const SweepVariant &v, bool multi, int kind);
 
 // KPM sweep (cheb_sweep.cu).
 cudaError_t launch_kpm(const SweepVariant &v, const KpmParams &p, int grid, cudaStream_t s);
