@@ -12,6 +12,8 @@
 #include "tbpm_internal.cuh"
 #include "sweep_ops.cuh"
 
+#include <algorithm>
+
 namespace tbpm {
 namespace {
 
@@ -362,6 +364,27 @@ int sweep_grid_b16(int num_sms)
         per_sm < 1)
         per_sm = 4;
     return per_sm * num_sms;
+}
+
+// The final sweep holds more registers (the FP64 dots of 16 states) than the
+// others: one wave of its own occupancy for this operator, at most `grid`.
+int sweep_grid_b16_final(const SweepVariant &v, int num_sms, int grid)
+{
+    int per_sm = 0;
+    cudaError_t e;
+    if (v.op == OP_SELL)
+        e = v.real_values ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                &per_sm, sweep_b16<OP_SELL, true, B_REAL, false, true, true>, kBlock, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                &per_sm, sweep_b16<OP_SELL, false, B_REAL, false, true, true>, kBlock, 0);
+    else if (v.op == OP_STENCIL_MONO)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, sweep_b16<OP_STENCIL_MONO, true, B_REAL, false, true, true>, kBlock, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, sweep_b16<OP_STENCIL_BI, true, B_REAL, false, true, true>, kBlock, 0);
+    if (e != cudaSuccess || per_sm < 1) return grid;
+    return std::min(grid, per_sm * num_sms);
 }
 
 }  // namespace tbpm

@@ -408,6 +408,7 @@ void set_kind_grids(tbpm_ctx *ctx)
     ctx->nblk_first = kind_grid(ctx, v, SW_FIRST);
     ctx->nblk_second = kind_grid(ctx, v, SW_SECOND);
     ctx->nblk_fin = kind_grid(ctx, v, SW_FINAL);
+    ctx->nblk16_fin = sweep_grid_b16_final(v, ctx->num_sms, ctx->nblk16);
 }
 
 // The grid of one single-state sweep kind.
@@ -523,7 +524,7 @@ int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, int B, int64_t ld, cudaStre
     const SweepVariant v = variant(ctx, B);
     auto sweep = [&](SweepKind kind, bool a_imag, bool has_z, const SweepParams &p) {
         return B == 1 ? launch_sweep(v, kind, a_imag, has_z, p, sweep_kind_grid(ctx, kind), s)
-                      : launch_sweep_b16(v, kind, a_imag, has_z, p, ctx->nblk16, s);
+                      : launch_sweep_b16(v, kind, a_imag, has_z, p, kind == SW_FINAL ? ctx->nblk16_fin : ctx->nblk16, s);
     };
     SweepParams p;
     fill_operator(ctx, p);
@@ -531,7 +532,7 @@ int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, int B, int64_t ld, cudaStre
     p.psi = ctx->d_psi;
     p.psi0 = ctx->d_psi0;
     p.partials = ctx->d_partials;
-    p.nblk = B == 1 ? ctx->nblk : ctx->nblk16;
+    p.nblk = B == 1 ? ctx->nblk : ctx->nblk16_fin;            // the final sweep's partial stride
     const bool renorm = (ctx->flags & TBPM_F_RENORM) != 0;
     if (renorm) {
         p.scale = ctx->d_scale;
@@ -590,7 +591,7 @@ int enqueue_dos_chunk(tbpm_ctx *ctx, int K, int len, int B, int64_t ld, cudaStre
     if (B == 1)
         CU(launch_reduce_seg(ctx->d_partials, len, 1, npart, ctx->d_seg_off, nseg, ctx->d_counter, 1,
                              ctx->d_out, ld, s));
-    else CU(launch_reduce_b16(ctx->d_partials, len, ctx->nblk16, ctx->d_counter, 1, ctx->d_out, ld, s));
+    else CU(launch_reduce_b16(ctx->d_partials, len, ctx->nblk16_fin, ctx->d_counter, 1, ctx->d_out, ld, s));
     CU(launch_advance(ctx->d_counter, len, s));
     *launches += 2;
     return TBPM_OK;

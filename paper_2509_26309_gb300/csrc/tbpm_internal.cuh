@@ -247,6 +247,7 @@ struct tbpm_ctx {
     int nblk_fin = 0;                // context's block shape
     int nblk_kpm = 0;                // the single-state KPM kernel
     int nblk16 = 0;                  // 16-state kernels
+    int nblk16_fin = 0;              // the 16-state final sweep (its dot partials per block of it)
     // coefficients
     double2 *d_coef = nullptr;       // [kMaxTerms]
     int *d_K = nullptr;
@@ -475,6 +476,8 @@ cudaError_t launch_dot_b16(const void *a, const void *b, int64_t nslices, double
 cudaError_t launch_reduce_b16(const double2 *partials, int nslot, int nblk, const int *counter,
                               int offset, double2 *out, int64_t ld, cudaStream_t s);
 int sweep_grid_b16(int num_sms);
+// The batched final sweep's grid: one wave of its own occupancy, at most grid.
+int sweep_grid_b16_final(const SweepVariant &v, int num_sms, int grid);
 
 // One FP64 state (device, [n] complex) into column `col` of an interleaved
 // [n_pad][B] buffer of the given precision, in both dst0 and dst1 (aux.cu).
