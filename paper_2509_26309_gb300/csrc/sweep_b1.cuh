@@ -83,8 +83,11 @@ __device__ __forceinline__ void sell_group(const SweepParams &p, const int64_t (
 // writes the run's sum to the slot of the run's first slice (zeros to the
 // others), one butterfly per run instead of one per slice.
 // Each row's arithmetic is the same for every shape; only the grouping of the
-// dot partials follows the grid.
-template <typename R, int OP, int VM, int BM, bool AIMAG, bool HASZ, bool FINAL, bool MULTI, int SPW, int LB>
+// dot partials follows the grid. NORM (final sweeps when renormalising) adds the
+// sum of |y|^2: a compile-time choice, since a run-time test on norm_partials
+// let the compiler form the two FP64 FMAs of every row unconditionally.
+template <typename R, int OP, int VM, int BM, bool AIMAG, bool HASZ, bool FINAL, bool MULTI, int SPW, int LB,
+          bool NORM = false>
 __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
 {
     typedef typename V2<R>::T V;
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
     auto flush_run = [&]() {
         const double sr = warp_sum(dr), si = warp_sum(di);
         if (lane == 0) p.partials[(int64_t)p.delta * p.nslices + run_slot] = make_double2(sr, si);
-        if (p.norm_partials) {
+        if constexpr (NORM) {
             const double sn = warp_sum(nn);
             if (lane == 0) p.norm_partials[(int64_t)p.delta * p.nslices + run_slot] = make_double2(sn, 0.0);
         }
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
             const V q = psi0[row];
             fr.add_dot((float)q.x, (float)out.x, (float)q.y, (float)out.y);
             fi.add_dot((float)q.x, (float)out.y, -(float)q.y, (float)out.x);
-            if (p.norm_partials) fn.add_dot((float)out.x, (float)out.x, (float)out.y, (float)out.y);
+            if constexpr (NORM) fn.add_dot((float)out.x, (float)out.x, (float)out.y, (float)out.y);
         } else if (FINAL) {
             const V q = psi0[row];
             const double qr = (double)q.x, qi = (double)q.y;
@@ -155,12 +158,12 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
                     run_inst = inst;
                 } else if (lane == 0) {
                     p.partials[(int64_t)p.delta * p.nslices + s] = make_double2(0.0, 0.0);
-                    if (p.norm_partials) p.norm_partials[(int64_t)p.delta * p.nslices + s] = make_double2(0.0, 0.0);
+                    if constexpr (NORM) p.norm_partials[(int64_t)p.delta * p.nslices + s] = make_double2(0.0, 0.0);
                 }
             }
             dr = fma(qr, orr, fma(qi, oi, dr));
             di = fma(qr, oi, fma(-qi, orr, di));
-            if (p.norm_partials) nn = fma(orr, orr, fma(oi, oi, nn));
+            if constexpr (NORM) nn = fma(orr, orr, fma(oi, oi, nn));
         }
     };
     // one slice on its own (every operator; the tail of a group)
@@ -267,14 +270,14 @@ __global__ void __launch_bounds__(LB) sweep_b1(SweepParams p)
         if (lane == 0) {
             const bool lead = (threadIdx.x >> 5) == 0;
             p.partials[(int64_t)p.delta * nwarps + warp] = lead ? make_double2(v[0], v[1]) : make_double2(0.0, 0.0);
-            if (p.norm_partials)
+            if constexpr (NORM)
                 p.norm_partials[(int64_t)p.delta * nwarps + warp] = make_double2(lead ? v[2] : 0.0, 0.0);
         }
     } else if (FINAL) {
         dr = warp_sum(dr);
         di = warp_sum(di);
         if (lane == 0) p.partials[(int64_t)p.delta * nwarps + warp] = make_double2(dr, di);
-        if (p.norm_partials) {
+        if constexpr (NORM) {
             nn = warp_sum(nn);
             if (lane == 0) p.norm_partials[(int64_t)p.delta * nwarps + warp] = make_double2(nn, 0.0);
         }
@@ -298,6 +301,10 @@ cudaError_t sweep_dispatch(SweepKind kind, bool a_imag, bool has_z, const SweepP
         return a_imag ? launch_pdl(sweep_b1<R, OP, VM, B_ONE, true, true, false, MULTI, SPW, LB>, grid, block, pdl, s, p)
                       : launch_pdl(sweep_b1<R, OP, VM, B_ONE, false, true, false, MULTI, SPW, LB>, grid, block, pdl, s, p);
     case SW_FINAL:
+        // the sum of |y|^2 is formed only when renormalising (norm_partials set)
+        if (p.norm_partials)
+            return has_z ? launch_pdl(sweep_b1<R, OP, VM, B_REAL, false, true, true, MULTI, SPW, LB, true>, grid, block, pdl, s, p)
+                         : launch_pdl(sweep_b1<R, OP, VM, B_REAL, false, false, true, MULTI, SPW, LB, true>, grid, block, pdl, s, p);
         return has_z ? launch_pdl(sweep_b1<R, OP, VM, B_REAL, false, true, true, MULTI, SPW, LB>, grid, block, pdl, s, p)
                      : launch_pdl(sweep_b1<R, OP, VM, B_REAL, false, false, true, MULTI, SPW, LB>, grid, block, pdl, s, p);
     }
@@ -306,7 +313,7 @@ cudaError_t sweep_dispatch(SweepKind kind, bool a_imag, bool has_z, const SweepP
 
 // Resident blocks per SM of one sweep kind at this shape (the fewest over the
 // kind's forms: c_k real or imaginary; the final sweep with b_2, the form of
-// every final sweep but K = 3's).
+// every final sweep but K = 3's; SW_FINAL_NORM: the same with the norm).
 template <typename R, int OP, int VM, bool MULTI, int SPW, int LB>
 int sweep_occupancy_of(int block, int kind = SW_MID)
 {
@@ -323,6 +330,8 @@ int sweep_occupancy_of(int block, int kind = SW_MID)
                         occ(sweep_b1<R, OP, VM, B_ONE, false, false, false, MULTI, SPW, LB>));
     case SW_FINAL:
         return occ(sweep_b1<R, OP, VM, B_REAL, false, true, true, MULTI, SPW, LB>);
+    case SW_FINAL_NORM:
+        return occ(sweep_b1<R, OP, VM, B_REAL, false, true, true, MULTI, SPW, LB, true>);
     default:
         return occ(sweep_b1<R, OP, VM, B_ONE, false, true, false, MULTI, SPW, LB>);
     }

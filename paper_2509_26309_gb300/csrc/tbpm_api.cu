@@ -398,7 +398,9 @@ int64_t sweep_warps(const tbpm_ctx *ctx) { return (int64_t)ctx->nblk_fin * ctx->
 // dependent loads in flight. The middle sweeps keep the context's grid.
 int kind_grid(const tbpm_ctx *ctx, const SweepVariant &v, SweepKind kind)
 {
-    const int occ = sweep_shape_occupancy(v, ctx->d_slice_inst != nullptr, kind);
+    // a renormalising context's final sweeps also sum |y|^2 (more registers)
+    const int k = kind == SW_FINAL && (ctx->flags & TBPM_F_RENORM) ? SW_FINAL_NORM : (int)kind;
+    const int occ = sweep_shape_occupancy(v, ctx->d_slice_inst != nullptr, k);
     return occ > 0 ? occ * ctx->num_sms : ctx->nblk;
 }
 

@@ -332,6 +332,8 @@ cudaError_t launch_bessel(double x, double tol, double2 *d_coef, int *d_K, cudaS
 // or 4 with up to 512 (cheb_sweep_shapes*.cu). Other shapes are refused
 // (cudaErrorInvalidValue).
 enum SweepKind { SW_FIRST = 0, SW_SECOND = 1, SW_MID = 2, SW_FINAL = 3 };
+// for occupancy queries only: the final sweep that also sums |y|^2
+constexpr int SW_FINAL_NORM = 4;
 cudaError_t launch_sweep(const SweepVariant &v, SweepKind kind, bool a_imag, bool has_z,
                          const SweepParams &p, int grid, cudaStream_t s);
 // Resident blocks per SM of one sweep kind (a SweepKind) at v's shape (0:

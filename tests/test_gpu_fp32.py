@@ -9,6 +9,7 @@ sqrt(17 n) * 2^-24 * O(1), i.e. ~1e-5 at n = 1024. The tests require
 |dC| <= 3e-5 (n <= 1024) and a DOS L1 relative error <= 1e-4 (the target
 stated for the mixed-precision path).
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -187,6 +188,49 @@ def test_packed_sell_matches_plain_and_oracle(orc, case):
         assert np.array_equal(out[a][1], out[b][1]), a
     assert np.max(np.abs(out["packed_default"][0] - ref)) <= C_TOL
     assert np.max(np.abs(out["packed_default"][1] - ref_mu)) <= 1e-4
+
+
+def _bond_levels(h, levels):
+    """The same lattice with each bond's hopping scaled by 1 + 0.01 k, k one of
+    `levels` values fixed by the bond's two ends (the same both ways, so H stays
+    Hermitian); the diagonal is unchanged."""
+    rows = np.repeat(np.arange(h.n), np.diff(h.row_ptr))
+    lo, hi = np.minimum(rows, h.col), np.maximum(rows, h.col)
+    k = (lo * 1000003 + hi * 7920) % levels
+    off = rows != h.col
+    val = h.val.copy()
+    val[off] *= 1.0 + 0.01 * k[off]
+    return dataclasses.replace(h, val=val)
+
+
+@pytest.mark.parametrize("case,form", [("ragged", 2), ("levels40", 1), ("levels300", 0)])
+def test_packed_form_choice(orc, case, form):
+    """Which packed form a graphene matrix gets: a ragged last slice still packs
+    per row (its padding rows hold offset 0 and value 0); 40 distinct hoppings
+    fit the per-entry form's 8-bit indices but not the per-row form's 5-bit ones;
+    300 fit neither. Every form matches the plain one bit for bit at the same
+    launch shape and the oracle within the FP32 bars."""
+    if case == "ragged":
+        h = ti.graphene_csr(61, 43, onsite=ti.anderson_onsite(2 * 61 * 43, 1.0, 7))
+    else:
+        h = _bond_levels(ti.graphene_csr(64, 48, onsite=ti.anderson_onsite(2 * 64 * 48, 1.0, 8)),
+                         40 if case == "levels40" else 300)
+    if case == "ragged":
+        assert h.n % 32 != 0
+    rescale = max(9.0, 1.02 * ti.gershgorin_bound(h))
+    dt = math.pi / rescale
+    psi0 = ti.random_phase_state(h.n, 9)
+    ref = orc.dos_corr(h, rescale, psi0, dt, 64)
+    out = {}
+    for name, flags in (("packed", 0), ("plain", tb.TBPM_F_PLAIN_SELL)):
+        ctx = tb.tbpm_create(h.n, h.row_ptr, h.col, h.val, rescale,
+                             tb.make_opts(precision=tb.TBPM_FP32, flags=flags | tb.TBPM_F_NO_CLUSTER,
+                                          block_threads=256, slices_per_warp=2))
+        assert tb.tbpm_get_info(ctx)["packed"] == (form if name == "packed" else 0)
+        out[name] = (tb.tbpm_dos_corr(ctx, psi0, dt, 64), tb.kpm_moments(ctx, psi0, 128))
+    assert np.array_equal(out["packed"][0], out["plain"][0])
+    assert np.array_equal(out["packed"][1], out["plain"][1])
+    assert np.max(np.abs(out["packed"][0] - ref)) <= C_TOL
 
 
 def test_what_is_not_packed(orc):
