@@ -468,6 +468,8 @@ B_TBLOCK_STEP = (12 + 16) + (28 + 16) + (28 + 8 + 8)
 # interior on the monolayer (a 96 x 32-cell region, interior 90 x 26)
 TB_REGION_MONO = (96 * 32) / (90 * 26)
 B_TBLOCK_STEP_HALO = (12 * TB_REGION_MONO + 16) + (28 * TB_REGION_MONO + 16) + (28 * TB_REGION_MONO + 8 + 8)
+# one middle block of 6 sweeps with its halo re-reads (8.8 B per orbital-term)
+B_TBLOCK_MIDDLE_HALO = 28 * TB_REGION_MONO + 16
 
 
 def run_variants(args, dev, stream):
@@ -681,6 +683,10 @@ def run_variants(args, dev, stream):
         if flags == 0:
             roof["halo_basis"] = hbm_roof(v1s, B_TBLOCK_STEP_HALO / (K - 1),
                                           "blocked time step with the halo re-reads of the 1.31x tile region, per sweep")
+            roof["middle_block_basis"] = hbm_roof(
+                v1s, B_TBLOCK_MIDDLE_HALO / 6,
+                "a middle block's bytes per orbital-term (6 sweeps, halo re-reads included); the step's first and "
+                "final blocks move less, so this basis overstates the step's bytes")
         res[name] = {"value": v1s, "unit": UNIT, "ms_per_call": ms1s, "states": 1,
                      "n_steps": steps, "kernel_launches": tb.tbpm_get_info(c1s)["kernel_launches"],
                      "max_abs_dC_vs_oracle": None if orc4 is None else
