@@ -134,6 +134,31 @@ __device__ __forceinline__ double block_sum_f2(F2Sum *a, float2 *sm, int warp, i
     return out;
 }
 
+// The tile coordinates (t1, t2) of a block's tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ...: one division for the first, then a step of gridDim.x tiles
+// split once into whole rows of tiles (dq) and a remainder (dr), so that no
+// tile pays for two integer divisions.
+struct TileWalk {
+    int t1, t2, dq, dr, tiles2;
+    __device__ __forceinline__ void init(int tile, int step, int nt2)
+    {
+        tiles2 = nt2;
+        t1 = tile / nt2;
+        t2 = tile - t1 * nt2;
+        dq = step / nt2;
+        dr = step - dq * nt2;
+    }
+    __device__ __forceinline__ void next(int &n1, int &n2) const
+    {
+        n1 = t1 + dq;
+        n2 = t2 + dr;
+        if (n2 >= tiles2) {
+            n2 -= tiles2;
+            ++n1;
+        }
+    }
+};
+
 // This thread's staging slots: slot (cell j, v) at [(j * V4 + v) * threads].
 struct Stage {
     float4 *ps, *bx, *bz;
@@ -141,11 +166,10 @@ struct Stage {
 };
 
 template <int PER, bool KPM>
-__device__ __forceinline__ void prefetch_tile(const TbParams &p, const Stage &st, int tile, int r0, int lane,
+__device__ __forceinline__ void prefetch_tile(const TbParams &p, const Stage &st, int t1, int t2, int r0, int lane,
                                               bool first)
 {
     typedef TbCfg<PER, KPM> C;
-    const int t1 = tile / p.tiles2, t2 = tile - t1 * p.tiles2;
     const int o1 = t1 * C::T1 - kTbH, o2 = t2 * C::T2 - kTbH;
     const float4 *psi = reinterpret_cast<const float4 *>(p.psi);
     const float4 *bx = reinterpret_cast<const float4 *>(p.bx);
@@ -196,6 +220,9 @@ __device__ __forceinline__ void tb_rows(const float2 (&ps)[PER * R * C2], const 
                                         const float2 (&up)[C2][PER / 2], const float2 (&dn)[C2][PER / 2],
                                         float t, float tp, const float *c)
 {
+    // the sweep's coefficients, read from the block's table once
+    const float c0 = c[0], c1 = c[1];
+    const float c2 = FORM == 2 ? c[2] : 0.0f, c3 = FORM == 2 ? c[3] : 0.0f, c4 = FORM == 2 ? c[4] : 0.0f;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         float2 sum[C2][PER];                          // unscaled sum of each orbital's in-layer neighbours
@@ -233,8 +260,8 @@ __device__ __forceinline__ void tb_rows(const float2 (&ps)[PER * R * C2], const 
                 if (FORM != 2) {
                     // the psi and z terms, then d x, the dimer partner, t times the neighbours
                     float rx, ry;
-                    if (FORM == 0) { rx = fmaf(c[0], pv.x, -zz.x); ry = fmaf(c[0], pv.y, -zz.y); }
-                    else if (FORM == 1) { rx = fmaf(-c[1], pv.y, -zz.x); ry = fmaf(c[1], pv.x, -zz.y); }
+                    if (FORM == 0) { rx = fmaf(c0, pv.x, -zz.x); ry = fmaf(c0, pv.y, -zz.y); }
+                    else if (FORM == 1) { rx = fmaf(-c1, pv.y, -zz.x); ry = fmaf(c1, pv.x, -zz.y); }
                     else { rx = -zz.x; ry = -zz.y; }
                     rx = fmaf(on[i], xi.x, rx);
                     ry = fmaf(on[i], xi.y, ry);
@@ -242,13 +269,13 @@ __device__ __forceinline__ void tb_rows(const float2 (&ps)[PER * R * C2], const 
                     out.x = fmaf(t, sum[cc][o].x, rx);
                     out.y = fmaf(t, sum[cc][o].y, ry);
                 } else {
-                    const float tr = fmaf(-c[4], zz.x, fmaf(c[0], pv.x, -c[1] * pv.y));
-                    const float ti = fmaf(-c[4], zz.y, fmaf(c[0], pv.y, c[1] * pv.x));
+                    const float tr = fmaf(-c4, zz.x, fmaf(c0, pv.x, -c1 * pv.y));
+                    const float ti = fmaf(-c4, zz.y, fmaf(c0, pv.y, c1 * pv.x));
                     float dr = on[i] * xi.x, di = on[i] * xi.y;
                     if (dimer) { dr = fmaf(tp, pt.x, dr); di = fmaf(tp, pt.y, di); }
                     const float hr = fmaf(t, sum[cc][o].x, dr), hi = fmaf(t, sum[cc][o].y, di);
-                    out.x = fmaf(c[2], hr, fmaf(-c[3], hi, tr));
-                    out.y = fmaf(c[2], hi, fmaf(c[3], hr, ti));
+                    out.x = fmaf(c2, hr, fmaf(-c3, hi, tr));
+                    out.y = fmaf(c2, hi, fmaf(c3, hr, ti));
                 }
                 z[i] = out;
             }
@@ -365,10 +392,14 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
     // (across tiles too), so a buffer is rewritten only two barriers after its reads
     int nsweep = 0;
     constexpr int kExch = 2 * C::V4 * C::C2 * C::warps * 32;   // float2 per exchange buffer
-    if ((int)blockIdx.x < ntiles) prefetch_tile<PER, false>(p, st, blockIdx.x, r0, lane, first);
+    TileWalk tw;
+    tw.init(blockIdx.x, gridDim.x, p.tiles2);
+    if ((int)blockIdx.x < ntiles) prefetch_tile<PER, false>(p, st, tw.t1, tw.t2, r0, lane, first);
     __syncthreads();                               // the coefficient table
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int t1 = tile / p.tiles2, t2 = tile - t1 * p.tiles2;
+        const int t1 = tw.t1, t2 = tw.t2;
+        int n1, n2;                               // the block's next tile
+        tw.next(n1, n2);
         const int o1 = t1 * C::T1 - kTbH, o2 = t2 * C::T2 - kTbH;
         cp_async_wait_all();                      // the staging slots this thread filled
         if (C::C2 > 1) __syncwarp();              // and those its warp's other lanes filled
@@ -400,7 +431,9 @@ __global__ void __launch_bounds__(TbCfg<PER>::threads, 1) tb_block_kernel(TbPara
         }
         // the staging slots are free again: fetch the next tile during the sweeps
         if (C::C2 > 1) __syncwarp();              // every lane has read its slots
-        if (tile + (int)gridDim.x < ntiles) prefetch_tile<PER, false>(p, st, tile + gridDim.x, r0, lane, first);
+        if (tile + (int)gridDim.x < ntiles) prefetch_tile<PER, false>(p, st, n1, n2, r0, lane, first);
+        tw.t1 = n1;
+        tw.t2 = n2;
         // the register arrays trade roles each sweep: even sweeps read b_{k+1} from
         // xo and overwrite zo with b_k, odd sweeps the reverse. The loop is unrolled
         // over the kTbS sweep positions (each copy knows its arrays' roles and its
@@ -511,9 +544,13 @@ __global__ void __launch_bounds__(TbCfg<PER, true>::threads, 1) tb_kpm_kernel(Tb
     float on[N];
     int nsweep = 0;
     constexpr int kExch = 2 * C::V4 * C::C2 * C::warps * 32;
-    if ((int)blockIdx.x < ntiles) prefetch_tile<PER, true>(p, st, blockIdx.x, r0, lane, false);
+    TileWalk tw;
+    tw.init(blockIdx.x, gridDim.x, p.tiles2);
+    if ((int)blockIdx.x < ntiles) prefetch_tile<PER, true>(p, st, tw.t1, tw.t2, r0, lane, false);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int t1 = tile / p.tiles2, t2 = tile - t1 * p.tiles2;
+        const int t1 = tw.t1, t2 = tw.t2;
+        int n1, n2;                               // the block's next tile
+        tw.next(n1, n2);
         const int o1 = t1 * C::T1 - kTbH, o2 = t2 * C::T2 - kTbH;
         cp_async_wait_all();
 #pragma unroll
@@ -532,7 +569,9 @@ __global__ void __launch_bounds__(TbCfg<PER, true>::threads, 1) tb_kpm_kernel(Tb
                 zo[i + 1] = make_float2(bz.z, bz.w);
             }
         }
-        if (tile + (int)gridDim.x < ntiles) prefetch_tile<PER, true>(p, st, tile + gridDim.x, r0, lane, false);
+        if (tile + (int)gridDim.x < ntiles) prefetch_tile<PER, true>(p, st, n1, n2, r0, lane, false);
+        tw.t1 = n1;
+        tw.t2 = n2;
         bool cell_in[C::R][C::C2];
 #pragma unroll
         for (int cc = 0; cc < C::C2; ++cc) {
