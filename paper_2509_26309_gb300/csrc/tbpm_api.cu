@@ -2058,6 +2058,8 @@ int tbpm_set_current(tbpm_ctx *ctx, const int64_t *row_ptr, const int32_t *col, 
     ctx->cur.cols = static_cast<int32_t *>(d_col);
     ctx->cur.jx = static_cast<double2 *>(d_x);
     ctx->cur.jy = static_cast<double2 *>(d_y);
+    ctx->cur.imag = true;
+    for (int64_t e = 0; e < nent && ctx->cur.imag; ++e) ctx->cur.imag = sx[e].x == 0.0 && sy[e].x == 0.0;
     ctx->cur_nnz = (int64_t)cc.size();
     destroy_graphs(ctx);
     return TBPM_OK;

@@ -146,6 +146,7 @@ struct CurrentOp {
     const int32_t *cols = nullptr;
     const double2 *jx = nullptr;
     const double2 *jy = nullptr;
+    bool imag = false;            // every stored value of J_x and J_y is purely imaginary
 };
 
 constexpr int kFermiCap = TBPM_FERMI_MAX_TERMS;   // Fermi series terms; 2x as many quadrature nodes
