@@ -2,7 +2,7 @@
 // shape so that the autotuner can pick the block width and the number of
 // 32-row slices a warp works on at once. cheb_sweep.cu instantiates the
 // default shape (one slice per warp iteration, blocks of up to 512 threads)
-// for every operator; cheb_sweep_shapes*.cu instantiate the other shapes for
+// for every operator; cheb_sweep_s*.cu instantiate the other shapes for
 // the stored-matrix (SELL) operator. The recurrence each sweep kind computes is
 // described in cheb_sweep.cu.
 #pragma once

@@ -330,7 +330,7 @@ cudaError_t launch_bessel(double x, double tol, double2 *d_coef, int *d_K, cudaS
 // One Clenshaw sweep of the given kind (cheb_sweep.cu) at the launch shape
 // v.block x v.spw: every operator takes spw = 1 with blocks of up to 512
 // threads; the stored matrix also takes spw = 1 with 1024 threads and spw = 2
-// or 4 with up to 512 (cheb_sweep_shapes*.cu). Other shapes are refused
+// or 4 with up to 512 (cheb_sweep_s*.cu). Other shapes are refused
 // (cudaErrorInvalidValue).
 enum SweepKind { SW_FIRST = 0, SW_SECOND = 1, SW_MID = 2, SW_FINAL = 3 };
 // for occupancy queries only: the final sweep that also sums |y|^2
