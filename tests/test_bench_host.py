@@ -33,6 +33,22 @@ def test_survey_bytes_per_orbital_term():
     assert bench.SURVEY_B_PER_TERM == 164
 
 
+def test_stored_matrix_and_blocked_stencil_byte_bases():
+    """Per orbital-term bytes of the FP32 forms: plain SELL (3 x (int32 column +
+    FP32 value) + FP32 diagonal + slice offset), packed per entry (16-bit offset
+    + 8-bit index), packed per row (one 64-bit word + diagonal); the blocked
+    stencil's step (first, middle and final blocks over 17 sweeps, without and
+    with the 96 x 32 / 90 x 26 region's halo re-reads) and one middle block of 6
+    sweeps with its halo (8.8 B)."""
+    assert bench.B_SELL32 == pytest.approx(28.25)
+    assert bench.B_SELL32_PACKED == pytest.approx(13.25)
+    assert bench.B_SELL32_ROWS == 12
+    assert bench.B_TBLOCK_STEP / 17 == pytest.approx(116 / 17)
+    region = (96 * 32) / (90 * 26)
+    assert bench.B_TBLOCK_STEP_HALO == pytest.approx(68 * region + 48)
+    assert bench.B_TBLOCK_MIDDLE_HALO / 6 == pytest.approx(8.79, abs=0.01)
+
+
 def test_traffic_record_follows_the_kernel_source(tmp_path, monkeypatch):
     """The recorded DRAM bytes are reported only while the sweep sources are the
     ones they were measured on."""
